@@ -1,0 +1,393 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, textbook special cases, exact identities of the upwind DG operator,
+values printed in the paper, and brute force on tiny inputs.  A dropped term,
+a wrong sign or index, or a transposed operand in ``oracle/`` breaks at least
+one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import legendre as npleg
+from numpy.polynomial import polynomial as P
+
+from oracle import lsrk
+from oracle.dg import ConstantField, PhaseSpaceField, Problem
+from oracle.quadrature import (Tables1D, gauss_legendre, gauss_lobatto,
+                               lagrange_derivatives, lagrange_values)
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+
+
+def _problem(w, basis="gl", field=None):
+    if field is None:
+        if w.field_kind == 0:
+            field = ConstantField(w.a_const)
+        else:
+            field = PhaseSpaceField(w.dx, w.dv, W.e_function(w))
+    shear = None if w.shear is None else np.array(w.shear).reshape(w.dx, w.dx)
+    return Problem(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
+                   field, shear=shear, basis=basis)
+
+
+# ---------------------------------------------------------------------------
+# 1D tables (Sec. 2.5: Gauss exact to 2n-1, Gauss-Lobatto to 2n-3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_gauss_legendre_exactness(n):
+    x, w = gauss_legendre(n)
+    for m in range(2 * n):
+        exact = 0.0 if m % 2 else 2.0 / (m + 1)
+        assert abs(np.sum(w * x ** m) - exact) < 1e-14
+    # and not exact one degree higher (even monomial 2n)
+    assert abs(np.sum(w * x ** (2 * n)) - 2.0 / (2 * n + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_gauss_lobatto_exactness(n):
+    x, w = gauss_lobatto(n)
+    assert x[0] == -1.0 and x[-1] == 1.0
+    for m in range(2 * n - 2):
+        exact = 0.0 if m % 2 else 2.0 / (m + 1)
+        assert abs(np.sum(w * x ** m) - exact) < 1e-13
+    m = 2 * n - 2
+    assert abs(np.sum(w * x ** m) - 2.0 / (m + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("basis", ["gl", "gll"])
+def test_lagrange_tables_reproduce_polynomials(k, basis):
+    T = Tables1D(k, basis)
+    rng = np.random.default_rng(k)
+    coef = rng.standard_normal(k + 1)                 # random degree-k polynomial
+    vals = P.polyval(T.nodes, coef)
+    dcoef = P.polyder(coef)
+    x = np.linspace(-1, 1, 7)
+    assert np.allclose(lagrange_values(T.nodes, x) @ vals, P.polyval(x, coef), atol=1e-12)
+    assert np.allclose(lagrange_derivatives(T.nodes, x) @ vals, P.polyval(x, dcoef), atol=1e-11)
+    assert np.allclose(lagrange_values(T.nodes, T.nodes), np.eye(k + 1), atol=1e-14)
+    assert abs(T.lp @ vals - P.polyval(1.0, coef)) < 1e-12
+    assert abs(T.lm @ vals - P.polyval(-1.0, coef)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# values printed in the paper
+# ---------------------------------------------------------------------------
+def test_paper_table_dofs_per_cell():
+    g = json.load(open(GOLDEN))["dofs_per_cell"]
+    for i, k in enumerate(g["k_rows"]):
+        for j, d in enumerate(g["d_cols"]):
+            dx = d // 2
+            p = Problem(dx, d - dx, k, [1] * dx, [1] * (d - dx), [0] * dx, [1] * dx,
+                        [0] * (d - dx), [1] * (d - dx), ConstantField(np.zeros(d)))
+            assert p.dofs_per_cell == g["values"][i][j]
+
+
+def test_paper_table_mapping_memory():
+    g = json.load(open(GOLDEN))["mapping_doubles_per_qpoint"]
+    n, dx, dv = g["k"] + 1, g["dx"], g["dv"]
+    tensor = (n ** dx * dx ** 2 + n ** dv * dv ** 2) / n ** (dx + dv)
+    assert round(tensor, 2) == g["tensor_product"]
+    assert (dx + dv) ** 2 == g["full_jacobian"]
+
+
+def test_paper_table_scaling_sizes():
+    g = json.load(open(GOLDEN))["strong_scaling_dofs"]
+    n = g["k"] + 1
+    for row in g["rows"]:
+        cells = [c // n for c in row["dofs_per_direction"]]
+        p = Problem(3, 3, g["k"], cells[:3], cells[3:], [0] * 3, [1] * 3, [0] * 3, [1] * 3,
+                    ConstantField(np.zeros(6)))
+        assert abs(p.n_dofs / row["dofs"] - 1.0) < 0.03
+
+
+# ---------------------------------------------------------------------------
+# brute force: axis-by-axis evaluation == dense Kronecker matrices
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dx,dv,k,cells", [
+    (1, 1, 3, (3, 2)), (1, 1, 1, (1, 2)), (2, 1, 2, (2, 1, 3)), (1, 2, 4, (2, 2, 1)),
+    (2, 2, 1, (2, 1, 2, 1)), (2, 3, 1, (1, 2, 1, 2, 1)), (3, 3, 1, (1, 1, 2, 1, 1, 2)),
+    (3, 2, 2, (1, 1, 1, 1, 1)), (1, 1, 5, (2, 2)),
+])
+@pytest.mark.parametrize("kind", ["const", "phase"])
+def test_axiswise_equals_dense(dx, dv, k, cells, kind):
+    rng = np.random.default_rng(dx * 10 + dv)
+    d = dx + dv
+    if kind == "const":
+        field = ConstantField(rng.uniform(-1, 1, d))
+    else:
+        if dv < dx:
+            pytest.skip("phase-space field needs dv >= dx")
+        amp = rng.uniform(0.2, 1, dv)
+        field = PhaseSpaceField(dx, dv, lambda y: amp * np.cos(2 * np.pi * y.sum(-1, keepdims=True) + np.arange(dv)))
+    shear = np.eye(dx) + 0.1 * np.triu(np.ones((dx, dx)), 1)
+    p = Problem(dx, dv, k, cells[:dx], cells[dx:], [0] * dx, [1] * dx, [-1] * dv, [1] * dv,
+                field, shear=shear)
+    u = rng.standard_normal(p.n_dofs)
+    a = p.apply(u)
+    b = p.apply_dense(u)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+# ---------------------------------------------------------------------------
+# textbook special case: k = 0 is first-order upwind finite volumes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("a", [(1.0, 0.5), (-0.7, 0.3), (0.4, -1.2), (-1.0, -2.0)])
+def test_k0_is_upwind_finite_volume(a):
+    nx, nv = 5, 4
+    p = Problem(1, 1, 0, (nx,), (nv,), (0,), (2,), (0,), (1,), ConstantField(a))
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(p.n_dofs)
+    U = u.reshape(nv, nx)                           # cell = ix + nx * iv
+    h = (2.0 / nx, 1.0 / nv)
+    du = np.zeros_like(U)
+    for axis, aj, hj in ((1, a[0], h[0]), (0, a[1], h[1])):
+        if aj > 0:
+            du -= aj / hj * (U - np.roll(U, 1, axis=axis))
+        else:
+            du -= aj / hj * (np.roll(U, -1, axis=axis) - U)
+    assert np.allclose(p.apply(u), du.reshape(-1), atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# invariants of the upwind DG operator
+# ---------------------------------------------------------------------------
+def _small_workloads():
+    return [
+        W.shrink(W.config_2d(), cells_x=(3,), cells_v=(4,)),
+        W.shrink(W.config_4d(), cells_x=(2, 3), cells_v=(3, 2), k=2),
+        W.shrink(W.config_6d(), cells_x=(2, 1, 1), cells_v=(1, 2, 1), k=1),
+        W.shrink(W.config_adjoint(), cells_x=(2, 1), cells_v=(1, 2, 1), k=2),
+    ]
+
+
+@pytest.mark.parametrize("w", _small_workloads(), ids=lambda w: w.name)
+def test_annihilates_constants(w):
+    p = _problem(w)
+    r = p.apply(np.ones(p.n_dofs))
+    scale = np.max(np.abs(p.apply(np.random.default_rng(0).standard_normal(p.n_dofs))))
+    assert np.max(np.abs(r)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("w", _small_workloads(), ids=lambda w: w.name)
+def test_conserves_mass(w):
+    p = _problem(w)
+    u = np.random.default_rng(1).standard_normal(p.n_dofs)
+    Mdiag = p.mass_diagonal()
+    Lu = p.apply(u)
+    assert abs(Mdiag @ Lu) <= 1e-13 * (np.abs(Mdiag) @ np.abs(Lu))
+
+
+def _independent_traces(vals, nodes):
+    """Value at -1 and +1 of the degree-k interpolant through (nodes, vals),
+    by a monomial fit (independent of the oracle's Lagrange tables)."""
+    c = P.polyfit(nodes, vals, len(nodes) - 1)
+    return P.polyval(-1.0, c), P.polyval(1.0, c)
+
+
+@pytest.mark.parametrize("w", _small_workloads()[:3], ids=lambda w: w.name)
+def test_energy_identity(w):
+    """u^T M L u = -1/2 sum over faces of |J| W_perp |c_n| [u]^2 (upwind flux,
+    divergence-free speed that does not vary along its own direction)."""
+    p = _problem(w)
+    u = np.random.default_rng(2).standard_normal(p.n_dofs)
+    lhs = u @ (p.mass_diagonal() * p.apply(u))
+    zeta, wq = npleg.leggauss(p.n)
+    d, n = p.d, p.n
+    h = np.array(w.h)
+    S = np.eye(w.dx) if w.shear is None else np.array(w.shear).reshape(w.dx, w.dx)
+    Sinv = np.linalg.inv(S)
+    detJ = np.linalg.det(S) * np.prod(h / 2)
+    E = W.e_function(w) if w.field_kind == 1 else None
+    rhs = 0.0
+    for e in range(p.ncells):
+        cc = (e // p.strides) % p.cells
+        Ue = u[e * n ** d:(e + 1) * n ** d].reshape([n] * d, order="F")
+        for j in range(d):
+            # this cell is the left side of its +face along j
+            cr = cc.copy()
+            cr[j] = (cr[j] + 1) % p.cells[j]
+            er = int(np.sum(cr * p.strides))
+            Ur = u[er * n ** d:(er + 1) * n ** d].reshape([n] * d, order="F")
+            for idx in np.ndindex(*([n] * (d - 1))):
+                full = list(idx[:j]) + [slice(None)] + list(idx[j:])
+                _, tl = _independent_traces(Ue[tuple(full)], zeta)
+                tr, _ = _independent_traces(Ur[tuple(full)], zeta)
+                q = [zeta[i] for i in idx]
+                pos = q[:j] + [1.0] + q[j:]            # reference face point
+                y = np.array([w.lo[m] + h[m] * (cc[m] + (pos[m] + 1) / 2) for m in range(d)])
+                if w.field_kind == 0:
+                    a = np.array(w.a_const)
+                else:
+                    a = np.concatenate([y[w.dx:2 * w.dx], E(y[None, :w.dx])[0]])
+                c = np.concatenate([(2 / h[:w.dx]) * (Sinv @ a[:w.dx]), (2 / h[w.dx:]) * a[w.dx:]])
+                wperp = np.prod([wq[i] for i in idx])
+                rhs += -0.5 * detJ * wperp * abs(c[j]) * (tl - tr) ** 2
+    assert lhs < 0
+    assert abs(lhs - rhs) <= 1e-11 * abs(rhs)
+
+
+@pytest.mark.parametrize("w", _small_workloads(), ids=lambda w: w.name)
+def test_transpose_is_mass_scaled_negated_field(w):
+    """L^T = M L(-a) M^{-1} for the upwind flux (exact, cell by cell)."""
+    p = _problem(w)
+    L = p.assemble().toarray()
+    pn = p.with_field(p.field.negated())
+    Ln = pn.assemble().toarray()
+    Md = p.mass_diagonal()
+    rhs = (Md[:, None] * Ln) / Md[None, :]
+    assert np.max(np.abs(L.T - rhs)) <= 1e-12 * np.max(np.abs(L))
+    # the oracle's adjoint routine is the transpose
+    y = np.random.default_rng(4).standard_normal(p.n_dofs)
+    assert np.allclose(p.apply_adjoint(y), L.T @ y, rtol=0, atol=1e-12 * np.max(np.abs(L.T @ y)))
+
+
+@pytest.mark.parametrize("w", _small_workloads()[:2], ids=lambda w: w.name)
+def test_gl_collocation_similar_to_gll_gauss(w):
+    """GL collocation and the paper's GLL basis with Gauss quadrature span the
+    same space with the same quadrature: L_GL = V L_GLL V^{-1} with
+    V_qi = phi^GLL_i(zeta_q) applied cell by cell."""
+    pg = _problem(w, "gl")
+    pl = _problem(w, "gll")
+    Lg = pg.assemble().toarray()
+    Ll = pl.assemble().toarray()
+    T = Tables1D(w.k, "gll")
+    V1 = lagrange_values(T.nodes, T.zeta)
+    V = np.ones((1, 1))
+    for _ in range(pg.d):
+        V = np.kron(V1, V)
+    Vg = np.kron(np.eye(pg.ncells), V)
+    assert np.max(np.abs(Lg @ Vg - Vg @ Ll)) <= 1e-11 * np.max(np.abs(Lg))
+
+
+def test_consistency_with_the_pde():
+    """L u -> -a . grad u for smooth u; a wrong sign gives relative error ~2."""
+    errs = []
+    for N in (8, 16):
+        w = W.config_2d(cells=N)
+        p = _problem(w)
+        zeta = npleg.leggauss(w.n)[0]
+        u = W.separable_state(w, zeta)
+        # exact: -(a1 d/dx + a2 d/dv) sin(2 pi x) sin(2 pi v)
+        fx = [lambda y: 2 * np.pi * np.cos(2 * np.pi * y), lambda y: np.sin(2 * np.pi * y)]
+        fv = [lambda y: np.sin(2 * np.pi * y), lambda y: 2 * np.pi * np.cos(2 * np.pi * y)]
+        ux = W.separable_state(W.Workload(**{**w.__dict__, "u0_factors": fx}), zeta)
+        uv = W.separable_state(W.Workload(**{**w.__dict__, "u0_factors": fv}), zeta)
+        exact = -(w.a_const[0] * ux + w.a_const[1] * uv)
+        errs.append(np.linalg.norm(p.apply(u) - exact) / np.linalg.norm(exact))
+    assert errs[1] < 2e-3
+    assert errs[0] / errs[1] > 4.0
+
+
+# ---------------------------------------------------------------------------
+# LSRK(5,4) (Sec. 5.4, Kennedy-Carpenter-Lewis 2R scheme)
+# ---------------------------------------------------------------------------
+def test_lsrk_order_conditions():
+    A, b, c = lsrk.butcher(frac=True)
+    s = lsrk.STAGES
+    Ac = [sum(A[i][j] * c[j] for j in range(s)) for i in range(s)]
+    Ac2 = [sum(A[i][j] * c[j] ** 2 for j in range(s)) for i in range(s)]
+    AAc = [sum(A[i][j] * Ac[j] for j in range(s)) for i in range(s)]
+    conds = [
+        (sum(b), 1), (sum(b[i] * c[i] for i in range(s)), 0.5),
+        (sum(b[i] * c[i] ** 2 for i in range(s)), 1 / 3), (sum(b[i] * Ac[i] for i in range(s)), 1 / 6),
+        (sum(b[i] * c[i] ** 3 for i in range(s)), 0.25), (sum(b[i] * c[i] * Ac[i] for i in range(s)), 1 / 8),
+        (sum(b[i] * Ac2[i] for i in range(s)), 1 / 12), (sum(b[i] * AAc[i] for i in range(s)), 1 / 24),
+    ]
+    from fractions import Fraction
+    for val, target in conds:
+        t = Fraction(target).limit_denominator(100)
+        assert abs(float(val - t)) < 1e-18
+
+
+def test_lsrk_low_storage_equals_butcher_form():
+    rng = np.random.default_rng(5)
+    Lm = rng.standard_normal((7, 7))
+    u = rng.standard_normal(7)
+    a = lsrk.step(lambda x: Lm @ x, u, 0.05)
+    b = lsrk.step_butcher(lambda x: Lm @ x, u, 0.05)
+    assert np.allclose(a, b, atol=1e-14)
+
+
+def test_lsrk_stability_polynomial():
+    g = lsrk.stability_polynomial_coeffs()
+    for m in range(5):
+        assert abs(float(g[m]) - 1.0 / math.factorial(m)) < 1e-15
+    lam, dt = -3.0 + 2.0j, 0.1
+    z = lam * dt
+    R = sum(float(g[m]) * z ** m for m in range(6))
+    y = lsrk.step(lambda x: lam * x, np.array([1.0 + 0j]), dt)
+    assert abs(y[0] - R) < 1e-14
+
+
+def test_lsrk_temporal_order_four():
+    import scipy.sparse.linalg as spla
+    w = W.shrink(W.config_2d(), cells_x=(4,), cells_v=(4,))
+    p = _problem(w)
+    L = p.assemble()
+    zeta = npleg.leggauss(w.n)[0]
+    u0 = W.separable_state(w, zeta)
+    T = 0.05
+    exact = spla.expm_multiply(L * T, u0)
+    errs = []
+    for nsteps in (8, 16):
+        u = u0.copy()
+        for _ in range(nsteps):
+            u = lsrk.step(lambda x: L @ x, u, T / nsteps)
+        errs.append(np.linalg.norm(u - exact))
+    assert 3.6 < math.log2(errs[0] / errs[1]) < 4.6
+
+
+def _rk_run(p, u, dt, steps):
+    L = p.assemble()
+    for _ in range(steps):
+        u = lsrk.step(lambda x: L @ x, u, dt)
+    return u
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_convergence_order_k_plus_one(k):
+    """Product of sines transported by a constant field; the L2 error at a
+    fixed time falls like h^{k+1} (smooth data, upwind DG)."""
+    errs = []
+    for N in (4, 8, 16):
+        w = W.config_2d(cells=N)
+        w = W.Workload(**{**w.__dict__, "k": k, "final_time": 0.25})
+        p = _problem(w)
+        zeta = npleg.leggauss(w.n)[0]
+        u0 = W.separable_state(w, zeta)
+        dt, steps = W.time_step(w)
+        dt, steps = dt / 4, steps * 4
+        u = _rk_run(p, u0, dt, steps)
+        T = dt * steps
+        shifted = W.Workload(**{**w.__dict__, "u0_factors": (
+            lambda y: np.sin(2 * np.pi * (y - w.a_const[0] * T)),
+            lambda y: np.sin(2 * np.pi * (y - w.a_const[1] * T)))})
+        exact = W.separable_state(shifted, zeta)
+        diff = u - exact
+        errs.append(math.sqrt(diff @ (p.mass_diagonal() * diff)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > k + 1 - 0.3, rates
+
+
+def test_one_period_return_2d_config():
+    """The 2D workload (16 x 16, k = 3, a = (1, 0.5)) returns to its initial
+    state after T = 2 up to the discretisation error."""
+    w = W.config_2d()
+    p = _problem(w)
+    zeta = npleg.leggauss(w.n)[0]
+    u0 = W.separable_state(w, zeta)
+    dt, steps = W.time_step(w)
+    assert steps == 240
+    u = _rk_run(p, u0, dt, steps)
+    Md = p.mass_diagonal()
+    rel = math.sqrt((u - u0) @ (Md * (u - u0)) / (u0 @ (Md * u0)))
+    assert rel < 2e-4
+    # mass conserved to round-off, energy non-increasing
+    assert abs(Md @ u - Md @ u0) < 1e-13
+    assert u @ (Md * u) <= u0 @ (Md * u0)
