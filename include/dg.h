@@ -1,0 +1,271 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) high-dimensional DG advection library.
+ *
+ * The library applies the matrix-free, sum-factorised, upwind discontinuous
+ * Galerkin advection operator of Munch, Kormann & Kronbichler, "hyper.deal:
+ * An efficient, matrix-free finite-element library for high-dimensional
+ * partial differential equations" (arXiv 2002.08110), on the tensor product
+ * of a configuration-space mesh (x, dim_x <= 3) and a velocity-space mesh
+ * (v, dim_v <= 3), and integrates it in time with the five-stage, fourth-order
+ * low-storage Runge-Kutta scheme the paper uses (Sec. 5.4).
+ *
+ * Discretisation (fixed by this library):
+ *  - PDE df/dt + div(a f) = 0 on a periodic box (Sec. 1.1, Eq. intro:advection);
+ *  - tensor-product polynomials of degree k, d = dim_x + dim_v (Sec. 2.3),
+ *    nodal at the k+1 Gauss-Legendre points of each direction, with the same
+ *    points as quadrature (collocation: diagonal mass matrix, Sec. 1.1 and
+ *    Algorithm 2 step 4);
+ *  - weak form in reference coordinates with the phase-space Jacobian
+ *    J = diag(J_x, J_v) (Sec. 1.1 Eq. into:adv:ref, Sec. 3) and the upwind flux;
+ *  - element-centric evaluation over all cell pairs (Algorithms 1 and 2).
+ *
+ * Supported: 1 <= dim_x <= 3, 1 <= dim_v <= 3, 2 <= d <= 6, 1 <= k <= 5.
+ *
+ * Conventions shared by every call:
+ *  - Vectors are device memory owned by the caller, contiguous, at least
+ *    16-byte aligned, n_dofs elements, laid out as
+ *        index = cell * (k+1)^d + q,
+ *    cell = sum_j c_j * prod_{m<j} N_m over the d cell coordinates (the x
+ *    dimensions first, x_1 fastest; i.e. cell = c_x + N_x * c_v as in the
+ *    paper's lexicographic enumeration, Sec. 3.2), and q = sum_j q_j (k+1)^j
+ *    over the node indices (x_1 fastest).
+ *  - Precision codes (argument ``prec``):
+ *      DG_PREC_FP64  (0): FP64 vectors, FP64 arithmetic;
+ *      DG_PREC_FP32  (1): FP32 vectors / stage vectors, FP32 sweeps
+ *                         (in dg_rk_step the state u stays FP64);
+ *      DG_PREC_MIXED (2): FP64 vectors, FP32 sweeps and fluxes.
+ *  - Calls that take ``stream`` (a cudaStream_t, NULL = legacy default
+ *    stream) only enqueue work: they are asynchronous with respect to the
+ *    host.  Errors found on the host are returned at once; errors found on
+ *    the device (non-finite results) are latched in the handle and reported
+ *    by dg_check().
+ *  - No function throws; every function returns a dg_status.  After an
+ *    error, dg_last_error() gives a message (thread-local).
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef DG_H
+#define DG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_ABI_VERSION 1
+
+typedef struct dg_ctx* dg_handle;
+typedef struct dg_batch_ctx* dg_batch;
+
+typedef enum {
+    DG_OK = 0,
+    DG_ERR_INVALID_ARG = 1,   /* bad pointer, size, precision or geometry   */
+    DG_ERR_UNSUPPORTED = 2,   /* dimension or degree outside the ranges     */
+    DG_ERR_CUDA = 3,          /* a CUDA runtime call failed                 */
+    DG_ERR_OOM = 4,           /* device or host allocation failed           */
+    DG_ERR_NONFINITE = 5,     /* a kernel produced NaN or Inf               */
+    DG_ERR_TIMEOUT = 6        /* reserved: a bounded device wait gave up    */
+} dg_status;
+
+typedef enum {
+    DG_PREC_FP64 = 0,
+    DG_PREC_FP32 = 1,
+    DG_PREC_MIXED = 2
+} dg_precision;
+
+/* Velocity field kinds. */
+typedef enum {
+    /* a = a_const, constant and uniform (the setting of Sec. 5.1). */
+    DG_FIELD_CONSTANT = 0,
+    /* Phase space (Sec. 6): a_x = (v_1, ..., v_{dim_x}) (needs dim_v >= dim_x)
+     * and a_v = E(x), E given at the x quadrature nodes (e_nodes). */
+    DG_FIELD_PHASE_SPACE = 1
+} dg_field_kind;
+
+/*
+ * Geometry and velocity field (Sec. 3: tensor product of two meshes; the
+ * mapping is block diagonal).  Configuration space is the lattice box
+ * [x_lo, x_hi] (first dim_x entries) with N_x cells per direction, mapped
+ * affinely by x = S y (S = shear_x, row-major dim_x x dim_x; an all-zero
+ * matrix means identity).  Velocity space is the box [v_lo, v_hi] with N_v
+ * cells per direction.  All boundaries are periodic.
+ *
+ * e_nodes (DG_FIELD_PHASE_SPACE only; NULL means E = 0): host array of
+ *   n_xcells * (k+1)^dim_x * dim_v doubles, E_i at the x node (cell c_x,
+ *   node q_x), index (c_x * (k+1)^dim_x + q_x) * dim_v + i, with c_x and q_x
+ *   lexicographic, x_1 fastest; node coordinates as given by
+ *   dg_node_coordinates().  The library copies it; the caller keeps ownership.
+ */
+typedef struct {
+    double x_lo[3], x_hi[3];
+    double v_lo[3], v_hi[3];
+    double shear_x[9];
+    int field_kind;
+    double a_const[6];
+    const double* e_nodes;
+} dg_geometry;
+
+typedef struct {
+    long long n_dofs;         /* |C| (k+1)^d  (Sec. 2.3, Eq. totalunknowns) */
+    long long n_cells;        /* |C_x| |C_v|                                */
+    long long n_xcells, n_vcells;
+    int dofs_per_cell;        /* (k+1)^d                                    */
+    int dim_x, dim_v, degree;
+    double speed_sum;         /* sum_j max over nodes of |a_j| / h_j        */
+    double det_jacobian;      /* |J| of every cell                          */
+    double h[6];              /* cell sizes (lattice sizes in x)            */
+} dg_info_t;
+
+/* Launch configuration of the cell kernels (chosen by dg_autotune). */
+typedef struct {
+    int threads;              /* threads per block                          */
+    int cells_per_block;      /* cells handled by one block (small cells)   */
+    int order[6];             /* order in which the d directions are swept  */
+    int variant;              /* 0 = generic, 1 = specialised (if present)  */
+} dg_launch;
+
+/* Library version (DG_ABI_VERSION). */
+int dg_version(void);
+
+/* Message of the last error on this thread ("" if none).  The pointer stays
+ * valid until the next call on this thread. */
+const char* dg_last_error(void);
+
+/*
+ * n = degree+1 Gauss-Legendre nodes and weights on [-1, 1] (Sec. 2.5), in
+ * ascending order, written to host arrays of n doubles (weights may be NULL).
+ * INVALID_ARG if degree < 0 or degree > 5 or nodes == NULL.
+ */
+dg_status dg_reference_nodes(int degree, double* nodes, double* weights);
+
+/*
+ * Create a handle for the mesh T_x (x) T_v (Sec. 3, Eq. concept:tria:tensor)
+ * of degree ``degree`` on the current CUDA device.  cells_x[dim_x] and
+ * cells_v[dim_v] give cells per direction (>= 1).  Computes the 1D tables in
+ * FP64 on the host and the contravariant speeds c = J^{-1} a at every x and
+ * v node (never the d-dimensional field, Sec. 6), and uploads them.  No
+ * vector is allocated.  Errors: INVALID_ARG (NULL pointers, bad sizes,
+ * empty boxes, singular shear, field kind), UNSUPPORTED (dimensions or degree
+ * out of range, phase-space field with dim_v < dim_x), OOM, CUDA.
+ */
+dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const int* cells_v,
+                    const dg_geometry* geometry, dg_handle* out);
+
+/* Release the handle and all device memory it owns.  NULL is a no-op. */
+dg_status dg_destroy(dg_handle h);
+
+/* Sizes and geometry of a handle (host struct filled by the library). */
+dg_status dg_info(dg_handle h, dg_info_t* info);
+
+/*
+ * Node coordinates (host output).  space 0: x nodes, n_xcells*(k+1)^dim_x
+ * rows of dim_x lattice coordinates y (physical x = S y); space 1: v nodes,
+ * n_vcells*(k+1)^dim_v rows of dim_v velocity coordinates.  Row order is
+ * (cell, node), both lexicographic with the first direction fastest.
+ */
+dg_status dg_node_coordinates(dg_handle h, int space, double* out);
+
+/*
+ * Replace E(x) of a DG_FIELD_PHASE_SPACE handle (host array, layout as
+ * dg_geometry.e_nodes).  Stream-ordered against work on ``stream``.
+ */
+dg_status dg_set_field(dg_handle h, const double* e_nodes, void* stream);
+
+/*
+ * dst = M^{-1} A(src): one application of the DG advection operator
+ * (Algorithm 2: gather, cell integrals, 2d face integrals with the upwind
+ * flux and the neighbour's trace across periodic faces, inverse mass,
+ * scatter).  src and dst are device vectors of n_dofs elements of the type
+ * given by prec (FP64 for DG_PREC_FP64 and DG_PREC_MIXED, FP32 for
+ * DG_PREC_FP32); they must not overlap (neighbours of src are read while dst
+ * is written).  Errors: INVALID_ARG (NULL, aliasing, misalignment, prec),
+ * CUDA.
+ */
+dg_status dg_apply(dg_handle h, const void* src, void* dst, int prec, void* stream);
+
+/*
+ * dst = L^T src with L = M^{-1} A, i.e. the transposed operator:
+ * L^T = M L(-a) M^{-1} -- the weak operator with the negated velocity (the
+ * downwind flux with respect to a) applied to the mass-scaled input.  Same
+ * arguments and errors as dg_apply.  (The paper has no adjoint; this is the
+ * exact transpose of dg_apply's operator.)
+ */
+dg_status dg_apply_adjoint(dg_handle h, const void* src, void* dst, int prec, void* stream);
+
+/*
+ * One fused stage s (0..4) of LSRK(5,4) in 2R form (Sec. 5.4; coefficients of
+ * Kennedy, Carpenter & Lewis 2000):
+ *     K = L(w_in)        (L^T if adjoint != 0)
+ *     w_out = u + a_s dt K    (s < 4)   or   w_out = u + b_4 dt K (s = 4)
+ *     u     = u + b_s dt K
+ * u is the FP64 state (updated in place); w_in/w_out are stage vectors of
+ * the type given by prec and must be distinct from each other and from u.
+ * Writing u + b_4 dt K at the last stage makes w_out the next step's first
+ * stage vector.
+ */
+dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
+                      double dt, int prec, int adjoint, void* stream);
+
+/*
+ * nsteps full LSRK(5,4) steps of size dt on the FP64 state u (in place),
+ * using the caller's stage vectors w0 and w1 (type by prec; contents on entry
+ * ignored, on exit unspecified).  Copies u into w0, then runs 5 fused stages
+ * per step, replayed from a CUDA graph that the handle captures on first use
+ * and re-captures when pointers, dt, prec or adjoint change.  If ``stream``
+ * is being captured by the caller, the kernels are enqueued directly.
+ * adjoint != 0 integrates with L^T (the adjoint step of a linear,
+ * autonomous problem: R(dt L)^T = R(dt L^T)).
+ */
+dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps,
+                     int prec, int adjoint, void* stream);
+
+/*
+ * Integrals of the FP64 vector u with the cell quadrature: out[0] = int u,
+ * out[1] = int u^2, out[2] = max |u_i| over the nodes.  Synchronises
+ * ``stream``; out is a host array of 3 doubles.
+ */
+dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream);
+
+/*
+ * Synchronise ``stream`` and report device-side errors latched since the
+ * last check: DG_ERR_NONFINITE if any kernel produced NaN or Inf.  Clears the
+ * latch.
+ */
+dg_status dg_check(dg_handle h, void* stream);
+
+/* Current launch configuration for ``prec`` (host struct). */
+dg_status dg_get_launch(dg_handle h, int prec, dg_launch* cfg);
+
+/* Override the launch configuration for ``prec`` (validated). */
+dg_status dg_set_launch(dg_handle h, int prec, const dg_launch* cfg);
+
+/*
+ * Autotuner: times the candidate launch configurations of dg_apply on the
+ * caller's buffers src/dst (prec as in dg_apply) and keeps the fastest for
+ * ``prec`` (and for the RK stages of the same prec).  dst is overwritten.
+ * Synchronises ``stream``.  best_ms (host, may be NULL) receives the time of
+ * the chosen configuration.
+ */
+dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* stream,
+                      double* best_ms);
+
+/*
+ * Batched execution of independent problems (constant velocity only).
+ * dg_batch_create groups ``count`` handles (each stays owned by the caller
+ * and must outlive the batch).  dg_batch_rk_step advances every member i by
+ * nsteps LSRK(5,4) steps of size dt[i] on its FP64 state u[i] with stage
+ * vectors w0[i], w1[i] (host arrays of device pointers); each stage of all
+ * members is one persistent launch that takes work tiles from a device
+ * queue, and each step is replayed from a CUDA graph.  prec: DG_PREC_FP64
+ * or DG_PREC_FP32 (FP32 stage vectors and sweeps, FP64 state).
+ */
+dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out);
+dg_status dg_batch_destroy(dg_batch b);
+dg_status dg_batch_rk_step(dg_batch b, double* const* u, void* const* w0, void* const* w1,
+                           const double* dt, int nsteps, int prec, void* stream);
+/* Number of work tiles and total DoFs of a batch (host outputs, may be NULL). */
+dg_status dg_batch_info(dg_batch b, long long* tiles, long long* n_dofs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

@@ -199,9 +199,15 @@ class Problem:
                 G = _axis_apply(T.B, G, m)
         return G
 
-    def cell_residual(self, u, cell):
-        """b = A(u) restricted to the test functions of ``cell`` (before M^{-1})."""
+    def cell_residual(self, u, cell, absolute=False):
+        """b = A(u) restricted to the test functions of ``cell`` (before M^{-1}).
+
+        absolute=True evaluates the same sums with the absolute value of every
+        factor and term (the "term scale" |A| |u| against which the rounding
+        error of a reduced-precision evaluation is measured)."""
         T, d = self.T, self.d
+        if absolute:
+            return self._cell_residual_abs(u, cell)
         Ue = self.cell_tensor(u, cell)
         # step 2: interpolate to quadrature points
         Uq = Ue
@@ -236,6 +242,57 @@ class Problem:
                 G = _axis_apply(ls[:, None], G, j)
                 b -= s * G
         return b
+
+    def _cell_residual_abs(self, u, cell):
+        T, d = self.T, self.d
+        aB, aBd = np.abs(T.B), np.abs(T.Bd)
+        Ue = np.abs(self.cell_tensor(u, cell))
+        Uq = Ue
+        for m in range(d):
+            Uq = _axis_apply(aB, Uq, m)
+        C = np.abs(self.contravariant_speed(cell, [T.zeta] * d))
+        W = _outer_weights([T.w] * d)
+        b = np.zeros_like(Ue)
+        for j in range(d):
+            G = W * self.detJ * C[..., j] * Uq
+            for m in range(d):
+                G = _axis_apply((aBd if m == j else aB).T, G, m)
+            b += G
+        for j in range(d):
+            for s in (1, -1):
+                ls, lo = (T.lp, T.lm) if s > 0 else (T.lm, T.lp)
+                own = self._face_trace_abs(Ue, j, np.abs(ls))
+                nbu = np.abs(self.cell_tensor(u, self.neighbour(cell, j, s)))
+                nb = self._face_trace_abs(nbu, j, np.abs(lo))
+                pts = [T.zeta] * d
+                pts[j] = np.array([float(s)])
+                cj = self.contravariant_speed(cell, pts)[..., j]
+                ustar = np.where(s * cj > 0, own, nb)
+                wf = [T.w] * d
+                wf[j] = np.array([1.0])
+                G = _outer_weights(wf) * self.detJ * np.abs(cj) * ustar
+                for m in range(d):
+                    if m != j:
+                        G = _axis_apply(aB.T, G, m)
+                G = _axis_apply(np.abs(ls)[:, None], G, j)
+                b += G
+        return b
+
+    def _face_trace_abs(self, U, j, l):
+        G = _axis_apply(l[None, :], U, j)
+        for m in range(self.d):
+            if m != j:
+                G = _axis_apply(np.abs(self.T.B), G, m)
+        return G
+
+    def apply_abs(self, u, cells=None):
+        """Term scale |M^{-1}| |A| |u| (collocation basis: M^{-1} diagonal)."""
+        assert self.basis == "gl"
+        u = np.asarray(u, dtype=np.float64)
+        sel = range(self.ncells) if cells is None else cells
+        out = [self.apply_mass_inverse(self._cell_residual_abs(u, e)).reshape(-1, order="F")
+               for e in sel]
+        return np.concatenate(out) if cells is None else np.stack(out)
 
     def mass_1d(self):
         T = self.T

@@ -1,0 +1,30 @@
+"""GB300-native (sm_103a) matrix-free DG advection in 2 to 6 dimensions.
+
+The method is that of hyper.deal (Munch, Kormann & Kronbichler, arXiv
+2002.08110): the upwind discontinuous Galerkin advection operator on the
+tensor product of a configuration-space and a velocity-space mesh, evaluated
+element by element with sum factorisation, inside low-storage Runge-Kutta
+time stepping.  The work runs in the CUDA library ``libdg.so`` behind the C
+ABI of ``include/dg.h``; this package is its thin Python binding plus the
+autograd wrapper of the adjoint.
+"""
+from ._lib import PREC_FP32, PREC_FP64, PREC_MIXED, DGError  # noqa: F401
+
+__all__ = ["DG", "DGError", "PREC_FP64", "PREC_FP32", "PREC_MIXED", "reference_nodes",
+           "build_library"]
+
+
+def build_library(verbose=False):
+    from .build import build
+    return build(verbose=verbose)
+
+
+def __getattr__(name):
+    # torch-dependent parts are imported lazily
+    if name in ("DG", "reference_nodes", "from_spec"):
+        from . import api
+        return getattr(api, name)
+    if name in ("MisfitGradient", "adjoint_gradient", "RKForward"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)

@@ -1,0 +1,188 @@
+"""Python binding of the DG advection library (argument marshalling only).
+
+``DG`` wraps one ``dg_handle``; vectors are torch CUDA tensors owned by the
+caller.  Every numerical step runs in ``libdg.so``; if the library is missing
+the import fails (no CPU fallback exists).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PREC_FP32, PREC_FP64, PREC_MIXED, DGError, check
+
+_WDTYPE = {PREC_FP64: torch.float64, PREC_FP32: torch.float32, PREC_MIXED: torch.float64}
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def reference_nodes(degree):
+    """Gauss-Legendre nodes and weights of the library (numpy, FP64)."""
+    lib = _lib.load()
+    x = np.zeros(degree + 1)
+    w = np.zeros(degree + 1)
+    check(lib.dg_reference_nodes(degree, x.ctypes.data_as(_lib.c_double_p),
+                                 w.ctypes.data_as(_lib.c_double_p)))
+    return x, w
+
+
+class DG:
+    """One advection problem on the tensor product of an x mesh and a v mesh.
+
+    field_kind 0: constant velocity ``a_const`` (d entries);
+    field_kind 1: a = (v[:dim_x], E(x)) with ``e_nodes`` of shape
+    (n_xcells, (k+1)^dim_x, dim_v) at the x nodes (``node_coordinates(0)``).
+    ``shear``: dim_x x dim_x matrix S of x = S y (None: identity).
+    """
+
+    def __init__(self, dim_x, dim_v, degree, cells_x, cells_v, x_lo, x_hi, v_lo, v_hi,
+                 field_kind=0, a_const=None, e_nodes=None, shear=None):
+        self.lib = _lib.load()
+        self.dim_x, self.dim_v, self.degree = int(dim_x), int(dim_v), int(degree)
+        g = _lib.Geometry()
+        for j in range(self.dim_x):
+            g.x_lo[j], g.x_hi[j] = float(x_lo[j]), float(x_hi[j])
+        for j in range(self.dim_v):
+            g.v_lo[j], g.v_hi[j] = float(v_lo[j]), float(v_hi[j])
+        if shear is not None:
+            S = np.asarray(shear, dtype=np.float64).reshape(self.dim_x, self.dim_x)
+            for i in range(self.dim_x):
+                for m in range(self.dim_x):
+                    g.shear_x[i * self.dim_x + m] = S[i, m]
+        g.field_kind = int(field_kind)
+        if a_const is not None:
+            for j, a in enumerate(a_const):
+                g.a_const[j] = float(a)
+        self._e_keep = None
+        if e_nodes is not None:
+            self._e_keep = np.ascontiguousarray(e_nodes, dtype=np.float64).reshape(-1)
+            g.e_nodes = self._e_keep.ctypes.data_as(_lib.c_double_p)
+        cx = (ctypes.c_int * self.dim_x)(*[int(c) for c in cells_x])
+        cv = (ctypes.c_int * self.dim_v)(*[int(c) for c in cells_v])
+        h = ctypes.c_void_p()
+        check(self.lib.dg_create(self.dim_x, self.dim_v, self.degree, cx, cv, ctypes.byref(g),
+                                 ctypes.byref(h)))
+        self.handle = h
+        info = _lib.Info()
+        check(self.lib.dg_info(self.handle, ctypes.byref(info)))
+        self.info = info
+        self.n_dofs = int(info.n_dofs)
+        self.n_cells = int(info.n_cells)
+        self.dofs_per_cell = int(info.dofs_per_cell)
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.dg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -----------------------------------------------------------------
+    def node_coordinates(self, space):
+        """x nodes (space 0, lattice coordinates) or v nodes (space 1)."""
+        if space == 0:
+            rows, cols = int(self.info.n_xcells) * (self.degree + 1) ** self.dim_x, self.dim_x
+        else:
+            rows, cols = int(self.info.n_vcells) * (self.degree + 1) ** self.dim_v, self.dim_v
+        out = np.zeros((rows, cols))
+        check(self.lib.dg_node_coordinates(self.handle, space, out.ctypes.data_as(_lib.c_double_p)))
+        return out
+
+    def set_field(self, e_nodes):
+        e = np.ascontiguousarray(e_nodes, dtype=np.float64).reshape(-1)
+        check(self.lib.dg_set_field(self.handle, e.ctypes.data_as(_lib.c_double_p), _stream()))
+
+    def empty(self, prec=PREC_FP64, device="cuda"):
+        return torch.empty(self.n_dofs, dtype=_WDTYPE[prec], device=device)
+
+    def _vec(self, t, prec, name):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != _WDTYPE[prec]:
+            raise TypeError(f"{name} must be {_WDTYPE[prec]} for precision {prec}")
+        if not t.is_contiguous() or t.numel() != self.n_dofs:
+            raise ValueError(f"{name} must be contiguous with {self.n_dofs} elements")
+        return _ptr(t)
+
+    # -- the operator ------------------------------------------------------------
+    def apply(self, src, dst=None, prec=PREC_FP64):
+        """dst = M^{-1} A(src)."""
+        if dst is None:
+            dst = torch.empty_like(src)
+        check(self.lib.dg_apply(self.handle, self._vec(src, prec, "src"),
+                                self._vec(dst, prec, "dst"), prec, _stream()))
+        return dst
+
+    def apply_adjoint(self, src, dst=None, prec=PREC_FP64):
+        """dst = L^T src (transpose of ``apply``)."""
+        if dst is None:
+            dst = torch.empty_like(src)
+        check(self.lib.dg_apply_adjoint(self.handle, self._vec(src, prec, "src"),
+                                        self._vec(dst, prec, "dst"), prec, _stream()))
+        return dst
+
+    def rk_stage(self, w_in, w_out, u, stage, dt, prec=PREC_FP64, adjoint=False):
+        check(self.lib.dg_rk_stage(self.handle, self._vec(w_in, prec, "w_in"),
+                                   self._vec(w_out, prec, "w_out"),
+                                   self._vec(u, PREC_FP64, "u"), int(stage), float(dt), prec,
+                                   int(bool(adjoint)), _stream()))
+
+    def rk_step(self, u, dt, nsteps=1, prec=PREC_FP64, adjoint=False, w0=None, w1=None):
+        """Advance the FP64 state u in place by nsteps LSRK(5,4) steps."""
+        if w0 is None:
+            w0 = self.empty(prec, u.device)
+        if w1 is None:
+            w1 = self.empty(prec, u.device)
+        check(self.lib.dg_rk_step(self.handle, self._vec(u, PREC_FP64, "u"),
+                                  self._vec(w0, prec, "w0"), self._vec(w1, prec, "w1"),
+                                  float(dt), int(nsteps), prec, int(bool(adjoint)), _stream()))
+        return u
+
+    def integrals(self, u):
+        """(int u, int u^2, max |u|) with the cell quadrature (synchronises)."""
+        out = np.zeros(3)
+        check(self.lib.dg_integrals(self.handle, self._vec(u, PREC_FP64, "u"),
+                                    out.ctypes.data_as(_lib.c_double_p), _stream()))
+        return tuple(float(x) for x in out)
+
+    def check(self):
+        """Synchronise and raise DGError(DG_ERR_NONFINITE) if a kernel saw NaN/Inf."""
+        check(self.lib.dg_check(self.handle, _stream()))
+
+    # -- launch configuration -----------------------------------------------------
+    def get_launch(self, prec):
+        c = _lib.Launch()
+        check(self.lib.dg_get_launch(self.handle, prec, ctypes.byref(c)))
+        return {"threads": c.threads, "cells_per_block": c.cells_per_block,
+                "order": list(c.order)[: self.dim_x + self.dim_v], "variant": c.variant}
+
+    def set_launch(self, prec, threads, cells_per_block, order=None, variant=0):
+        c = _lib.Launch()
+        c.threads, c.cells_per_block, c.variant = int(threads), int(cells_per_block), int(variant)
+        order = list(range(self.dim_x + self.dim_v)) if order is None else list(order)
+        for j in range(6):
+            c.order[j] = order[j] if j < len(order) else j
+        check(self.lib.dg_set_launch(self.handle, prec, ctypes.byref(c)))
+
+    def autotune(self, src, dst, prec):
+        best = ctypes.c_double()
+        check(self.lib.dg_autotune(self.handle, self._vec(src, prec, "src"),
+                                   self._vec(dst, prec, "dst"), prec, _stream(), ctypes.byref(best)))
+        return float(best.value)
+
+
+def from_spec(spec, e_nodes=None):
+    """Build a DG from a plain description (dict with the constructor's keys)."""
+    return DG(e_nodes=e_nodes, **spec)

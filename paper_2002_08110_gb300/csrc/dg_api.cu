@@ -1,0 +1,795 @@
+// C ABI of the DG advection library: handle set-up, validation, dispatch of
+// the cell kernels, fused LSRK stages replayed from CUDA graphs, integrals,
+// error latch and the launch-configuration autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+
+using namespace dg;
+
+namespace {
+
+thread_local std::string g_err;
+
+dg_status fail(dg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+dg_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(DG_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(DG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// LSRK(5,4), 2R form: Kennedy, Carpenter & Lewis (2000), the scheme cited in
+// Sec. 5.4 of the paper.
+const double kRkA[4] = {970286171893.0 / 4311952581923.0, 6584761158862.0 / 12103376702013.0,
+                        2251764453980.0 / 15575788980749.0, 26877169314380.0 / 34165994151039.0};
+const double kRkB[5] = {1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+                        -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+                        5198255086312.0 / 14908931495163.0};
+
+int combo_of(int prec) {
+  switch (prec) {
+    case DG_PREC_FP64: return kDDD;
+    case DG_PREC_FP32: return kFFF;
+    case DG_PREC_MIXED: return kFDD;
+    default: return -1;
+  }
+}
+
+size_t elem_bytes(int prec) { return prec == DG_PREC_FP32 ? 4 : 8; }
+size_t compute_bytes(int prec) { return prec == DG_PREC_FP64 ? 8 : 4; }
+
+int ipow(int b, int e) {
+  int r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cached <= 0)
+      cached = 1;
+  }
+  return cached;
+}
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+dg_status check_vec(const void* ptr, const char* name) {
+  if (ptr == nullptr) return fail(DG_ERR_INVALID_ARG, "%s is NULL", name);
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0)
+    return fail(DG_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  return DG_OK;
+}
+
+KParams base_params(const dg_ctx* h, int prec) {
+  KParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.dx = h->dx;
+  p.dv = h->dv;
+  for (int j = 0; j < kMaxDim; ++j) {
+    p.ncell[j] = j < h->d ? h->ncell[j] : 1;
+    p.cstride[j] = j < h->d ? h->cstride[j] : 1;
+  }
+  p.ncells = h->ncells;
+  p.ncx = h->ncx;
+  const LaunchCfg& c = h->cfg[prec];
+  for (int j = 0; j < kMaxDim; ++j) p.order[j] = c.order[j];
+  p.cells_per_block = c.cells_per_block;
+  const bool f = prec != DG_PREC_FP64;
+  p.cx_tab = f ? static_cast<const void*>(h->cx_d32) : static_cast<const void*>(h->cx_d64);
+  p.cv_tab = f ? static_cast<const void*>(h->cv_d32) : static_cast<const void*>(h->cv_d64);
+  p.scratch = h->scratch;
+  p.err = h->err_d;
+  p.t64 = h->tables.t64;
+  p.t32 = h->tables.t32;
+  return p;
+}
+
+// Scratch needed by the global-memory variant of the generic kernel.
+dg_status ensure_scratch(dg_ctx* h, int prec) {
+  const int combo = combo_of(prec);
+  if (generic_smem_bytes(h->d, h->n, combo, 1) != 0) return DG_OK;
+  const int blocks = generic_grid_blocks(h->d, h->n, h->ncells, 1, h->cfg[prec].threads);
+  const size_t need = static_cast<size_t>(blocks) * generic_scratch_elems(h->d, h->n) *
+                      compute_bytes(prec);
+  if (h->scratch_bytes >= need) return DG_OK;
+  // captured graphs hold the old scratch pointer
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) {
+      cudaGraphExecDestroy(h->gexec[i]);
+      h->gexec[i] = nullptr;
+    }
+  if (h->scratch) cudaFree(h->scratch);
+  h->scratch = nullptr;
+  h->scratch_bytes = 0;
+  cudaError_t e = cudaMalloc(&h->scratch, need);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+  h->scratch_bytes = need;
+  return DG_OK;
+}
+
+cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
+                        cudaStream_t s) {
+  if (cfg.variant == 1 && h->d == 6 && h->n == 4) {
+    cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  switch (h->d) {
+    case 2: return launch_cell_d2(h->n, combo, p, cfg, s);
+    case 3: return launch_cell_d3(h->n, combo, p, cfg, s);
+    case 4: return launch_cell_d4(h->n, combo, p, cfg, s);
+    case 5: return launch_cell_d5(h->n, combo, p, cfg, s);
+    case 6: return launch_cell_d6(h->n, combo, p, cfg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+dg_status do_apply(dg_handle h, const void* src, void* dst, int prec, void* stream, int adjoint) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  const int combo = combo_of(prec);
+  if (combo < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  dg_status st;
+  if ((st = check_vec(src, "src")) != DG_OK) return st;
+  if ((st = check_vec(dst, "dst")) != DG_OK) return st;
+  const size_t bytes = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
+  if (ranges_overlap(src, dst, bytes)) return fail(DG_ERR_INVALID_ARG, "src and dst overlap");
+  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  KParams p = base_params(h, prec);
+  p.src = src;
+  p.dst = dst;
+  p.mode = 0;
+  p.adjoint = adjoint;
+  cudaError_t e = launch_cell(h, combo, p, h->cfg[prec], static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cell kernel launch");
+  return DG_OK;
+}
+
+dg_status enqueue_stage(dg_handle h, const void* w_in, void* w_out, double* u, int stage, double dt,
+                        int prec, int adjoint, cudaStream_t s) {
+  KParams p = base_params(h, prec);
+  p.src = w_in;
+  p.dst = w_out;
+  p.u = u;
+  p.mode = 1;
+  p.adjoint = adjoint;
+  p.last_stage = stage == 4;
+  p.a_dt = stage < 4 ? kRkA[stage] * dt : kRkB[4] * dt;
+  p.b_dt = kRkB[stage] * dt;
+  cudaError_t e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s);
+  if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
+  return DG_OK;
+}
+
+// One LSRK step: stage s reads w[s % 2 ^ parity] and writes the other buffer.
+dg_status enqueue_step(dg_handle h, double* u, void* w0, void* w1, double dt, int prec,
+                       int adjoint, int parity, cudaStream_t s) {
+  void* w[2] = {parity ? w1 : w0, parity ? w0 : w1};
+  for (int st = 0; st < 5; ++st) {
+    dg_status r = enqueue_stage(h, w[st % 2], w[(st + 1) % 2], u, st, dt, prec, adjoint, s);
+    if (r != DG_OK) return r;
+  }
+  return DG_OK;
+}
+
+void default_cfg(dg_ctx* h) {
+  for (int prec = 0; prec < 3; ++prec) {
+    LaunchCfg& c = h->cfg[prec];
+    c.threads = 256;
+    c.variant = 0;
+    for (int j = 0; j < kMaxDim; ++j) c.order[j] = j;
+    int cpb = std::max(1, 2048 / h->npc);
+    while (cpb > 1 && generic_smem_bytes(h->d, h->n, combo_of(prec), cpb) == 0) --cpb;
+    c.cells_per_block = cpb;
+    if (h->npc >= 1024) c.threads = 512;
+    if (h->d == 6 && h->n == 4 && prec != DG_PREC_FP64) c.variant = 1;
+  }
+}
+
+dg_status validate_cfg(const dg_ctx* h, int prec, const LaunchCfg& c) {
+  if (c.threads < 32 || c.threads > 512 || c.threads % 32 != 0)
+    return fail(DG_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512]");
+  if (c.cells_per_block < 1 || c.cells_per_block > 4096)
+    return fail(DG_ERR_INVALID_ARG, "cells_per_block out of range");
+  if (c.variant < 0 || c.variant > 1) return fail(DG_ERR_INVALID_ARG, "unknown variant");
+  bool seen[kMaxDim] = {false};
+  for (int j = 0; j < h->d; ++j) {
+    if (c.order[j] < 0 || c.order[j] >= h->d || seen[c.order[j]])
+      return fail(DG_ERR_INVALID_ARG, "order must be a permutation of 0..d-1");
+    seen[c.order[j]] = true;
+  }
+  (void)prec;
+  return DG_OK;
+}
+
+void free_ctx(dg_ctx* h) {
+  if (!h) return;
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  cudaFree(h->cx_d64);
+  cudaFree(h->cx_d32);
+  cudaFree(h->cv_d64);
+  cudaFree(h->cv_d32);
+  cudaFree(h->err_d);
+  cudaFree(h->scratch);
+  cudaFree(h->partial);
+  delete h;
+}
+
+template <typename T>
+cudaError_t upload(const std::vector<double>& src, T** dst) {
+  std::vector<T> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = static_cast<T>(src[i]);
+  cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, tmp.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Contravariant speeds c = J^{-1} a at the x and v nodes (Sec. 3: only the
+// low-dimensional parts are stored and combined on the fly, Sec. 6).
+dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
+  const int n = h->n, dx = h->dx, dv = h->dv;
+  h->cx_host.assign(static_cast<size_t>(h->ncv) * h->nqv * dx, 0.0);
+  h->cv_host.assign(static_cast<size_t>(h->ncx) * h->nqx * dv, 0.0);
+  const double* z = h->tables.zeta;
+  for (long long cv = 0; cv < h->ncv; ++cv)
+    for (int q = 0; q < h->nqv; ++q) {
+      double a[3] = {0, 0, 0};
+      if (h->field_kind == DG_FIELD_CONSTANT) {
+        for (int i = 0; i < dx; ++i) a[i] = h->a_const[i];
+      } else {
+        long long c = cv;
+        int qq = q;
+        double v[3] = {0, 0, 0};
+        for (int m = 0; m < dv; ++m) {
+          const int j = dx + m;
+          const long long cm = c % h->ncell[j];
+          c /= h->ncell[j];
+          v[m] = h->lo[j] + h->h[j] * (static_cast<double>(cm) + (z[qq % n] + 1.0) / 2.0);
+          qq /= n;
+        }
+        for (int i = 0; i < dx; ++i) a[i] = v[i];
+      }
+      for (int i = 0; i < dx; ++i) {
+        double s = 0.0;
+        for (int m = 0; m < dx; ++m) s += h->Sinv[i * dx + m] * a[m];
+        h->cx_host[(cv * h->nqv + q) * dx + i] = 2.0 / h->h[i] * s;
+      }
+    }
+  for (long long cx = 0; cx < h->ncx; ++cx)
+    for (int q = 0; q < h->nqx; ++q)
+      for (int i = 0; i < dv; ++i) {
+        double a = 0.0;
+        if (h->field_kind == DG_FIELD_CONSTANT)
+          a = h->a_const[dx + i];
+        else if (e_nodes)
+          a = e_nodes[(cx * h->nqx + q) * dv + i];
+        if (!std::isfinite(a)) return fail(DG_ERR_INVALID_ARG, "E is not finite");
+        h->cv_host[(cx * h->nqx + q) * dv + i] = 2.0 / h->h[dx + i] * a;
+      }
+  double sum = 0.0;
+  for (int j = 0; j < h->d; ++j) {
+    double mx = 0.0;
+    if (j < dx) {
+      for (size_t r = j; r < h->cx_host.size(); r += dx) mx = std::max(mx, std::fabs(h->cx_host[r]));
+    } else {
+      for (size_t r = j - dx; r < h->cv_host.size(); r += dv)
+        mx = std::max(mx, std::fabs(h->cv_host[r]));
+    }
+    sum += 0.5 * mx;  // |c_j| / 2 = |a_j| / h_j (without shear)
+  }
+  h->speed_sum = sum;
+  return DG_OK;
+}
+
+}  // namespace
+
+namespace dg {
+
+size_t generic_smem_bytes(int d, int n, int combo, int cells_per_block) {
+  const size_t tb = combo == kDDD ? 8 : 4;
+  const size_t b = static_cast<size_t>(ipow(n, d)) * tb * 2 * cells_per_block;
+  return b <= 200 * 1024 ? b : 0;
+}
+
+long long generic_scratch_elems(int d, int n) { return ipow(n, d); }
+
+int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int threads) {
+  (void)d;
+  (void)n;
+  (void)threads;
+  long long want = 2LL * sm_count();
+  const long long chunks = (ncells + cells_per_block - 1) / cells_per_block;
+  return static_cast<int>(std::max<long long>(1, std::min(want, chunks)));
+}
+
+}  // namespace dg
+
+extern "C" {
+
+int dg_version(void) { return DG_ABI_VERSION; }
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+dg_status dg_reference_nodes(int degree, double* nodes, double* weights) {
+  if (nodes == nullptr) return fail(DG_ERR_INVALID_ARG, "nodes is NULL");
+  if (degree < 0 || degree > 5) return fail(DG_ERR_INVALID_ARG, "degree must be in [0, 5]");
+  double x[kMaxN], w[kMaxN];
+  gauss_legendre(degree + 1, x, w);
+  for (int i = 0; i <= degree; ++i) {
+    nodes[i] = x[i];
+    if (weights) weights[i] = w[i];
+  }
+  return DG_OK;
+}
+
+dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const int* cells_v,
+                    const dg_geometry* geometry, dg_handle* out) {
+  if (out == nullptr) return fail(DG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (cells_x == nullptr || cells_v == nullptr || geometry == nullptr)
+    return fail(DG_ERR_INVALID_ARG, "cells_x, cells_v and geometry must not be NULL");
+  if (dim_x < 1 || dim_x > 3 || dim_v < 1 || dim_v > 3)
+    return fail(DG_ERR_UNSUPPORTED, "dim_x and dim_v must be in [1, 3] (got %d, %d)", dim_x, dim_v);
+  if (dim_x + dim_v > 6) return fail(DG_ERR_UNSUPPORTED, "d = dim_x + dim_v must be <= 6");
+  if (degree < 1 || degree > 5) return fail(DG_ERR_UNSUPPORTED, "degree must be in [1, 5]");
+  const dg_geometry& g = *geometry;
+  if (g.field_kind != DG_FIELD_CONSTANT && g.field_kind != DG_FIELD_PHASE_SPACE)
+    return fail(DG_ERR_INVALID_ARG, "unknown field_kind %d", g.field_kind);
+  if (g.field_kind == DG_FIELD_PHASE_SPACE && dim_v < dim_x)
+    return fail(DG_ERR_UNSUPPORTED, "phase-space field needs dim_v >= dim_x");
+
+  dg_ctx* h = new (std::nothrow) dg_ctx();
+  if (!h) return fail(DG_ERR_OOM, "host allocation failed");
+  h->dx = dim_x;
+  h->dv = dim_v;
+  h->d = dim_x + dim_v;
+  h->k = degree;
+  h->n = degree + 1;
+  h->field_kind = g.field_kind;
+  long long ncx = 1, ncv = 1;
+  for (int j = 0; j < h->d; ++j) {
+    const int c = j < dim_x ? cells_x[j] : cells_v[j - dim_x];
+    if (c < 1 || c > (1 << 24)) {
+      delete h;
+      return fail(DG_ERR_INVALID_ARG, "cells per direction must be in [1, 2^24]");
+    }
+    h->ncell[j] = c;
+    const double lo = j < dim_x ? g.x_lo[j] : g.v_lo[j - dim_x];
+    const double hi = j < dim_x ? g.x_hi[j] : g.v_hi[j - dim_x];
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) {
+      delete h;
+      return fail(DG_ERR_INVALID_ARG, "box of direction %d is empty or not finite", j);
+    }
+    h->lo[j] = lo;
+    h->h[j] = (hi - lo) / c;
+    if (j < dim_x) ncx *= c; else ncv *= c;
+  }
+  h->ncx = ncx;
+  h->ncv = ncv;
+  h->ncells = ncx * ncv;
+  long long st = 1;
+  for (int j = 0; j < h->d; ++j) {
+    h->cstride[j] = st;
+    st *= h->ncell[j];
+  }
+  h->npc = ipow(h->n, h->d);
+  h->nqx = ipow(h->n, dim_x);
+  h->nqv = ipow(h->n, dim_v);
+  if (h->ncells > (1LL << 40) / h->npc) {
+    delete h;
+    return fail(DG_ERR_INVALID_ARG, "mesh too large");
+  }
+  h->n_dofs = h->ncells * h->npc;
+  // shear S (row-major), identity if all zero
+  bool zero = true;
+  for (int i = 0; i < 9; ++i) zero = zero && g.shear_x[i] == 0.0;
+  for (int i = 0; i < dim_x; ++i)
+    for (int m = 0; m < dim_x; ++m)
+      h->S[i * dim_x + m] = zero ? (i == m ? 1.0 : 0.0) : g.shear_x[i * dim_x + m];
+  {
+    // invert the dx-by-dx shear by Gauss-Jordan elimination with pivoting
+    double a[3][6];
+    const int m = dim_x;
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c < 2 * m; ++c) a[i][c] = c < m ? h->S[i * m + c] : (c - m == i ? 1.0 : 0.0);
+    double det = 1.0;
+    for (int c = 0; c < m; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < m; ++r)
+        if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+      if (!(std::fabs(a[piv][c]) > 1e-300) || !std::isfinite(a[piv][c])) {
+        delete h;
+        return fail(DG_ERR_INVALID_ARG, "shear matrix is singular or not finite");
+      }
+      if (piv != c) {
+        for (int k2 = 0; k2 < 2 * m; ++k2) std::swap(a[c][k2], a[piv][k2]);
+        det = -det;
+      }
+      det *= a[c][c];
+      const double inv = 1.0 / a[c][c];
+      for (int k2 = 0; k2 < 2 * m; ++k2) a[c][k2] *= inv;
+      for (int r = 0; r < m; ++r) {
+        if (r == c) continue;
+        const double f = a[r][c];
+        for (int k2 = 0; k2 < 2 * m; ++k2) a[r][k2] -= f * a[c][k2];
+      }
+    }
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c < m; ++c) h->Sinv[i * m + c] = a[i][m + c];
+    double dj = std::fabs(det);
+    for (int j = 0; j < h->d; ++j) dj *= h->h[j] / 2.0;
+    h->detJ = dj;
+  }
+  for (int j = 0; j < h->d; ++j) {
+    h->a_const[j] = g.a_const[j];
+    if (!std::isfinite(g.a_const[j])) {
+      delete h;
+      return fail(DG_ERR_INVALID_ARG, "a_const is not finite");
+    }
+  }
+  build_tables(h->n, &h->tables);
+  dg_status s = compute_speeds(h, g.e_nodes);
+  if (s != DG_OK) {
+    delete h;
+    return s;
+  }
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess ||
+      (e = upload(h->cx_host, &h->cx_d64)) != cudaSuccess ||
+      (e = upload(h->cx_host, &h->cx_d32)) != cudaSuccess ||
+      (e = upload(h->cv_host, &h->cv_d64)) != cudaSuccess ||
+      (e = upload(h->cv_host, &h->cv_d32)) != cudaSuccess ||
+      (e = cudaMalloc(&h->err_d, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(h->err_d, 0, sizeof(int))) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    free_ctx(h);
+    return cuda_fail(e, "dg_create");
+  }
+  h->partial_blocks = std::min<long long>(4 * sm_count(), std::max<long long>(1, h->n_dofs / 256));
+  if ((e = cudaMalloc(&h->partial, sizeof(double) * 3 * h->partial_blocks)) != cudaSuccess) {
+    free_ctx(h);
+    return cuda_fail(e, "dg_create");
+  }
+  default_cfg(h);
+  *out = h;
+  return DG_OK;
+}
+
+dg_status dg_destroy(dg_handle h) {
+  free_ctx(h);
+  return DG_OK;
+}
+
+dg_status dg_info(dg_handle h, dg_info_t* info) {
+  if (h == nullptr || info == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n_dofs = h->n_dofs;
+  info->n_cells = h->ncells;
+  info->n_xcells = h->ncx;
+  info->n_vcells = h->ncv;
+  info->dofs_per_cell = h->npc;
+  info->dim_x = h->dx;
+  info->dim_v = h->dv;
+  info->degree = h->k;
+  info->speed_sum = h->speed_sum;
+  info->det_jacobian = h->detJ;
+  for (int j = 0; j < h->d; ++j) info->h[j] = h->h[j];
+  return DG_OK;
+}
+
+dg_status dg_node_coordinates(dg_handle h, int space, double* out) {
+  if (h == nullptr || out == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  if (space != 0 && space != 1) return fail(DG_ERR_INVALID_ARG, "space must be 0 (x) or 1 (v)");
+  const int dims = space == 0 ? h->dx : h->dv;
+  const int off = space == 0 ? 0 : h->dx;
+  const long long nc = space == 0 ? h->ncx : h->ncv;
+  const int nq = space == 0 ? h->nqx : h->nqv;
+  const double* z = h->tables.zeta;
+  for (long long c = 0; c < nc; ++c)
+    for (int q = 0; q < nq; ++q) {
+      long long cc = c;
+      int qq = q;
+      for (int m = 0; m < dims; ++m) {
+        const int j = off + m;
+        const long long cm = cc % h->ncell[j];
+        cc /= h->ncell[j];
+        out[(c * nq + q) * dims + m] =
+            h->lo[j] + h->h[j] * (static_cast<double>(cm) + (z[qq % h->n] + 1.0) / 2.0);
+        qq /= h->n;
+      }
+    }
+  return DG_OK;
+}
+
+dg_status dg_set_field(dg_handle h, const double* e_nodes, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->field_kind != DG_FIELD_PHASE_SPACE)
+    return fail(DG_ERR_INVALID_ARG, "dg_set_field needs a phase-space handle");
+  dg_status s = compute_speeds(h, e_nodes);
+  if (s != DG_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<float> f(h->cv_host.begin(), h->cv_host.end());
+  cudaError_t e;
+  // synchronous with respect to the host buffers (pageable copies)
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess ||
+      (e = cudaMemcpy(h->cv_d64, h->cv_host.data(), h->cv_host.size() * 8, cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(h->cv_d32, f.data(), f.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "dg_set_field");
+  // graphs captured with the old field stay valid (tables are read at run time)
+  return DG_OK;
+}
+
+dg_status dg_apply(dg_handle h, const void* src, void* dst, int prec, void* stream) {
+  return do_apply(h, src, dst, prec, stream, 0);
+}
+
+dg_status dg_apply_adjoint(dg_handle h, const void* src, void* dst, int prec, void* stream) {
+  return do_apply(h, src, dst, prec, stream, 1);
+}
+
+dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int stage, double dt,
+                      int prec, int adjoint, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  if (stage < 0 || stage > 4) return fail(DG_ERR_INVALID_ARG, "stage must be in [0, 4]");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  dg_status st;
+  if ((st = check_vec(w_in, "w_in")) != DG_OK || (st = check_vec(w_out, "w_out")) != DG_OK ||
+      (st = check_vec(u, "u")) != DG_OK)
+    return st;
+  const size_t wb = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
+  const size_t ub = static_cast<size_t>(h->n_dofs) * 8;
+  if (ranges_overlap(w_in, w_out, wb) || ranges_overlap(w_in, u, std::max(wb, ub)) ||
+      ranges_overlap(w_out, u, std::max(wb, ub)))
+    return fail(DG_ERR_INVALID_ARG, "w_in, w_out and u must not overlap");
+  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  return enqueue_stage(h, w_in, w_out, u, stage, dt, prec, adjoint ? 1 : 0,
+                       static_cast<cudaStream_t>(stream));
+}
+
+dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
+                     int adjoint, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  dg_status st;
+  if ((st = check_vec(u, "u")) != DG_OK || (st = check_vec(w0, "w0")) != DG_OK ||
+      (st = check_vec(w1, "w1")) != DG_OK)
+    return st;
+  const size_t wb = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
+  const size_t ub = static_cast<size_t>(h->n_dofs) * 8;
+  if (ranges_overlap(w0, w1, wb) || ranges_overlap(w0, u, std::max(wb, ub)) ||
+      ranges_overlap(w1, u, std::max(wb, ub)))
+    return fail(DG_ERR_INVALID_ARG, "u, w0 and w1 must not overlap");
+  if (nsteps == 0) return DG_OK;
+  adjoint = adjoint ? 1 : 0;
+  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_convert(u, w0, prec == DG_PREC_FP32, h->n_dofs, s);
+  if (e != cudaSuccess) return cuda_fail(e, "stage-vector initialisation");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return cuda_fail(e, "capture query");
+  if (cap != cudaStreamCaptureStatusNone) {
+    for (int i = 0; i < nsteps; ++i)
+      if ((st = enqueue_step(h, u, w0, w1, dt, prec, adjoint, i % 2, s)) != DG_OK) return st;
+    return DG_OK;
+  }
+  for (int parity = 0; parity < 2 && parity < nsteps; ++parity) {
+    dg_ctx::GraphKey key;
+    key.u = u;
+    key.w0 = w0;
+    key.w1 = w1;
+    key.dt = dt;
+    key.prec = prec;
+    key.adjoint = adjoint;
+    key.parity = parity;
+    if (h->gexec[parity] && h->gkey[parity] == key) continue;
+    if (h->gexec[parity]) {
+      cudaGraphExecDestroy(h->gexec[parity]);
+      h->gexec[parity] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      return cuda_fail(e, "graph capture");
+    st = enqueue_step(h, u, w0, w1, dt, prec, adjoint, parity, h->capture_stream);
+    e = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (st != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&h->gexec[parity], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->gexec[parity] = nullptr;
+      return cuda_fail(e, "graph instantiation");
+    }
+    h->gkey[parity] = key;
+  }
+  for (int i = 0; i < nsteps; ++i)
+    if ((e = cudaGraphLaunch(h->gexec[i % 2], s)) != cudaSuccess) return cuda_fail(e, "graph launch");
+  return DG_OK;
+}
+
+dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream) {
+  if (h == nullptr || out == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  dg_status st;
+  if ((st = check_vec(u, "u")) != DG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  KParams p = base_params(h, DG_PREC_FP64);
+  cudaError_t e = launch_integrals(p, h->n, u, h->partial, h->partial_blocks, h->detJ, s);
+  if (e != cudaSuccess) return cuda_fail(e, "integrals kernel");
+  std::vector<double> host(3 * h->partial_blocks);
+  if ((e = cudaMemcpyAsync(host.data(), h->partial, host.size() * 8, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "integrals readback");
+  double m = 0.0, l = 0.0, x = 0.0;
+  for (int b = 0; b < h->partial_blocks; ++b) {
+    m += host[3 * b];
+    l += host[3 * b + 1];
+    x = std::max(x, host[3 * b + 2]);
+  }
+  out[0] = m;
+  out[1] = l;
+  out[2] = x;
+  return DG_OK;
+}
+
+dg_status dg_check(dg_handle h, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int flag = 0;
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess ||
+      (e = cudaMemcpy(&flag, h->err_d, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemset(h->err_d, 0, sizeof(int))) != cudaSuccess)
+    return cuda_fail(e, "dg_check");
+  if (flag) return fail(DG_ERR_NONFINITE, "a kernel produced a non-finite value");
+  return DG_OK;
+}
+
+dg_status dg_get_launch(dg_handle h, int prec, dg_launch* cfg) {
+  if (h == nullptr || cfg == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  const LaunchCfg& c = h->cfg[prec];
+  cfg->threads = c.threads;
+  cfg->cells_per_block = c.cells_per_block;
+  for (int j = 0; j < 6; ++j) cfg->order[j] = c.order[j];
+  cfg->variant = c.variant;
+  return DG_OK;
+}
+
+dg_status dg_set_launch(dg_handle h, int prec, const dg_launch* cfg) {
+  if (h == nullptr || cfg == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
+  if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  LaunchCfg c;
+  c.threads = cfg->threads;
+  c.cells_per_block = cfg->cells_per_block;
+  for (int j = 0; j < 6; ++j) c.order[j] = j < h->d ? cfg->order[j] : j;
+  c.variant = cfg->variant;
+  dg_status s = validate_cfg(h, prec, c);
+  if (s != DG_OK) return s;
+  h->cfg[prec] = c;
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) {
+      cudaGraphExecDestroy(h->gexec[i]);
+      h->gexec[i] = nullptr;
+    }
+  return DG_OK;
+}
+
+dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* stream,
+                      double* best_ms) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  const int combo = combo_of(prec);
+  if (combo < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  dg_status st;
+  if ((st = check_vec(src, "src")) != DG_OK || (st = check_vec(dst, "dst")) != DG_OK) return st;
+  const size_t bytes = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
+  if (ranges_overlap(src, dst, bytes)) return fail(DG_ERR_INVALID_ARG, "src and dst overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // candidate set: threads x cells-per-block x sweep order x variant
+  std::vector<LaunchCfg> cands;
+  const int threads_c[] = {128, 256, 512};
+  std::vector<int> cpbs;
+  for (int c = 1; c <= 4096; c *= 2)
+    if (static_cast<long long>(c) * h->npc <= 8192 &&
+        (generic_smem_bytes(h->d, h->n, combo, c) != 0 || c == 1))
+      cpbs.push_back(c);
+  for (int variant = 0; variant < 2; ++variant) {
+    if (variant == 1 && !(h->d == 6 && h->n == 4 && prec != DG_PREC_FP64)) continue;
+    for (int rev = 0; rev < 2; ++rev)
+      for (int t : threads_c)
+        for (int c : cpbs) {
+          LaunchCfg cfg;
+          cfg.threads = t;
+          cfg.cells_per_block = c;
+          cfg.variant = variant;
+          for (int j = 0; j < kMaxDim; ++j) cfg.order[j] = j;
+          if (rev)
+            for (int j = 0; j < h->d; ++j) cfg.order[j] = h->d - 1 - j;
+          if (variant == 1 && (c != 1 || rev)) continue;
+          cands.push_back(cfg);
+        }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const LaunchCfg saved = h->cfg[prec];
+  double best = 1e300;
+  LaunchCfg best_cfg = saved;
+  for (const LaunchCfg& cfg : cands) {
+    h->cfg[prec] = cfg;
+    if ((st = ensure_scratch(h, prec)) != DG_OK) break;
+    KParams p = base_params(h, prec);
+    p.src = src;
+    p.dst = dst;
+    cudaError_t e = launch_cell(h, combo, p, cfg, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const int reps = 3;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) {
+      KParams q = base_params(h, prec);
+      q.src = src;
+      q.dst = dst;
+      launch_cell(h, combo, q, cfg, s);
+    }
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / reps < best) {
+      best = ms / reps;
+      best_cfg = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->cfg[prec] = best_cfg;
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) {
+      cudaGraphExecDestroy(h->gexec[i]);
+      h->gexec[i] = nullptr;
+    }
+  if (best_ms) *best_ms = best;
+  if (st != DG_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  return DG_OK;
+}
+
+}  // extern "C"

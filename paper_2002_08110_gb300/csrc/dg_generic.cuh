@@ -1,0 +1,242 @@
+// Generic element-centric DG advection cell kernel (any d <= 6, n <= 6).
+//
+// One block processes ``cells_per_block`` cells (Algorithm 1: the loop over
+// cell pairs (c_x, c_v) is the grid).  Per cell (Algorithm 2):
+//   1. gather the n^d values of the input into shared memory;
+//   2./3. for each direction j, every line of n values along j is contracted
+//      with the collocated 1D operator (cell term of direction j, both faces
+//      normal to j with the upwind flux, inverse mass; see Tab1D).  The
+//      neighbour's trace is needed on inflow faces only; it is computed from
+//      the neighbour's line read from global memory (periodic wrap, tensor
+//      product cell index);
+//   4. the inverse mass is already folded into the 1D operator;
+//   5. scatter (or the fused LSRK stage update).
+// Directions are processed one after another with a block barrier between
+// them; within a direction the lines are disjoint, so the accumulation into
+// the per-cell residual needs no atomics (the element-centric loop writes
+// every DoF exactly once, Sec. 2.6).
+//
+// Large cells (6D with n >= 5 in FP64, n = 6 in FP32) do not fit in shared
+// memory: then the block reads the cell from global memory and accumulates in
+// a per-block slab of scratch memory, looping over cells persistently.
+#pragma once
+
+#include "dg_internal.h"
+
+namespace dg {
+
+template <int B, int E>
+struct Pow { static constexpr int v = B * Pow<B, E - 1>::v; };
+template <int B>
+struct Pow<B, 0> { static constexpr int v = 1; };
+
+template <typename T>
+__device__ __forceinline__ const Tab1D<T>& tab(const KParams& p);
+template <>
+__device__ __forceinline__ const Tab1D<double>& tab<double>(const KParams& p) { return p.t64; }
+template <>
+__device__ __forceinline__ const Tab1D<float>& tab<float>(const KParams& p) { return p.t32; }
+
+// Product of the 1D weights (or inverse weights) over the d digits of node q.
+template <int D, int N, typename TC>
+__device__ __forceinline__ TC node_weight(const TC* w1, int q) {
+  TC r = TC(1);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    r *= w1[q % N];
+    q /= N;
+  }
+  return r;
+}
+
+// Contravariant speed c_j of the line whose first node is ``base`` (q_j = 0)
+// in ``cell``.  x directions depend on the v node only, v directions on the x
+// node only (phase-space structure, Sec. 3 and Sec. 6).
+template <typename TC>
+__device__ __forceinline__ TC line_speed(const KParams& p, int j, long long cell, int base,
+                                         int nqx, int nqv) {
+  if (j < p.dx) {
+    const long long cv = cell / p.ncx;
+    const int qv = base / nqx;
+    return static_cast<const TC*>(p.cx_tab)[(cv * nqv + qv) * p.dx + j];
+  }
+  const long long cx = cell % p.ncx;
+  const int qx = base % nqx;
+  return static_cast<const TC*>(p.cv_tab)[(cx * nqx + qx) * p.dv + (j - p.dx)];
+}
+
+__device__ __forceinline__ long long neighbour_cell(const KParams& p, long long cell, int j, int s) {
+  const long long st = p.cstride[j];
+  const int nj = p.ncell[j];
+  const int cj = static_cast<int>((cell / st) % nj);
+  int c2 = cj + s;
+  if (c2 < 0) c2 += nj;
+  if (c2 >= nj) c2 -= nj;
+  return cell + static_cast<long long>(c2 - cj) * st;
+}
+
+template <int D, int N, typename TC, typename TIN, typename TW, bool SMEM>
+__global__ void __launch_bounds__(512) k_generic(const KParams p) {
+  constexpr int NP = Pow<N, D>::v;
+  constexpr int NL = NP / N;
+  const Tab1D<TC>& T = tab<TC>(p);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
+  int nqx = 1, nqv = 1;
+  for (int m = 0; m < p.dx; ++m) nqx *= N;
+  for (int m = 0; m < p.dv; ++m) nqv *= N;
+  const int cpb = SMEM ? p.cells_per_block : 1;
+  int bad = 0;
+
+  for (long long cell0 = static_cast<long long>(blockIdx.x) * cpb; cell0 < p.ncells;
+       cell0 += static_cast<long long>(gridDim.x) * cpb) {
+    const int nc = static_cast<int>(min(static_cast<long long>(cpb), p.ncells - cell0));
+    TC* su = reinterpret_cast<TC*>(smem_raw);
+    TC* sr = SMEM ? su + cpb * NP : static_cast<TC*>(p.scratch) + static_cast<long long>(blockIdx.x) * NP;
+
+    // step 1: gather (and the M^{-1} scaling of the adjoint's input)
+    for (int i = threadIdx.x; i < nc * NP; i += blockDim.x) {
+      if (SMEM) {
+        TC v = static_cast<TC>(src[cell0 * NP + i]);
+        if (p.adjoint) v *= node_weight<D, N, TC>(T.winv, i % NP);
+        su[i] = v;
+      }
+      sr[i] = TC(0);
+    }
+    __syncthreads();
+
+    // steps 2-4, direction by direction
+    for (int jj = 0; jj < D; ++jj) {
+      const int j = p.order[jj];
+      int sj = 1;
+      for (int m = 0; m < j; ++m) sj *= N;
+      for (int it = threadIdx.x; it < nc * NL; it += blockDim.x) {
+        const int c = it / NL;
+        const int l = it - c * NL;
+        const int base = (l % sj) + (l / sj) * sj * N;
+        const long long cell = cell0 + c;
+        TC cj = line_speed<TC>(p, j, cell, base, nqx, nqv);
+        if (p.adjoint) cj = -cj;
+        if (cj == TC(0)) continue;
+        const bool pos = cj > TC(0);
+        TC uu[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          if (SMEM) {
+            uu[q] = su[c * NP + base + q * sj];
+          } else {
+            TC v = static_cast<TC>(src[cell * NP + base + q * sj]);
+            if (p.adjoint) v *= node_weight<D, N, TC>(T.winv, base + q * sj);
+            uu[q] = v;
+          }
+        }
+        // trace of the upwind neighbour's line at the shared face
+        const long long nb = neighbour_cell(p, cell, j, pos ? -1 : 1);
+        const TIN* ns = src + nb * NP + base;
+        TC t = TC(0);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          TC v = static_cast<TC>(ns[q * sj]);
+          if (p.adjoint) v *= node_weight<D, N, TC>(T.winv, base + q * sj);
+          t += (pos ? T.lp[q] : T.lm[q]) * v;
+        }
+        TC* r = sr + c * NP + base;
+        if (pos) {
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            TC acc = T.Lm[q] * t;
+#pragma unroll
+            for (int s = 0; s < N; ++s) acc += T.Gp[q * N + s] * uu[s];
+            r[q * sj] += cj * acc;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            TC acc = -T.Lp[q] * t;
+#pragma unroll
+            for (int s = 0; s < N; ++s) acc += T.Gn[q * N + s] * uu[s];
+            r[q * sj] += cj * acc;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+    // step 5: scatter / fused LSRK stage update
+    for (int i = threadIdx.x; i < nc * NP; i += blockDim.x) {
+      TC K = sr[i];
+      if (p.adjoint) K *= node_weight<D, N, TC>(T.w, i % NP);
+      if (!isfinite(K)) bad = 1;
+      const long long g = cell0 * NP + i;
+      if (p.mode == 0) {
+        static_cast<TW*>(p.dst)[g] = static_cast<TW>(K);
+      } else {
+        const double uo = p.u[g];
+        const double kd = static_cast<double>(K);
+        const double un = uo + p.b_dt * kd;
+        p.u[g] = un;
+        static_cast<TW*>(p.dst)[g] = static_cast<TW>(p.last_stage ? un : uo + p.a_dt * kd);
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(p.err, 1);
+}
+
+constexpr size_t kSmemLimit = 200 * 1024;
+
+template <int D, int N, typename TC>
+constexpr bool fits_smem() {
+  return static_cast<size_t>(Pow<N, D>::v) * sizeof(TC) * 2 <= kSmemLimit;
+}
+
+template <int D, int N, typename TC, typename TIN, typename TW>
+cudaError_t launch_generic(KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
+  constexpr int NP = Pow<N, D>::v;
+  if constexpr (fits_smem<D, N, TC>()) {
+    int cpb = cfg.cells_per_block < 1 ? 1 : cfg.cells_per_block;
+    size_t smem = static_cast<size_t>(cpb) * NP * sizeof(TC) * 2;
+    while (smem > kSmemLimit && cpb > 1) {
+      --cpb;
+      smem = static_cast<size_t>(cpb) * NP * sizeof(TC) * 2;
+    }
+    p.cells_per_block = cpb;
+    auto kern = k_generic<D, N, TC, TIN, TW, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const long long grid = (p.ncells + cpb - 1) / cpb;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<static_cast<unsigned>(grid), cfg.threads, smem, s>>>(p);
+  } else {
+    if (p.scratch == nullptr) return cudaErrorInvalidValue;
+    p.cells_per_block = 1;
+    const int blocks = generic_grid_blocks(D, N, p.ncells, 1, cfg.threads);
+    k_generic<D, N, TC, TIN, TW, false><<<blocks, cfg.threads, 0, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <int D, int N>
+cudaError_t launch_generic_combo(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
+  switch (combo) {
+    case kDDD: return launch_generic<D, N, double, double, double>(p, cfg, s);
+    case kFFF: return launch_generic<D, N, float, float, float>(p, cfg, s);
+    case kFDD: return launch_generic<D, N, float, double, double>(p, cfg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int D>
+cudaError_t launch_generic_dim(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
+  switch (n) {
+    case 2: return launch_generic_combo<D, 2>(combo, p, cfg, s);
+    case 3: return launch_generic_combo<D, 3>(combo, p, cfg, s);
+    case 4: return launch_generic_combo<D, 4>(combo, p, cfg, s);
+    case 5: return launch_generic_combo<D, 5>(combo, p, cfg, s);
+    case 6: return launch_generic_combo<D, 6>(combo, p, cfg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,150 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int kMaxDim = 6;
+constexpr int kMaxN = 6;
+
+// 1D tables of the collocated Gauss-Legendre element, precomputed in FP64 on
+// the host (Sec. 2.3, Sec. 2.5).  With nodal basis phi_i at the GL points
+// zeta_i, weights w_i, D[p][i] = phi_i'(zeta_p), and face values
+// l_i(+-1) = phi_i(+-1), the collocated weak form of one direction j of
+// Algorithm 2 (cell term, both faces, inverse mass) reduces, for a line of
+// n values u along j with contravariant speed c (constant along the line),
+// to
+//   c > 0:  du_q = c ( sum_p Gp[q][p] u_p + Lm[q] t ),  t = sum_p lp[p] u^-_p
+//   c < 0:  du_q = c ( sum_p Gn[q][p] u_p - Lp[q] t ),  t = sum_p lm[p] u^+_p
+// with u^- / u^+ the line of the upwind neighbour below / above, and
+//   Dt[q][p] = D[p][q] w_p / w_q,  Lp = lp / w,  Lm = lm / w,
+//   Gp = Dt - Lp lp^T,  Gn = Dt + Lm lm^T.
+// (The transverse weights and |J| of the cell and face integrals cancel
+// against the diagonal mass matrix.)
+template <typename T>
+struct Tab1D {
+  T Gp[kMaxN * kMaxN];
+  T Gn[kMaxN * kMaxN];
+  T Lp[kMaxN];
+  T Lm[kMaxN];
+  T lp[kMaxN];
+  T lm[kMaxN];
+  T w[kMaxN];
+  T winv[kMaxN];
+};
+
+// Host-side FP64 tables (dg_tables.cpp).
+struct HostTables {
+  int n;
+  double zeta[kMaxN], w[kMaxN];
+  double D[kMaxN][kMaxN];  // D[p][i] = phi_i'(zeta_p)
+  double lp[kMaxN], lm[kMaxN];
+  Tab1D<double> t64;
+  Tab1D<float> t32;
+};
+bool gauss_legendre(int n, double* x, double* w);
+void build_tables(int n, HostTables* t);
+
+// Kernel parameters (passed by value; lives in the constant bank).
+struct KParams {
+  int dx, dv;
+  int ncell[kMaxDim];
+  long long cstride[kMaxDim];
+  long long ncells;
+  long long ncx;            // cells of the x mesh (cell = c_x + ncx * c_v)
+  int order[kMaxDim];       // sweep order of the directions
+  int cells_per_block;
+  const void* cx_tab;       // contravariant speeds of the x directions at v nodes: [ncv][n^dv][dx]
+  const void* cv_tab;       // contravariant speeds of the v directions at x nodes: [ncx][n^dx][dv]
+  const void* src;          // operator input (apply) / stage vector w_in
+  void* dst;                // operator output (apply) / stage vector w_out
+  double* u;                // FP64 state (stage mode)
+  void* scratch;            // per-block accumulators (large cells)
+  int* err;                 // device error latch
+  int mode;                 // 0 = apply, 1 = LSRK stage
+  int adjoint;              // 1: L^T = M L(-a) M^{-1}
+  int last_stage;           // stage mode: w_out = u_new
+  double a_dt, b_dt;        // stage mode coefficients (a_s dt, b_s dt)
+  Tab1D<double> t64;
+  Tab1D<float> t32;
+};
+
+// Precision combinations of the cell kernels: compute type / input / output.
+enum Combo { kDDD = 0, kFFF = 1, kFDD = 2, kNumCombo = 3 };
+
+struct LaunchCfg {
+  int threads = 256;
+  int cells_per_block = 1;
+  int order[kMaxDim] = {0, 1, 2, 3, 4, 5};
+  int variant = 0;
+};
+
+// Launch entry points, one per dimension (dg_inst_d*.cu).  Return a CUDA
+// error code (cudaSuccess on success).
+cudaError_t launch_cell_d2(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_cell_d3(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_cell_d4(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_cell_d5(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_cell_d6(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+
+// Bytes of dynamic shared memory of the generic kernel, or 0 if the cell does
+// not fit (then the global-memory variant with per-block scratch is used).
+size_t generic_smem_bytes(int d, int n, int combo, int cells_per_block);
+// Scratch elements (of the compute type) per block for the global variant.
+long long generic_scratch_elems(int d, int n);
+int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int threads);
+
+// Specialised 6D, n = 4, FP32-sweep kernel (dg_cell6d.cu).  Returns
+// cudaErrorNotSupported if the configuration is not covered.
+cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+
+// Small kernels (dg_misc.cu).
+cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s);
+cudaError_t launch_integrals(const KParams& p, int n, const double* u, double* partial,
+                             int blocks, double detJ, cudaStream_t s);
+
+}  // namespace dg
+
+// The handle.
+struct dg_ctx {
+  int dx = 0, dv = 0, d = 0, k = 0, n = 0;
+  int ncell[dg::kMaxDim] = {0};
+  long long cstride[dg::kMaxDim] = {0};
+  long long ncells = 0, ncx = 0, ncv = 0, n_dofs = 0;
+  int npc = 0;            // n^d
+  int nqx = 0, nqv = 0;   // n^dx, n^dv
+  double h[dg::kMaxDim] = {0};
+  double lo[dg::kMaxDim] = {0};
+  double S[9] = {0}, Sinv[9] = {0};
+  double detJ = 0.0;
+  int field_kind = 0;
+  double a_const[dg::kMaxDim] = {0};
+  double speed_sum = 0.0;
+  int device = 0;
+  dg::HostTables tables;
+  std::vector<double> cx_host, cv_host;   // contravariant speeds (FP64)
+  double* cx_d64 = nullptr; float* cx_d32 = nullptr;
+  double* cv_d64 = nullptr; float* cv_d32 = nullptr;
+  int* err_d = nullptr;
+  void* scratch = nullptr; size_t scratch_bytes = 0;
+  double* partial = nullptr; int partial_blocks = 0;
+  cudaStream_t capture_stream = nullptr;
+  dg::LaunchCfg cfg[3];
+  // cached RK graphs
+  struct GraphKey {
+    const void* u = nullptr; const void* w0 = nullptr; const void* w1 = nullptr;
+    double dt = 0.0; int prec = -1; int adjoint = -1; int parity = -1;
+    bool operator==(const GraphKey& o) const {
+      return u == o.u && w0 == o.w0 && w1 == o.w1 && dt == o.dt && prec == o.prec &&
+             adjoint == o.adjoint && parity == o.parity;
+    }
+  };
+  GraphKey gkey[2];
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};

@@ -1,0 +1,108 @@
+// Host-side 1D tables of the collocated Gauss-Legendre element, in FP64.
+//
+// Gauss-Legendre points (Sec. 2.5 of arXiv 2002.08110) by Newton's method on
+// the three-term recurrence of the Legendre polynomials, weights
+// w = 2 / ((1 - x^2) P_n'(x)^2); Lagrange derivatives by the barycentric
+// formula D[p][i] = (lambda_i / lambda_p) / (x_p - x_i) (p != i), with the
+// diagonal making each row sum to zero (derivative of a constant).
+#include <cmath>
+#include <cstring>
+
+#include "dg_internal.h"
+
+namespace dg {
+
+static void legendre_eval(int n, double z, double* pn, double* dpn) {
+  double p0 = 1.0, p1 = z;
+  if (n == 0) { *pn = 1.0; *dpn = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  *pn = p1;
+  // P_n'(z) = n (z P_n - P_{n-1}) / (z^2 - 1)
+  *dpn = n * (z * p1 - p0) / (z * z - 1.0);
+}
+
+bool gauss_legendre(int n, double* x, double* w) {
+  if (n < 1 || n > kMaxN) return false;
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double pn = 0.0, dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      legendre_eval(n, z, &pn, &dp);
+      const double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    legendre_eval(n, z, &pn, &dp);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  return true;
+}
+
+void build_tables(int n, HostTables* t) {
+  std::memset(t, 0, sizeof(*t));
+  t->n = n;
+  gauss_legendre(n, t->zeta, t->w);
+  const double* x = t->zeta;
+  double lam[kMaxN];
+  for (int i = 0; i < n; ++i) {
+    double prod = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != i) prod *= (x[i] - x[m]);
+    lam[i] = 1.0 / prod;
+  }
+  for (int p = 0; p < n; ++p) {
+    double diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      if (i == p) continue;
+      t->D[p][i] = (lam[i] / lam[p]) / (x[p] - x[i]);
+      diag -= t->D[p][i];
+    }
+    t->D[p][p] = diag;
+  }
+  for (int i = 0; i < n; ++i) {
+    double a = 1.0, b = 1.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == i) continue;
+      a *= (1.0 - x[m]) / (x[i] - x[m]);
+      b *= (-1.0 - x[m]) / (x[i] - x[m]);
+    }
+    t->lp[i] = a;
+    t->lm[i] = b;
+  }
+  Tab1D<double>& d = t->t64;
+  for (int q = 0; q < n; ++q) {
+    d.lp[q] = t->lp[q];
+    d.lm[q] = t->lm[q];
+    d.w[q] = t->w[q];
+    d.winv[q] = 1.0 / t->w[q];
+    d.Lp[q] = t->lp[q] / t->w[q];
+    d.Lm[q] = t->lm[q] / t->w[q];
+  }
+  for (int q = 0; q < n; ++q)
+    for (int p = 0; p < n; ++p) {
+      const double dt = t->D[p][q] * t->w[p] / t->w[q];
+      d.Gp[q * n + p] = dt - d.Lp[q] * t->lp[p];
+      d.Gn[q * n + p] = dt + d.Lm[q] * t->lm[p];
+    }
+  Tab1D<float>& f = t->t32;
+  for (int i = 0; i < kMaxN * kMaxN; ++i) {
+    f.Gp[i] = static_cast<float>(d.Gp[i]);
+    f.Gn[i] = static_cast<float>(d.Gn[i]);
+  }
+  for (int i = 0; i < kMaxN; ++i) {
+    f.Lp[i] = static_cast<float>(d.Lp[i]);
+    f.Lm[i] = static_cast<float>(d.Lm[i]);
+    f.lp[i] = static_cast<float>(d.lp[i]);
+    f.lm[i] = static_cast<float>(d.lm[i]);
+    f.w[i] = static_cast<float>(d.w[i]);
+    f.winv[i] = static_cast<float>(d.winv[i]);
+  }
+}
+
+}  // namespace dg

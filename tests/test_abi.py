@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads, exports every declared symbol, and rejects
+bad arguments on the host (no GPU needed)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import __graft_entry__ as entry
+from paper_2002_08110_gb300 import _lib
+
+
+@pytest.fixture(scope="module")
+def lib():
+    entry.build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _lib.declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_reference_nodes(lib):
+    assert lib.dg_version() == 1
+    for k in range(6):
+        x = np.zeros(k + 1)
+        w = np.zeros(k + 1)
+        assert lib.dg_reference_nodes(k, x.ctypes.data_as(_lib.c_double_p),
+                                      w.ctypes.data_as(_lib.c_double_p)) == 0
+        xr, wr = np.polynomial.legendre.leggauss(k + 1)
+        assert np.allclose(x, xr, atol=1e-15) and np.allclose(w, wr, atol=1e-15)
+    assert lib.dg_reference_nodes(6, x.ctypes.data_as(_lib.c_double_p), None) == 1
+    assert lib.dg_reference_nodes(2, None, None) == 1
+
+
+def _create(lib, dx, dv, k, cx, cv, kind=0):
+    g = _lib.Geometry()
+    for j in range(3):
+        g.x_lo[j], g.x_hi[j], g.v_lo[j], g.v_hi[j] = 0.0, 1.0, 0.0, 1.0
+    g.field_kind = kind
+    h = ctypes.c_void_p()
+    cxa = (ctypes.c_int * max(1, len(cx)))(*cx)
+    cva = (ctypes.c_int * max(1, len(cv)))(*cv)
+    st = lib.dg_create(dx, dv, k, cxa, cva, ctypes.byref(g), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("dx,dv,k,status", [
+    (0, 1, 3, 2), (1, 0, 3, 2), (4, 1, 3, 2), (3, 4, 3, 2), (1, 1, 0, 2), (1, 1, 6, 2),
+])
+def test_create_rejects_unsupported(lib, dx, dv, k, status):
+    st, h = _create(lib, dx, dv, k, [2] * max(dx, 1), [2] * max(dv, 1))
+    assert st == status
+    assert h.value is None
+    assert len(lib.dg_last_error()) > 0
+
+
+def test_create_rejects_bad_arguments(lib):
+    st, _ = _create(lib, 1, 1, 2, [0], [2])
+    assert st == 1
+    st, _ = _create(lib, 2, 1, 2, [2, 2], [2], kind=1)   # phase space needs dv >= dx
+    assert st == 2
+    st, _ = _create(lib, 1, 1, 2, [2], [2], kind=7)
+    assert st == 1
+    g = _lib.Geometry()
+    h = ctypes.c_void_p()
+    c = (ctypes.c_int * 1)(2)
+    assert lib.dg_create(1, 1, 2, c, c, ctypes.byref(g), ctypes.byref(h)) == 1  # empty box
+    assert lib.dg_create(1, 1, 2, None, c, ctypes.byref(g), ctypes.byref(h)) == 1
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.dg_apply(None, None, None, 0, None) == 1
+    assert lib.dg_apply_adjoint(None, None, None, 0, None) == 1
+    assert lib.dg_rk_step(None, None, None, None, 0.1, 1, 0, 0, None) == 1
+    assert lib.dg_rk_stage(None, None, None, None, 0, 0.1, 0, 0, None) == 1
+    assert lib.dg_check(None, None) == 1
+    assert lib.dg_destroy(None) == 0

@@ -180,6 +180,15 @@ def e_function(w: Workload):
     return E
 
 
+def dg_kwargs(w: Workload):
+    """Constructor arguments of the library's problem handle (plain data)."""
+    return dict(dim_x=w.dx, dim_v=w.dv, degree=w.k, cells_x=tuple(w.cells_x),
+                cells_v=tuple(w.cells_v), x_lo=tuple(w.x_lo), x_hi=tuple(w.x_hi),
+                v_lo=tuple(w.v_lo), v_hi=tuple(w.v_hi), field_kind=w.field_kind,
+                a_const=tuple(w.a_const) if w.field_kind == 0 else None,
+                shear=None if w.shear is None else np.array(w.shear).reshape(w.dx, w.dx))
+
+
 # -- the five problems --------------------------------------------------------
 def _sin2pi(y):
     return np.sin(TWO_PI * y)
