@@ -1,0 +1,429 @@
+"""Benchmark of the DG advection hot path on the 6D workload.
+
+One step = one fused LSRK(5,4) stage on the 6D, degree-3 problem
+(8^3 x 8^3 cells, 1,073,741,824 DoFs): the operator application M^{-1} A(w)
+(FP32 sweeps and fluxes on the FP32 stage vector w) fused with the FP64
+state update u += b_s dt K and the next stage vector.  The metric is DoFs
+per second (GDoF/s) of such operator applications; the line also reports
+the stand-alone operator applications in FP32, FP32-with-FP64-vectors and
+FP64, each against the HBM roofline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the whole
+workload (the method needs no exchange between independent problems;
+"replicas only"), and the value is the total over ranks / max time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "6D DG advection GDoF/s per operator apply (FP32 vs FP64), % of HBM roofline"
+UNIT = "GDoF/s"
+# algorithmic bytes per DoF (each vector element read or written once)
+BYTES_PER_DOF = {
+    "stage_fp32w_fp64u": 4 + 8 + 8 + 4,   # read w_in, read+write u, write w_out
+    "stage_fp64": 8 + 8 + 8 + 8,
+    "apply_fp32": 4 + 4,
+    "apply_fp32_fp64io": 8 + 8,
+    "apply_fp64": 8 + 8,
+}
+KERNEL_SOURCES = ["dg_cell6d.cu", "dg_generic.cuh", "dg_internal.h"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cells", type=int, default=8, help="cells per direction (default 8)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-reps", type=int, default=2)
+    ap.add_argument("--step-kind", default="stage",
+                    choices=["stage", "apply_fp32", "apply_fp32_fp64io", "apply_fp64"],
+                    help="what one timed step is (default: the fused LSRK stage)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        p = os.path.join(ROOT, "paper_2002_08110_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    """Max over ranks (identity for one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample_worker(cells_per_dim, n_cells, reps, q):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    import numpy as np
+    import workloads as W
+    from oracle import lsrk
+    from oracle.dg import PhaseSpaceField, Problem
+    w = W.config_6d(cells=cells_per_dim)
+    p = Problem(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
+                PhaseSpaceField(w.dx, w.dv, W.e_function(w)))
+    rng = np.random.default_rng(0)
+    cells = sorted(int(c) for c in rng.choice(p.ncells, size=n_cells, replace=False))
+
+    class Cells:
+        """The 6D initial state on the sampled cells and their neighbours only,
+        materialised before the timed region."""
+        shape = (p.n_dofs,)
+
+        def __init__(self):
+            self.cache = {}
+            for e in cells:
+                for c in [e] + [p.neighbour(e, j, s) for j in range(p.d) for s in (1, -1)]:
+                    if c not in self.cache:
+                        self.cache[c] = p.interpolate(lambda yx, v: _u0(w, yx, v), [c])
+
+        def __getitem__(self, s):
+            return self.cache[s.start // p.dofs_per_cell]
+
+    u = Cells()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        K = np.stack([p.apply_mass_inverse(p.cell_residual(u, e)).reshape(-1, order="F")
+                      for e in cells])
+        # the stage update of the sampled cells (LSRK stage 0)
+        for i, e in enumerate(cells):
+            uo = u[slice(e * p.dofs_per_cell, (e + 1) * p.dofs_per_cell)]
+            _ = uo + lsrk.B[0] * 1e-3 * K[i], uo + lsrk.A[0] * 1e-3 * K[i]
+        times.append(time.perf_counter() - t0)
+    q.put({"seconds": times, "dofs": n_cells * p.dofs_per_cell, "cells": n_cells})
+
+
+def _u0(w, yx, v):
+    import numpy as np
+    f = w.u0_factors
+    out = np.ones(yx.shape[:-1])
+    for j in range(w.dx):
+        out = out * f[j](yx[..., j])
+    for j in range(w.dv):
+        out = out * f[w.dx + j](v[..., j])
+    return out
+
+
+def oracle_sample(cells_per_dim, n_cells, reps):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_oracle_sample_worker, args=(cells_per_dim, n_cells, reps, q))
+    pr.start()
+    res = q.get()
+    pr.join()
+    return res
+
+
+def reference_arm(args, world, rank):
+    """--impl reference: the FP64 oracle, as it stands, on host cores."""
+    if rank != 0:
+        return
+    n_cells = 40
+    res = oracle_sample(args.cells, n_cells, args.warmup + args.steps)
+    ts = res["seconds"][args.warmup:]
+    total = sum(ts)
+    value = res["dofs"] * len(ts) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"6d_k3_{args.cells}^6", "stage": "LSRK(5,4) stage 0",
+                   "sample": f"{n_cells} cells x 4096 DoFs per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_cells} random cells of the 6D mesh per step, FP64 numpy"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2002_08110_gb300 import DG, PREC_FP32, PREC_FP64, PREC_MIXED, reference_nodes
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.config_6d(cells=args.cells)
+    zeta, _ = reference_nodes(w.k)
+    E = W.e_table(w, zeta)
+    dg = DG(e_nodes=E, **W.dg_kwargs(w))
+    n = dg.n_dofs
+    dt, _ = W.time_step(w)
+    u0 = W.separable_state(w, zeta, xp=torch, device=dev)
+    u = u0.clone()
+    w0 = u0.float()
+    w1 = torch.empty_like(w0)
+    hbm_peak, peak_kind = peaks()
+
+    # ---- the timed step: one fused LSRK stage (FP32 sweeps, FP32 w, FP64 u)
+    kind = args.step_kind
+    if kind == "apply_fp64" or kind == "apply_fp32_fp64io":
+        d64 = torch.empty_like(u)
+
+    def stage(i):
+        if kind == "stage":
+            a, b = (w0, w1) if i % 2 == 0 else (w1, w0)
+            dg.rk_stage(a, b, u, i % 5, dt, prec=PREC_FP32)
+        elif kind == "apply_fp32":
+            dg.apply(w0, w1, prec=PREC_FP32)
+        elif kind == "apply_fp32_fp64io":
+            dg.apply(u, d64, prec=PREC_MIXED)
+        else:
+            dg.apply(u, d64, prec=PREC_FP64)
+
+    for i in range(args.warmup):
+        stage(i)
+    dg.check()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    barrier(world)
+    ev[0].record(stream)
+    for i in range(args.steps):
+        stage(args.warmup + i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dg.check()
+    per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = reduce_max(total_ms, world)
+    barrier(world)
+    value = world * n * args.steps / (total_ms * 1e-3) / 1e9
+    avg_launch = sum(per_launch) / len(per_launch)
+    bpd = BYTES_PER_DOF["stage_fp32w_fp64u" if kind == "stage" else kind]
+    achieved = bpd * n / (avg_launch * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": recorded_traffic(kind),
+            "peak_kind": peak_kind, "bytes_per_dof": bpd,
+            "kernel": "fused LSRK stage (cell kernel, stage mode)" if kind == "stage" else "cell kernel, operator application"}
+
+    # ---- stand-alone operator applications
+    variants = {}
+    if not args.no_variants:
+        def time_fn(fn, reps, warm=1):
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        src32 = w0
+        dst32 = torch.empty_like(src32)
+        ms = time_fn(lambda: dg.apply(src32, dst32, prec=PREC_FP32), 10)
+        variants["apply_fp32"] = ms
+        src64 = u
+        dst64 = torch.empty_like(u)
+        ms = time_fn(lambda: dg.apply(src64, dst64, prec=PREC_MIXED), 10)
+        variants["apply_fp32_fp64io"] = ms
+        ms = time_fn(lambda: dg.apply(src64, dst64, prec=PREC_FP64), args.fp64_reps, warm=1)
+        variants["apply_fp64"] = ms
+        del dst32
+        dg.check()
+        for k in list(variants):
+            ms = variants[k]
+            gbs = BYTES_PER_DOF[k] * n / (ms * 1e-3) / 1e9
+            variants[k] = {"ms": ms, "GDoF/s": n / (ms * 1e-3) / 1e9, "GB/s": gbs,
+                           "frac_hbm": gbs / hbm_peak}
+        del dst64
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        steps_e2e = 3
+        h_w = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        h_u = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        h_w.copy_(w0)
+        h_u.copy_(u)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps_e2e):
+            w0.copy_(h_w, non_blocking=True)
+            u.copy_(h_u, non_blocking=True)
+            dg.rk_stage(w0, w1, u, i % 5, dt, prec=PREC_FP32)
+            h_u.copy_(u, non_blocking=True)
+            h_w.copy_(w1, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps_e2e
+        ms = reduce_max(ms, world)
+        e2e = {"value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": n * (4 + 8), "d2h_bytes_per_step": n * (8 + 4),
+               "ms_per_step": ms}
+        del h_w, h_u
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        res = oracle_sample(args.cells, 1000, 1)
+        sec = min(res["seconds"])
+        cpu = {"value": res["dofs"] / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{res['cells']} random cells of the 6D mesh, one fused stage, FP64 numpy"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": w.name, "dofs": n, "cells": w.ncells, "degree": w.k,
+                       "step": "fused LSRK(5,4) stage: FP32 sweeps, FP32 stage vector, FP64 state",
+                       "l2": "inputs larger than L2 (vectors 4.3-8.6 GB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "step_kind": kind,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "variants": variants,
+            "launch": dg.get_launch(PREC_FP32),
+        }
+        print(json.dumps(line), flush=True)
+    dg.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

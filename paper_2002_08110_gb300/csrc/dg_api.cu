@@ -72,9 +72,13 @@ int sm_count() {
   return cached;
 }
 
-bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-  return x < y + bytes && y < x + bytes;
+  return x < y + bbytes && y < x + abytes;
+}
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  return ranges_overlap(a, bytes, b, bytes);
 }
 
 dg_status check_vec(const void* ptr, const char* name) {
@@ -564,8 +568,8 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
     return st;
   const size_t wb = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
   const size_t ub = static_cast<size_t>(h->n_dofs) * 8;
-  if (ranges_overlap(w_in, w_out, wb) || ranges_overlap(w_in, u, std::max(wb, ub)) ||
-      ranges_overlap(w_out, u, std::max(wb, ub)))
+  if (ranges_overlap(w_in, w_out, wb) || ranges_overlap(w_in, wb, u, ub) ||
+      ranges_overlap(w_out, wb, u, ub))
     return fail(DG_ERR_INVALID_ARG, "w_in, w_out and u must not overlap");
   if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
   return enqueue_stage(h, w_in, w_out, u, stage, dt, prec, adjoint ? 1 : 0,
@@ -584,8 +588,8 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
     return st;
   const size_t wb = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
   const size_t ub = static_cast<size_t>(h->n_dofs) * 8;
-  if (ranges_overlap(w0, w1, wb) || ranges_overlap(w0, u, std::max(wb, ub)) ||
-      ranges_overlap(w1, u, std::max(wb, ub)))
+  if (ranges_overlap(w0, w1, wb) || ranges_overlap(w0, wb, u, ub) ||
+      ranges_overlap(w1, wb, u, ub))
     return fail(DG_ERR_INVALID_ARG, "u, w0 and w1 must not overlap");
   if (nsteps == 0) return DG_OK;
   adjoint = adjoint ? 1 : 0;
@@ -736,7 +740,8 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
           for (int j = 0; j < kMaxDim; ++j) cfg.order[j] = j;
           if (rev)
             for (int j = 0; j < h->d; ++j) cfg.order[j] = h->d - 1 - j;
-          if (variant == 1 && (c != 1 || rev)) continue;
+          // the specialised kernel fixes 64 threads per cell and its sweep order
+          if (variant == 1 && (c > 2 || rev || t != 128)) continue;
           cands.push_back(cfg);
         }
   }

@@ -21,6 +21,7 @@
 // a per-block slab of scratch memory, looping over cells persistently.
 #pragma once
 
+#include "dg_convert.cuh"
 #include "dg_internal.h"
 
 namespace dg {
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
     // step 1: gather (and the M^{-1} scaling of the adjoint's input)
     for (int i = threadIdx.x; i < nc * NP; i += blockDim.x) {
       if (SMEM) {
-        TC v = static_cast<TC>(src[cell0 * NP + i]);
+        TC v = cvt<TC>(src[cell0 * NP + i]);
         if (p.adjoint) v *= node_weight<D, N, TC>(T.winv, i % NP);
         su[i] = v;
       }
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
           if (SMEM) {
             uu[q] = su[c * NP + base + q * sj];
           } else {
-            TC v = static_cast<TC>(src[cell * NP + base + q * sj]);
+            TC v = cvt<TC>(src[cell * NP + base + q * sj]);
             if (p.adjoint) v *= node_weight<D, N, TC>(T.winv, base + q * sj);
             uu[q] = v;
           }
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
         TC t = TC(0);
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-          TC v = static_cast<TC>(ns[q * sj]);
+          TC v = cvt<TC>(ns[q * sj]);
           if (p.adjoint) v *= node_weight<D, N, TC>(T.winv, base + q * sj);
           t += (pos ? T.lp[q] : T.lm[q]) * v;
         }
@@ -169,13 +170,23 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
       if (!isfinite(K)) bad = 1;
       const long long g = cell0 * NP + i;
       if (p.mode == 0) {
-        static_cast<TW*>(p.dst)[g] = static_cast<TW>(K);
+        static_cast<TW*>(p.dst)[g] = cvt<TW>(K);
       } else {
         const double uo = p.u[g];
-        const double kd = static_cast<double>(K);
-        const double un = uo + p.b_dt * kd;
-        p.u[g] = un;
-        static_cast<TW*>(p.dst)[g] = static_cast<TW>(p.last_stage ? un : uo + p.a_dt * kd);
+        if constexpr (sizeof(TC) == 8) {
+          const double un = uo + p.b_dt * K;
+          p.u[g] = un;
+          static_cast<TW*>(p.dst)[g] = cvt<TW>(p.last_stage ? un : uo + p.a_dt * K);
+        } else {
+          // FP32 sweeps: one FP64 add for the state, the rest in FP32 / integer
+          const double un = uo + f32_to_f64(static_cast<float>(p.b_dt) * K);
+          p.u[g] = un;
+          if constexpr (sizeof(TW) == 4)
+            static_cast<TW*>(p.dst)[g] =
+                p.last_stage ? f64_to_f32(un) : fmaf(static_cast<float>(p.a_dt), K, f64_to_f32(uo));
+          else
+            static_cast<TW*>(p.dst)[g] = p.last_stage ? un : uo + p.a_dt * f32_to_f64(K);
+        }
       }
     }
     __syncthreads();

@@ -69,3 +69,96 @@ def test_apply_parity(case, kind, prec):
         scale = np.linalg.norm(p.apply_abs(u))
         assert np.linalg.norm(out - ref) <= TOL32 * scale
     dg.close()
+
+
+ADJ_CASES = [(1, 1, 3, (5, 4)), (2, 2, 2, (3, 2, 2, 3)), (2, 3, 3, (2, 1, 2, 1, 2)),
+             (3, 3, 2, (2, 1, 2, 2, 1, 2)), (3, 3, 1, (2, 2, 1, 1, 2, 2))]
+
+
+@pytest.mark.parametrize("case", ADJ_CASES, ids=lambda c: f"{c[0]}x{c[1]}v_k{c[2]}")
+@pytest.mark.parametrize("kind", ["const", "phase"])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_adjoint_parity(case, kind, prec):
+    """dg_apply_adjoint == the oracle's transposed operator (dense cell blocks)."""
+    dx, dv, k, cells = case
+    shear = None if dx == 1 else np.eye(dx) + 0.1 * np.eye(dx, k=1)
+    dg, p = random_problem(dx, dv, k, cells, kind, seed=3, shear=shear)
+    y, out = _run(dg, p, prec, adjoint=True, seed=4)
+    ref = p.apply_adjoint(y)
+    if prec == 0:
+        assert np.linalg.norm(out - ref) <= TOL64 * np.linalg.norm(ref)
+    else:
+        # term scale of the transpose: |L^T| |y| <= sum of the transposed |blocks|
+        L = p.assemble()
+        scale = np.linalg.norm(abs(L).T @ np.abs(y))
+        assert np.linalg.norm(out - ref) <= 4 * TOL32 * scale
+    dg.close()
+
+
+def _dot_identity(dg, p, prec, seed):
+    """<y, L x> (oracle) against <L^T y, x> (library): the adjoint is the
+    transpose at any size, without assembling L."""
+    rng = np.random.default_rng(seed)
+    dt = torch.float32 if prec == 1 else torch.float64
+    x = torch.tensor(rng.standard_normal(p.n_dofs), device="cuda", dtype=dt)
+    y = torch.tensor(rng.standard_normal(p.n_dofs), device="cuda", dtype=dt)
+    ltx = dg.apply_adjoint(y, prec=prec).double().cpu().numpy()
+    xh, yh = x.double().cpu().numpy(), y.double().cpu().numpy()
+    lhs = yh @ p.apply(xh)
+    rhs = ltx @ xh
+    scale = np.abs(yh) @ p.apply_abs(xh)
+    return abs(lhs - rhs), scale
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_adjoint_dot_identity_6d(prec):
+    dg, p = random_problem(3, 3, 3, (2, 1, 2, 2, 1, 3), "phase", seed=5)
+    err, scale = _dot_identity(dg, p, prec, seed=6)
+    assert err <= (1e-12 if prec == 0 else TOL32) * scale
+    dg.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_specialised_6d_kernel_matches_generic(prec, adjoint):
+    """The 6D, k = 3 specialised kernel and the generic kernel agree; both
+    match the oracle (forward) or satisfy the transpose identity (adjoint)."""
+    dg, p = random_problem(3, 3, 3, (2, 3, 1, 2, 1, 2), "phase", seed=7)
+    u = np.random.default_rng(8).standard_normal(p.n_dofs)
+    dt = torch.float32 if prec == 1 else torch.float64
+    ut = torch.tensor(u, device="cuda", dtype=dt)
+    uin = ut.double().cpu().numpy()
+    outs = []
+    for variant in (0, 1):
+        dg.set_launch(prec, threads=256, cells_per_block=1, variant=variant)
+        f = dg.apply_adjoint if adjoint else dg.apply
+        outs.append(f(ut, prec=prec).double().cpu().numpy())
+        if adjoint:
+            err, scale = _dot_identity(dg, p, prec, seed=10 + variant)
+            assert err <= TOL32 * scale
+    dg.check()
+    scale = np.linalg.norm(p.apply_abs(uin))
+    if not adjoint:
+        ref = p.apply(uin)
+        for o in outs:
+            assert np.linalg.norm(o - ref) <= TOL32 * scale
+    assert np.linalg.norm(outs[0] - outs[1]) <= 4 * TOL32 * scale
+    dg.close()
+
+
+def test_launch_configurations_agree():
+    """Every cells-per-block / thread count / sweep order gives the same result."""
+    dg, p = random_problem(2, 2, 2, (3, 2, 3, 2), "phase", seed=9)
+    u = torch.tensor(np.random.default_rng(1).standard_normal(p.n_dofs), device="cuda")
+    ref = dg.apply(u).cpu().numpy()
+    for threads in (64, 128, 512):
+        for cpb in (1, 3, 8):
+            for order in ([0, 1, 2, 3], [3, 2, 1, 0], [2, 0, 3, 1]):
+                dg.set_launch(0, threads=threads, cells_per_block=cpb, order=order)
+                out = dg.apply(u).cpu().numpy()
+                assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))
+    best = dg.autotune(u, torch.empty_like(u), 0)
+    assert best > 0
+    out = dg.apply(u).cpu().numpy()
+    assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))
+    dg.close()

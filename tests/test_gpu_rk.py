@@ -1,0 +1,166 @@
+"""GPU parity of the fused LSRK(5,4) stages and of whole time steps, the
+invariants over time, integrals and the device error latch."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W  # noqa: E402
+from dg_helpers import dg_for, oracle_for, random_problem  # noqa: E402
+from oracle import lsrk  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as entry
+    entry.build()
+
+
+@pytest.mark.parametrize("case", [(1, 1, 3, (6, 5)), (2, 2, 2, (2, 3, 2, 2)),
+                                  (3, 3, 3, (2, 1, 2, 1, 2, 2))],
+                         ids=lambda c: f"{c[0]}x{c[1]}v_k{c[2]}")
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("stage", [0, 2, 4])
+def test_fused_stage(case, prec, stage):
+    """K = L(w); u <- u + b_s dt K; w_out = u_old + a_s dt K (s < 4) or u_new."""
+    dx, dv, k, cells = case
+    dg, p = random_problem(dx, dv, k, cells, "phase", seed=11)
+    rng = np.random.default_rng(12)
+    w = rng.standard_normal(p.n_dofs)
+    u = rng.standard_normal(p.n_dofs)
+    dt = 1e-2
+    wdt = torch.float32 if prec == 1 else torch.float64
+    wt = torch.tensor(w, device="cuda", dtype=wdt)
+    ut = torch.tensor(u, device="cuda", dtype=torch.float64)
+    wo = torch.empty_like(wt)
+    dg.rk_stage(wt, wo, ut, stage, dt, prec=prec)
+    dg.check()
+    win = wt.double().cpu().numpy()
+    K = p.apply(win)
+    u_ref = u + lsrk.B[stage] * dt * K
+    w_ref = u_ref if stage == 4 else u + lsrk.A[stage] * dt * K
+    scale = 1.0 if prec == 0 else np.abs(p.apply_abs(win))
+    tol = 1e-13 if prec == 0 else 1e-5
+    err_u = np.abs(ut.cpu().numpy() - u_ref)
+    err_w = np.abs(wo.double().cpu().numpy() - w_ref)
+    if prec == 0:
+        assert np.max(err_u) <= tol * np.max(np.abs(u_ref))
+        assert np.max(err_w) <= tol * np.max(np.abs(w_ref))
+    else:
+        # K error (term scale) times dt, plus the FP32 rounding of w_out
+        bound_u = 1e-14 * np.abs(u_ref) + tol * dt * (scale + np.abs(K))
+        assert np.all(err_u <= bound_u + 1e-300)
+        if prec == 1:
+            a_dtK = np.abs((lsrk.B[4] if stage == 4 else lsrk.A[stage]) * dt * K)
+            assert np.all(err_w <= bound_u + 2.5e-7 * (np.abs(u) + a_dtK) + 1e-30)
+        else:
+            assert np.all(err_w <= bound_u + 1e-14 * np.abs(w_ref))
+    dg.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_rk_steps_match_oracle(prec, adjoint):
+    """nsteps full LSRK(5,4) steps (graph replay) == the oracle's steps with
+    the assembled L (or L^T)."""
+    w = W.shrink(W.config_4d(), cells_x=(3, 2), cells_v=(2, 3), k=2)
+    dg, p = dg_for(w)
+    L = p.assemble()
+    A = L.T.tocsr() if adjoint else L
+    zeta = np.polynomial.legendre.leggauss(w.n)[0]
+    u0 = W.initial_state(w, zeta)
+    dt = 0.5 * W.time_step(w)[0]
+    nsteps = 7
+    ref = u0.copy()
+    for _ in range(nsteps):
+        ref = lsrk.step(lambda x: A @ x, ref, dt)
+    ut = torch.tensor(u0, device="cuda")
+    dg.rk_step(ut, dt, nsteps=nsteps, prec=prec, adjoint=adjoint)
+    dg.check()
+    out = ut.cpu().numpy()
+    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert rel < (1e-13 if prec == 0 else 1e-5), rel
+    # replay again from the same start (graphs cached) gives the same result
+    ut2 = torch.tensor(u0, device="cuda")
+    dg.rk_step(ut2, dt, nsteps=nsteps, prec=prec, adjoint=adjoint)
+    assert torch.equal(ut, ut2)
+    dg.close()
+
+
+def test_rk_2d_config_one_period():
+    """The 2D workload through the library: after T = 2 (240 steps) the state
+    matches the oracle's time integration and returns to u0 up to the
+    discretisation error; mass is conserved and the L2 norm does not grow."""
+    w = W.config_2d()
+    dg, p = dg_for(w)
+    zeta = np.polynomial.legendre.leggauss(w.n)[0]
+    u0 = W.separable_state(w, zeta)
+    dt, steps = W.time_step(w)
+    ut = torch.tensor(u0, device="cuda")
+    m0, l0, _ = dg.integrals(ut)
+    dg.rk_step(ut, dt, nsteps=steps)
+    dg.check()
+    m1, l1, _ = dg.integrals(ut)
+    L = p.assemble()
+    ref = u0.copy()
+    for _ in range(steps):
+        ref = lsrk.step(lambda x: L @ x, ref, dt)
+    out = ut.cpu().numpy()
+    assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+    Md = p.mass_diagonal()
+    assert math.sqrt((out - u0) @ (Md * (out - u0)) / (u0 @ (Md * u0))) < 2e-4
+    assert abs(m1 - m0) < 1e-13
+    assert l1 <= l0 * (1 + 1e-14)
+    dg.close()
+
+
+def test_integrals_match_oracle():
+    w = W.shrink(W.config_4d(), cells_x=(3, 2), cells_v=(2, 3), k=3)
+    dg, p = dg_for(w)
+    u = np.random.default_rng(3).standard_normal(p.n_dofs)
+    m, l2, mx = dg.integrals(torch.tensor(u, device="cuda"))
+    rm, rl2, rmx = p.integrals(u)
+    assert abs(m - rm) <= 1e-12 * abs(rl2) and abs(l2 - rl2) <= 1e-12 * rl2 and mx == rmx
+    dg.close()
+
+
+def test_nonfinite_is_latched_and_cleared():
+    from paper_2002_08110_gb300 import DGError
+    dg, p = random_problem(2, 2, 1, (2, 2, 2, 2), "const", seed=1)
+    u = torch.zeros(p.n_dofs, device="cuda", dtype=torch.float64)
+    u[5] = float("nan")
+    dg.apply(u)
+    with pytest.raises(DGError) as ei:
+        dg.check()
+    assert ei.value.status == 5
+    u[5] = 0.0
+    dg.apply(u)
+    dg.check()          # latch cleared
+    dg.close()
+
+
+def test_host_argument_errors():
+    from paper_2002_08110_gb300 import DGError
+    dg, p = random_problem(1, 1, 2, (3, 3), "const", seed=1)
+    u = torch.zeros(p.n_dofs, device="cuda", dtype=torch.float64)
+    lib = dg.lib
+    import ctypes
+    ptr = ctypes.c_void_p(u.data_ptr())
+    assert lib.dg_apply(dg.handle, ptr, ptr, 0, None) == 1            # aliasing
+    assert lib.dg_apply(dg.handle, ptr, ctypes.c_void_p(u.data_ptr() + 8 * p.n_dofs // 2),
+                        0, None) == 1                                  # overlap
+    assert lib.dg_apply(dg.handle, ptr, ctypes.c_void_p(u.data_ptr() + 4), 0, None) == 1
+    assert lib.dg_apply(dg.handle, ptr, None, 0, None) == 1
+    assert lib.dg_apply(dg.handle, ptr, ptr, 3, None) == 1             # precision
+    assert lib.dg_rk_stage(dg.handle, ptr, ptr, ptr, 5, 0.1, 0, 0, None) == 1
+    with pytest.raises(DGError):
+        dg.set_launch(0, threads=48, cells_per_block=1)
+    with pytest.raises(DGError):
+        dg.set_launch(0, threads=64, cells_per_block=1, order=[0, 0])
+    dg.close()
