@@ -62,7 +62,7 @@ typedef enum {
     DG_ERR_CUDA = 3,          /* a CUDA runtime call failed                 */
     DG_ERR_OOM = 4,           /* device or host allocation failed           */
     DG_ERR_NONFINITE = 5,     /* a kernel produced NaN or Inf               */
-    DG_ERR_TIMEOUT = 6        /* reserved: a bounded device wait gave up    */
+    DG_ERR_TIMEOUT = 6        /* a bounded wait inside a kernel gave up     */
 } dg_status;
 
 typedef enum {
@@ -112,6 +112,10 @@ typedef struct {
     double speed_sum;         /* sum_j max over nodes of |a_j| / h_j        */
     double det_jacobian;      /* |J| of every cell                          */
     double h[6];              /* cell sizes (lattice sizes in x)            */
+    int uniform_sides;        /* 1 if no speed component changes sign inside
+                                 a cell (each cell has one upwind neighbour
+                                 per direction); the specialised 6D kernel
+                                 runs only then                             */
 } dg_info_t;
 
 /* Launch configuration of the cell kernels (chosen by dg_autotune). */
@@ -226,8 +230,9 @@ dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream);
 
 /*
  * Synchronise ``stream`` and report device-side errors latched since the
- * last check: DG_ERR_NONFINITE if any kernel produced NaN or Inf.  Clears the
- * latch.
+ * last check: DG_ERR_TIMEOUT if a kernel's bounded wait for an asynchronous
+ * copy gave up (its results are invalid), else DG_ERR_NONFINITE if any kernel
+ * produced NaN or Inf.  Clears the latch.
  */
 dg_status dg_check(dg_handle h, void* stream);
 

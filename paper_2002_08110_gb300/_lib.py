@@ -32,7 +32,8 @@ class Info(ctypes.Structure):
                 ("n_xcells", ctypes.c_longlong), ("n_vcells", ctypes.c_longlong),
                 ("dofs_per_cell", ctypes.c_int), ("dim_x", ctypes.c_int), ("dim_v", ctypes.c_int),
                 ("degree", ctypes.c_int), ("speed_sum", ctypes.c_double),
-                ("det_jacobian", ctypes.c_double), ("h", ctypes.c_double * 6)]
+                ("det_jacobian", ctypes.c_double), ("h", ctypes.c_double * 6),
+                ("uniform_sides", ctypes.c_int)]
 
 
 class Launch(ctypes.Structure):

@@ -137,7 +137,7 @@ dg_status ensure_scratch(dg_ctx* h, int prec) {
 
 cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
                         cudaStream_t s) {
-  if (cfg.variant == 1 && h->d == 6 && h->n == 4) {
+  if (cfg.variant == 1 && h->d == 6 && h->n == 4 && h->uniform_sides) {
     cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
     if (e != cudaErrorNotSupported) return e;
   }
@@ -294,6 +294,21 @@ dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
         if (!std::isfinite(a)) return fail(DG_ERR_INVALID_ARG, "E is not finite");
         h->cv_host[(cx * h->nqx + q) * dv + i] = 2.0 / h->h[dx + i] * a;
       }
+  // uniform upwind side per cell and direction (zero speeds fit either side)
+  auto uniform = [](const std::vector<double>& tab, long long ncellsub, int nq, int dims) {
+    for (long long c = 0; c < ncellsub; ++c)
+      for (int j = 0; j < dims; ++j) {
+        bool pos = false, neg = false;
+        for (int q = 0; q < nq; ++q) {
+          const double v = tab[(c * nq + q) * dims + j];
+          pos |= v > 0.0;
+          neg |= v < 0.0;
+        }
+        if (pos && neg) return false;
+      }
+    return true;
+  };
+  h->uniform_sides = uniform(h->cx_host, h->ncv, h->nqv, dx) && uniform(h->cv_host, h->ncx, h->nqx, dv);
   double sum = 0.0;
   for (int j = 0; j < h->d; ++j) {
     double mx = 0.0;
@@ -478,6 +493,10 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
     free_ctx(h);
     return cuda_fail(e, "dg_create");
   }
+  if (h->d == 6 && h->n == 4 && (e = init_cell6d_tables(h->tables.t32)) != cudaSuccess) {
+    free_ctx(h);
+    return cuda_fail(e, "dg_create");
+  }
   default_cfg(h);
   *out = h;
   return DG_OK;
@@ -502,6 +521,7 @@ dg_status dg_info(dg_handle h, dg_info_t* info) {
   info->speed_sum = h->speed_sum;
   info->det_jacobian = h->detJ;
   for (int j = 0; j < h->d; ++j) info->h[j] = h->h[j];
+  info->uniform_sides = h->uniform_sides ? 1 : 0;
   return DG_OK;
 }
 
@@ -676,7 +696,8 @@ dg_status dg_check(dg_handle h, void* stream) {
       (e = cudaMemcpy(&flag, h->err_d, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
       (e = cudaMemset(h->err_d, 0, sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "dg_check");
-  if (flag) return fail(DG_ERR_NONFINITE, "a kernel produced a non-finite value");
+  if (flag & 2) return fail(DG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+  if (flag & 1) return fail(DG_ERR_NONFINITE, "a kernel produced a non-finite value");
   return DG_OK;
 }
 

@@ -2,28 +2,44 @@
 // FP32 sweeps and fluxes.
 //
 // A cell has 4096 values, q = q_x + 64 q_v with q_x = (q1,q2,q3), q_v = (q4,q5,q6)
-// (x_1 fastest).  64 threads (one "group") process one cell in two phases,
-// mirroring Algorithm 2's split of the cell work into the x-space part and the
-// v-space part (which reduces the working set):
-//   phase X: thread t owns the v node q_v = t and holds the 4x4x4 x-block
-//            {q_x} of that node in registers, so every line along x1, x2, x3
-//            is thread-local; the contravariant speeds c_1..c_3 depend on q_v
+// (x_1 fastest).  One block of 64 threads processes one cell at a time, in two
+// phases that follow Algorithm 2's split of the cell work into the x-space
+// part and the v-space part:
+//   phase X: thread t owns the v node q_v = t and holds the 4x4x4 x-block of
+//            that node in registers, so every line along x1, x2, x3 is
+//            thread-local; the contravariant speeds c_1..c_3 depend on q_v
 //            only (a_x = v), so they are thread constants;
 //   phase V: thread t owns the x node q_x = t and holds the 4x4x4 v-block,
-//            lines along v1, v2, v3 thread-local; c_4..c_6 = 2 E(x)/h_v depend
-//            on q_x only.
+//            lines along v1, v2, v3 thread-local; c_4..c_6 = 2 E(x) / h_v
+//            depend on q_x only.
 // Per direction and line: du_q += c (sum_p G[q][p] u_p + L_nb[q] t_nb) with the
-// collocated 1D operator of dg_internal.h; t_nb is the upwind neighbour's trace
-// on the shared face, computed from the neighbour's line, read from global
-// memory (periodic wrap; phase X reads the neighbour's contiguous 256-byte
-// x-block, phase V reads stride-64 values that are coalesced across the warp).
-// Shared memory holds the cell's input (for the phase V transpose) and the
-// phase X partial result; blocks of 64 floats are padded to 68 so that the
-// 16-byte accesses of phase X and the 4-byte accesses of phase V are free of
-// bank conflicts.
+// collocated 1D operator (see Tab1D); t_nb is the upwind neighbour's trace on
+// the shared face, computed from the neighbour's line (periodic wrap).  The
+// two phases read different views of the padded shared buffers: rows of a
+// block in phase X, columns across blocks in phase V.
+// The host uses this kernel only when every cell has one upwind side per
+// direction (no speed changes sign inside a cell).
+//
+// Data movement: every cell the block needs -- the cell itself and its six
+// upwind neighbours -- is brought into shared memory by the TMA engine
+// (cp.async.bulk, one 256-byte block per thread, completion counted on an
+// mbarrier), into buffers whose 64-float blocks are padded to 68 floats so
+// that the 16-byte row reads of phase X and the 4-byte column reads of phase V
+// are free of bank conflicts.  Three buffers rotate (so that four blocks fit
+// on an SM): the current cell and two landing buffers; the next cell lands in
+// the cell buffer once phase V has its values in registers, and the phase X
+// result passes to phase V through a landing buffer.  Every copy is issued as
+// soon as its buffer is free, so the next cell and the next neighbours are in
+// flight while the current direction is computed.
+//
+// Waits on mbarriers are bounded: after the poll limit the block latches an
+// error flag (reported as DG_ERR_TIMEOUT), waits (bounded) for its copies in
+// flight and returns.
 //
 // Modes: operator application (dst = K) or fused LSRK stage
 // (u += b dt K in FP64; w_out = u + a dt K).  Adjoint: L^T = M L(-a) M^{-1}.
+// FP64 input (DG_PREC_MIXED) is converted while the threads copy it into
+// shared memory themselves.
 #include "dg_convert.cuh"
 #include "dg_generic.cuh"
 
@@ -32,69 +48,131 @@ namespace {
 
 constexpr int kPad = 68;              // padded floats per 64-value block
 constexpr int kCellSmem = 64 * kPad;  // floats per cell buffer
+constexpr int kNumBuf = 3;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s of SM clock before giving up
 
-__device__ __forceinline__ void group_sync(int grp) {
-  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(64) : "memory");
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Waits for the phase with the given parity; the thread is suspended (up to
+// the hint, in ns) instead of spinning.  Returns false if the phase is not
+// complete yet.
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (TMA) writes to it; every reuse of a buffer by the TMA is
+// preceded by this fence in all threads and then a block barrier.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <typename TIN>
-struct Ld;
-template <>
-struct Ld<float> {
-  static __device__ __forceinline__ float4 ld4(const float* p) {
-    return __ldg(reinterpret_cast<const float4*>(p));
-  }
-  static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
-};
-template <>
-struct Ld<double> {
-  static __device__ __forceinline__ float4 ld4(const double* p) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    return make_float4(f64_to_f32(a.x), f64_to_f32(a.y), f64_to_f32(b.x), f64_to_f32(b.y));
-  }
-  static __device__ __forceinline__ float ld1(const double* p) {
-    return f64_to_f32(__ldg(p));
-  }
-};
+__device__ __forceinline__ float4 ld4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  return make_float4(f64_to_f32(a.x), f64_to_f32(a.y), f64_to_f32(b.x), f64_to_f32(b.y));
+}
 
-// Element index inside a 4x4x4 block of the point p on line (l1, l2) along
-// local direction J.
+// Element index inside a 4x4x4 block of point p on line (l1, l2) along local
+// direction J.
 template <int J>
 __device__ __forceinline__ constexpr int eidx(int l1, int l2, int p) {
   return J == 0 ? p + 4 * l1 + 16 * l2 : (J == 1 ? l1 + 4 * p + 16 * l2 : l1 + 4 * l2 + 16 * p);
-}
-
-// Row (b, c) of the neighbour's block: the four values a = 0..3 at element
-// a + 4 b + 16 c.  STRIDE is the distance between consecutive elements in
-// memory (1 in phase X, 64 in phase V).
-template <typename TIN, int STRIDE>
-__device__ __forceinline__ float4 nb_row(const TIN* base, int b, int c) {
-  const TIN* p = base + (4 * b + 16 * c) * STRIDE;
-  if constexpr (STRIDE == 1) {
-    return Ld<TIN>::ld4(p);
-  } else {
-    return make_float4(Ld<TIN>::ld1(p), Ld<TIN>::ld1(p + STRIDE), Ld<TIN>::ld1(p + 2 * STRIDE),
-                       Ld<TIN>::ld1(p + 3 * STRIDE));
-  }
 }
 
 __device__ __forceinline__ float comp(const float4& v, int a) {
   return a == 0 ? v.x : (a == 1 ? v.y : (a == 2 ? v.z : v.w));
 }
 
-// Block weights for the adjoint's M^{-1} scaling of the neighbour values:
-// product of the inverse 1D weights over the three block digits.
+// Product of three 1D weights over the digits of a block element.
 __device__ __forceinline__ float wprod(const float* w, int e) {
   return w[e & 3] * w[(e >> 2) & 3] * w[e >> 4];
 }
 
-// Contribution of local direction J (0..2) of the thread's block: all 16
-// lines along J.  POS: c > 0 (inflow through the lower face, neighbour below).
-template <int J, bool POS, bool ADJ, typename TIN, int STRIDE>
-__device__ __forceinline__ void sweep(const float (&u)[64], float (&r)[64], float c,
-                                      const Tab1D<float>& T, const TIN* nb, float wnb) {
-  // traces of the 16 neighbour lines on the shared face
+// Upwind neighbour of `cell` along direction j (s = -1 below, +1 above) with
+// periodic wrap, in 32-bit arithmetic (cell counts are below 2^31).
+__device__ __forceinline__ unsigned nb32(const KParams& p, unsigned cell, int j, int s) {
+  const unsigned st = static_cast<unsigned>(p.cstride[j]);
+  const unsigned nj = static_cast<unsigned>(p.ncell[j]);
+  const unsigned cj = (cell / st) % nj;
+  if (s < 0) return cj == 0 ? cell + (nj - 1) * st : cell - st;
+  return cj == nj - 1 ? cell - (nj - 1) * st : cell + st;
+}
+
+// The thread's block inside a padded buffer: row view (phase X: block t,
+// element e at +e) or column view (phase V: element t of block e, at e*kPad).
+template <bool ROWS>
+__device__ __forceinline__ const float* view(const float* buf, int t) {
+  return ROWS ? buf + t * kPad : buf + t;
+}
+template <bool ROWS>
+__device__ __forceinline__ float4 row4(const float* v, int i) {
+  if constexpr (ROWS) {
+    return *reinterpret_cast<const float4*>(v + 4 * i);
+  } else {
+    return make_float4(v[(4 * i) * kPad], v[(4 * i + 1) * kPad], v[(4 * i + 2) * kPad],
+                       v[(4 * i + 3) * kPad]);
+  }
+}
+template <bool ROWS>
+__device__ __forceinline__ void load_block(float (&x)[64], const float* v) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float4 a = row4<ROWS>(v, i);
+    x[4 * i] = a.x;
+    x[4 * i + 1] = a.y;
+    x[4 * i + 2] = a.z;
+    x[4 * i + 3] = a.w;
+  }
+}
+
+// The collocated 1D tables of n = 4 for both upwind sides (index 0: c > 0,
+// index 1: c < 0), in constant memory so that a block-uniform side selects
+// them with one broadcast load: G = Gp / Gn, Ln = Lm / -Lp, lw = lp / lm.
+__constant__ float c_G[2][16];
+__constant__ float c_Ln[2][4];
+__constant__ float c_lw[2][4];
+
+// One direction J of the thread's block: traces of the upwind neighbour's 16
+// lines from the landing buffer, then the 16 line contractions.  The upwind
+// side is chosen at run time; the 1D matrices of that side (scaled by c) are
+// held in registers so that one body serves both signs.
+template <int J, bool ROWS, bool ADJ>
+__device__ __forceinline__ void direction(float (&r)[64], const float (&u)[64], const float* nbv,
+                                          float c, float wthread, const Tab1D<float>& T) {
+  const int side = c > 0.f ? 0 : 1;
+  float lw[4], Ln[4], G[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    lw[i] = c_lw[side][i];
+    Ln[i] = c * c_Ln[side][i];
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) G[i] = c * c_G[side][i];
   float tr[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) tr[i] = 0.f;
@@ -102,212 +180,306 @@ __device__ __forceinline__ void sweep(const float (&u)[64], float (&r)[64], floa
   for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      float4 v = nb_row<TIN, STRIDE>(nb, b, cc);
-      if (ADJ) {
-        v.x *= wprod(T.winv, 0 + 4 * b + 16 * cc);
-        v.y *= wprod(T.winv, 1 + 4 * b + 16 * cc);
-        v.z *= wprod(T.winv, 2 + 4 * b + 16 * cc);
-        v.w *= wprod(T.winv, 3 + 4 * b + 16 * cc);
-      }
+      const float4 v = row4<ROWS>(nbv, b + 4 * cc);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        // element (a, b, cc): line and position along J
         const int l1 = J == 0 ? b : a;
         const int l2 = J == 2 ? b : cc;
         const int pp = J == 0 ? a : (J == 1 ? b : cc);
-        const float lw = POS ? T.lp[pp] : T.lm[pp];
-        tr[l1 + 4 * l2] = fmaf(lw, comp(v, a), tr[l1 + 4 * l2]);
+        float x = comp(v, a);
+        if (ADJ) x *= wprod(T.winv, a + 4 * b + 16 * cc);
+        tr[l1 + 4 * l2] = fmaf(lw[pp], x, tr[l1 + 4 * l2]);
       }
     }
 #pragma unroll
   for (int l2 = 0; l2 < 4; ++l2)
 #pragma unroll
     for (int l1 = 0; l1 < 4; ++l1) {
-      const float t = (ADJ ? wnb : 1.f) * tr[l1 + 4 * l2];
+      const float t = ADJ ? wthread * tr[l1 + 4 * l2] : tr[l1 + 4 * l2];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float acc = (POS ? T.Lm[q] : -T.Lp[q]) * t;
+        float acc = fmaf(Ln[q], t, r[eidx<J>(l1, l2, q)]);
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp)
-          acc = fmaf(POS ? T.Gp[q * 4 + pp] : T.Gn[q * 4 + pp], u[eidx<J>(l1, l2, pp)], acc);
-        r[eidx<J>(l1, l2, q)] = fmaf(c, acc, r[eidx<J>(l1, l2, q)]);
+        for (int pp = 0; pp < 4; ++pp) acc = fmaf(G[q * 4 + pp], u[eidx<J>(l1, l2, pp)], acc);
+        r[eidx<J>(l1, l2, q)] = acc;
       }
     }
 }
 
-template <int J, bool ADJ, typename TIN, int STRIDE>
-__device__ __forceinline__ void direction(const KParams& p, long long cell, int gdim, int off,
-                                          const float (&u)[64], float (&r)[64], float c,
-                                          const Tab1D<float>& T, float wnb) {
-  if (ADJ) c = -c;
-  if (c == 0.f) return;
-  const TIN* src = static_cast<const TIN*>(p.src);
-  if (c > 0.f) {
-    const long long nb = neighbour_cell(p, cell, gdim, -1);
-    sweep<J, true, ADJ, TIN, STRIDE>(u, r, c, T, src + nb * 4096 + off, wnb);
-  } else {
-    const long long nb = neighbour_cell(p, cell, gdim, 1);
-    sweep<J, false, ADJ, TIN, STRIDE>(u, r, c, T, src + nb * 4096 + off, wnb);
-  }
-}
+struct Pipe {
+  unsigned long long bar[kNumBuf];
+  int failed;
+};
 
-template <typename TIN, typename TW, int CPB, bool ADJ>
-__global__ void __launch_bounds__(64 * CPB) k_cell6d4(const KParams p) {
-  extern __shared__ __align__(16) float sm6[];
-  const int grp = threadIdx.x >> 6;
-  const int t = threadIdx.x & 63;
-  float* su = sm6 + grp * 2 * kCellSmem;
-  float* sr = su + kCellSmem;
+// Moves cells into the padded buffers and waits for them.  FP32 input: TMA
+// bulk copies (one padded 256-byte block per thread, counted on the buffer's
+// mbarrier).  FP64 input: the threads load, convert and store their own block
+// and the wait is a block barrier.
+template <typename TIN>
+struct Mover {
+  float* sm;
+  Pipe* pp;
+  unsigned phase = 0;  // parity bit per buffer
+
+  __device__ __forceinline__ void issue(int b, const TIN* cellp, int t) {
+    float* d = sm + b * kCellSmem + t * kPad;
+    if constexpr (sizeof(TIN) == 4) {
+      if (t == 0) mbar_expect_tx(&pp->bar[b], 4096 * 4);
+      bulk_g2s(d, cellp + t * 64, 256, &pp->bar[b]);
+    } else {
+      const TIN* g = cellp + t * 64;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) *reinterpret_cast<float4*>(d + 4 * i) = ld4(g + 4 * i);
+    }
+  }
+  // returns false if the wait gave up
+  __device__ __forceinline__ bool wait(int b, int* err) {
+    if constexpr (sizeof(TIN) == 4) {
+      const unsigned par = (phase >> b) & 1u;
+      phase ^= 1u << b;
+      if (mbar_try_wait(&pp->bar[b], par)) return true;
+      const long long t0 = clock64();
+      while (clock64() - t0 < kWaitCycles)
+        if (mbar_try_wait(&pp->bar[b], par)) return true;
+      atomicOr(err, 2);
+      return false;
+    } else {
+      __syncthreads();
+      return true;
+    }
+  }
+};
+
+template <typename TIN, typename TW, bool ADJ>
+__global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
+  extern __shared__ __align__(128) float sm6[];
+  __shared__ Pipe pipe;
+  const int t = threadIdx.x;
   const Tab1D<float>& T = p.t32;
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
-  // thread-constant weight factors of the adjoint scaling
-  const float wv_inv = ADJ ? wprod(T.winv, t) : 1.f;   // phase X: v node t
+  const unsigned ncells = static_cast<unsigned>(p.ncells);
+  const unsigned ncx = static_cast<unsigned>(p.ncx);
+  const float winv_t = ADJ ? wprod(T.winv, t) : 1.f;
+  const float w_t = ADJ ? wprod(T.w, t) : 1.f;
   int bad = 0;
 
-  for (long long cell = static_cast<long long>(blockIdx.x) * CPB + grp; cell < p.ncells;
-       cell += static_cast<long long>(gridDim.x) * CPB) {
-    // ---- step 1: gather the cell into shared memory (coalesced, padded)
-    const TIN* cs = src + cell * 4096;
-#pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
-      const int f = i * 64 + t;                 // float4 index within the cell
-      const int m = f >> 4, ch = f & 15;        // block (v node) and chunk
-      float4 v = Ld<TIN>::ld4(cs + 4 * f);
-      if (ADJ) {
-        const float wm = wprod(T.winv, m);
-        v.x *= wm * wprod(T.winv, 4 * ch + 0);
-        v.y *= wm * wprod(T.winv, 4 * ch + 1);
-        v.z *= wm * wprod(T.winv, 4 * ch + 2);
-        v.w *= wm * wprod(T.winv, 4 * ch + 3);
-      }
-      *reinterpret_cast<float4*>(su + m * kPad + 4 * ch) = v;
+  unsigned cell = blockIdx.x;
+  if (cell >= ncells) return;
+  if (t == 0) {
+    for (int b = 0; b < kNumBuf; ++b) mbar_init(&pipe.bar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  Mover<TIN> mv{sm6, &pipe};
+  auto cellp = [&](unsigned c) { return src + static_cast<size_t>(c) * 4096; };
+  // speeds and upwind neighbours (x speeds depend on the v node t, v speeds
+  // on the x node t; the upwind side is the same for all threads)
+  auto setup = [&](unsigned c, float (&sp)[6], unsigned (&nbr)[6]) {
+    const unsigned cv = c / ncx, cx = c - cv * ncx;
+    const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * 64 + t) * 3;
+    const float* ctv = static_cast<const float*>(p.cv_tab) + (static_cast<size_t>(cx) * 64 + t) * 3;
+    sp[0] = ctx[0];
+    sp[1] = ctx[1];
+    sp[2] = ctx[2];
+    sp[3] = ctv[0];
+    sp[4] = ctv[1];
+    sp[5] = ctv[2];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (ADJ) sp[j] = -sp[j];
+      nbr[j] = nb32(p, c, j, sp[j] > 0.f ? -1 : 1);
     }
-    group_sync(grp);
+  };
 
-    // ---- phase X: directions x1, x2, x3 on the x-block of v node t
+  // buffers: A = 0 holds the current cell, B = 1 and C = 2 are landing
+  // buffers; the next cell lands in A once phase V has its values in
+  // registers.
+  constexpr int A = 0, B = 1, C = 2;
+  float sp[6];
+  unsigned nbr[6];
+  setup(cell, sp, nbr);
+  mv.issue(A, cellp(cell), t);
+  mv.issue(B, cellp(nbr[0]), t);
+  mv.issue(C, cellp(nbr[1]), t);
+  bool ok = true;
+
+  for (;;) {
+    const unsigned next = cell + gridDim.x;
+    const bool has_next = next < ncells;
+    float spn[6];
+    unsigned nbn[6];
+    if (has_next) setup(next, spn, nbn);
     float u[64], r[64];
+#pragma unroll
+    for (int e = 0; e < 64; ++e) r[e] = 0.f;
+
+    // ---- phase X: rows of the padded buffers, directions x1, x2, x3
+    ok &= mv.wait(A, p.err);
+    load_block<true>(u, view<true>(sm6 + A * kCellSmem, t));
+    if (ADJ) {
+#pragma unroll
+      for (int e = 0; e < 64; ++e) u[e] *= winv_t * wprod(T.winv, e);
+    }
+    ok &= mv.wait(B, p.err);
+    direction<0, true, ADJ>(r, u, view<true>(sm6 + B * kCellSmem, t), sp[0], winv_t, T);
+    fence_async_smem();
+    __syncthreads();
+    mv.issue(B, cellp(nbr[2]), t);               // x3
+    ok &= mv.wait(C, p.err);
+    direction<1, true, ADJ>(r, u, view<true>(sm6 + C * kCellSmem, t), sp[1], winv_t, T);
+    fence_async_smem();
+    __syncthreads();
+    mv.issue(C, cellp(nbr[3]), t);               // v1
+    ok &= mv.wait(B, p.err);
+    direction<2, true, ADJ>(r, u, view<true>(sm6 + B * kCellSmem, t), sp[2], winv_t, T);
+    __syncthreads();                             // B is free: it takes the phase X result
     {
-      const float* ub = su + t * kPad;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float4 v = *reinterpret_cast<const float4*>(ub + 4 * i);
-        u[4 * i] = v.x;
-        u[4 * i + 1] = v.y;
-        u[4 * i + 2] = v.z;
-        u[4 * i + 3] = v.w;
-      }
-#pragma unroll
-      for (int e = 0; e < 64; ++e) r[e] = 0.f;
-      const long long cv = cell / p.ncx;
-      const float* ct = static_cast<const float*>(p.cx_tab) + (cv * 64 + t) * 3;
-      const float c0 = ct[0], c1 = ct[1], c2 = ct[2];
-      direction<0, ADJ, TIN, 1>(p, cell, 0, t * 64, u, r, c0, T, wv_inv);
-      direction<1, ADJ, TIN, 1>(p, cell, 1, t * 64, u, r, c1, T, wv_inv);
-      direction<2, ADJ, TIN, 1>(p, cell, 2, t * 64, u, r, c2, T, wv_inv);
-      float* rb = sr + t * kPad;
+      float* rb = sm6 + B * kCellSmem + t * kPad;
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         *reinterpret_cast<float4*>(rb + 4 * i) =
             make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
     }
-    group_sync(grp);
+    __syncthreads();
 
-    // ---- phase V: directions v1, v2, v3 on the v-block of x node t
-    {
+    // ---- phase V: columns, directions v1, v2, v3
+    load_block<false>(u, view<false>(sm6 + A * kCellSmem, t));
+    load_block<false>(r, view<false>(sm6 + B * kCellSmem, t));
+    if (ADJ) {
 #pragma unroll
-      for (int m = 0; m < 64; ++m) {
-        u[m] = su[m * kPad + t];
-        r[m] = sr[m * kPad + t];
-      }
-      const long long cx = cell % p.ncx;
-      const float* ct = static_cast<const float*>(p.cv_tab) + (cx * 64 + t) * 3;
-      const float c3 = ct[0], c4 = ct[1], c5 = ct[2];
-      const float wx_inv = ADJ ? wprod(T.winv, t) : 1.f;
-      direction<0, ADJ, TIN, 64>(p, cell, 3, t, u, r, c3, T, wx_inv);
-      direction<1, ADJ, TIN, 64>(p, cell, 4, t, u, r, c4, T, wx_inv);
-      direction<2, ADJ, TIN, 64>(p, cell, 5, t, u, r, c5, T, wx_inv);
+      for (int e = 0; e < 64; ++e) u[e] *= winv_t * wprod(T.winv, e);
     }
+    fence_async_smem();
+    __syncthreads();                             // A and B are free
+    if (has_next) mv.issue(A, cellp(next), t);   // the next cell
+    mv.issue(B, cellp(nbr[4]), t);               // v2
+    ok &= mv.wait(C, p.err);
+    direction<0, false, ADJ>(r, u, view<false>(sm6 + C * kCellSmem, t), sp[3], winv_t, T);
+    fence_async_smem();
+    __syncthreads();
+    mv.issue(C, cellp(nbr[5]), t);               // v3
+    ok &= mv.wait(B, p.err);
+    direction<1, false, ADJ>(r, u, view<false>(sm6 + B * kCellSmem, t), sp[4], winv_t, T);
+    fence_async_smem();
+    __syncthreads();
+    if (has_next) mv.issue(B, cellp(nbn[0]), t);   // x1 of the next cell
+    ok &= mv.wait(C, p.err);
 
-    // ---- step 5: scatter / fused LSRK stage update (coalesced across x nodes)
-    const float wx = ADJ ? wprod(T.w, t) : 1.f;
-    const long long g0 = cell * 4096 + t;
+    // ---- last direction fused with step 5: scatter / LSRK stage update
+    const size_t g0 = static_cast<size_t>(cell) * 4096 + t;
     if (p.mode == 0) {
+      direction<2, false, ADJ>(r, u, view<false>(sm6 + C * kCellSmem, t), sp[5], winv_t, T);
       TW* dst = static_cast<TW*>(p.dst);
 #pragma unroll
       for (int m = 0; m < 64; ++m) {
         float K = r[m];
-        if (ADJ) K *= wx * wprod(T.w, m);
+        if (ADJ) K *= w_t * wprod(T.w, m);
         bad |= !isfinite(K);
         dst[g0 + 64 * m] = cvt<TW>(K);
       }
     } else {
-      TW* dst = static_cast<TW*>(p.dst);
+      // the FP64 state of the first half of the cell is loaded while the
+      // last direction is computed, the second half while the first is used
       double* uu = p.u;
+      double uo[32];
+#pragma unroll
+      for (int m = 0; m < 32; ++m) uo[m] = __ldcs(uu + g0 + 64 * m);
+      direction<2, false, ADJ>(r, u, view<false>(sm6 + C * kCellSmem, t), sp[5], winv_t, T);
+      TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
       const float af = static_cast<float>(p.a_dt);
 #pragma unroll
-      for (int m = 0; m < 64; ++m) {
-        float K = r[m];
-        if (ADJ) K *= wx * wprod(T.w, m);
-        bad |= !isfinite(K);
-        const long long g = g0 + 64 * m;
-        const double uo = __ldcs(uu + g);
-        // one FP64 add per value; everything else in FP32 / integer arithmetic
-        const double un = uo + f32_to_f64(bf * K);
-        __stcs(uu + g, un);
-        if constexpr (sizeof(TW) == 4) {
-          dst[g] = p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(uo));
-        } else {
-          dst[g] = p.last_stage ? un : uo + p.a_dt * f32_to_f64(K);
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1) {
+#pragma unroll
+          for (int m = 0; m < 32; ++m) uo[m] = __ldcs(uu + g0 + 64 * (32 + m));
+        }
+#pragma unroll
+        for (int mm = 0; mm < 32; ++mm) {
+          const int m = 32 * h + mm;
+          float K = r[m];
+          if (ADJ) K *= w_t * wprod(T.w, m);
+          bad |= !isfinite(K);
+          const size_t g = g0 + 64 * m;
+          // one FP64 add per value; everything else in FP32 / integer arithmetic
+          const double un = uo[mm] + f32_to_f64(bf * K);
+          __stcs(uu + g, un);
+          if constexpr (sizeof(TW) == 4) {
+            dst[g] = p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(uo[mm]));
+          } else {
+            dst[g] = p.last_stage ? un : uo[mm] + p.a_dt * f32_to_f64(K);
+          }
         }
       }
     }
-    group_sync(grp);  // shared buffers are reused by the next cell
+    fence_async_smem();
+    __syncthreads();                             // C is free
+    if (!ok || !has_next) break;
+    mv.issue(C, cellp(nbn[1]), t);               // x2 of the next cell
+    cell = next;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      sp[j] = spn[j];
+      nbr[j] = nbn[j];
+    }
+  }
+  if (!ok && sizeof(TIN) == 4) {
+    // a wait gave up: wait (bounded) for every copy that may still be in
+    // flight before the block's shared memory is released
+    for (int b = 0; b < kNumBuf; ++b) {
+      const long long t0 = clock64();
+      while (clock64() - t0 < kWaitCycles)
+        if (mbar_try_wait(&pipe.bar[b], (mv.phase >> b) & 1u)) break;
+    }
   }
   if (bad) atomicOr(p.err, 1);
 }
 
-template <typename TIN, typename TW, int CPB, bool ADJ>
+template <typename TIN, typename TW, bool ADJ>
 cudaError_t launch6(KParams& p, cudaStream_t s) {
-  auto kern = k_cell6d4<TIN, TW, CPB, ADJ>;
-  const size_t smem = static_cast<size_t>(CPB) * 2 * kCellSmem * sizeof(float);
+  auto kern = k_cell6d4<TIN, TW, ADJ>;
+  const size_t smem = static_cast<size_t>(kNumBuf) * kCellSmem * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64 * CPB, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const long long chunks = (p.ncells + CPB - 1) / CPB;
-  const long long grid = std::min<long long>(chunks, static_cast<long long>(sms) * per_sm);
-  kern<<<static_cast<unsigned>(grid), 64 * CPB, smem, s>>>(p);
+  const long long grid = std::min<long long>(p.ncells, static_cast<long long>(sms) * per_sm);
+  kern<<<static_cast<unsigned>(grid), 64, smem, s>>>(p);
   return cudaGetLastError();
-}
-
-template <typename TIN, typename TW, bool ADJ>
-cudaError_t launch6_cpb(int cpb, KParams& p, cudaStream_t s) {
-  switch (cpb) {
-    case 1: return launch6<TIN, TW, 1, ADJ>(p, s);
-    case 2: return launch6<TIN, TW, 2, ADJ>(p, s);
-    default: return cudaErrorNotSupported;
-  }
 }
 
 }  // namespace
 
+cudaError_t init_cell6d_tables(const Tab1D<float>& t) {
+  float G[2][16], Ln[2][4], lw[2][4];
+  for (int i = 0; i < 16; ++i) {
+    G[0][i] = t.Gp[(i / 4) * 4 + i % 4];
+    G[1][i] = t.Gn[(i / 4) * 4 + i % 4];
+  }
+  for (int i = 0; i < 4; ++i) {
+    Ln[0][i] = t.Lm[i];
+    Ln[1][i] = -t.Lp[i];
+    lw[0][i] = t.lp[i];
+    lw[1][i] = t.lm[i];
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_G, G, sizeof(G))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_Ln, Ln, sizeof(Ln))) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_lw, lw, sizeof(lw));
+}
+
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
-  if (p.dx != 3 || p.dv != 3) return cudaErrorNotSupported;
-  const int cpb = cfg.cells_per_block;
-  if (combo == kFFF) {
-    return p.adjoint ? launch6_cpb<float, float, true>(cpb, p, s)
-                     : launch6_cpb<float, float, false>(cpb, p, s);
-  }
-  if (combo == kFDD) {
-    return p.adjoint ? launch6_cpb<double, double, true>(cpb, p, s)
-                     : launch6_cpb<double, double, false>(cpb, p, s);
-  }
+  (void)cfg;
+  if (p.dx != 3 || p.dv != 3 || p.ncells >= (1LL << 31)) return cudaErrorNotSupported;
+  if (combo == kFFF)
+    return p.adjoint ? launch6<float, float, true>(p, s) : launch6<float, float, false>(p, s);
+  if (combo == kFDD)
+    return p.adjoint ? launch6<double, double, true>(p, s) : launch6<double, double, false>(p, s);
   return cudaErrorNotSupported;
 }
 

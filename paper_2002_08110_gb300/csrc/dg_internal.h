@@ -103,6 +103,8 @@ int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int
 // Specialised 6D, n = 4, FP32-sweep kernel (dg_cell6d.cu).  Returns
 // cudaErrorNotSupported if the configuration is not covered.
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+// Uploads the n = 4 tables of the specialised kernel (they depend on n only).
+cudaError_t init_cell6d_tables(const Tab1D<float>& t);
 
 // Small kernels (dg_misc.cu).
 cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s);
@@ -126,6 +128,9 @@ struct dg_ctx {
   int field_kind = 0;
   double a_const[dg::kMaxDim] = {0};
   double speed_sum = 0.0;
+  // every cell has a single upwind side per direction (no speed component
+  // changes sign inside a cell): required by the specialised kernels
+  bool uniform_sides = true;
   int device = 0;
   dg::HostTables tables;
   std::vector<double> cx_host, cv_host;   // contravariant speeds (FP64)

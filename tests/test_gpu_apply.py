@@ -118,31 +118,55 @@ def test_adjoint_dot_identity_6d(prec):
     dg.close()
 
 
+def _uniform_6d_problems():
+    """6D, k = 3 problems in which no speed changes sign inside a cell, so the
+    specialised kernel runs: the 6D workload on 2^6 cells (v = 0 and the zeros
+    of E lie on cell faces) and a constant field on a ragged mesh."""
+    import workloads as W
+    from dg_helpers import dg_for
+    w = W.shrink(W.config_6d(), cells_x=(2, 2, 2), cells_v=(2, 2, 2))
+    yield "6d_config", dg_for(w)
+    yield "const_ragged", random_problem(3, 3, 3, (2, 3, 1, 2, 1, 3), "const", seed=7)
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_specialised_6d_kernel_matches_generic(prec, adjoint):
     """The 6D, k = 3 specialised kernel and the generic kernel agree; both
     match the oracle (forward) or satisfy the transpose identity (adjoint)."""
-    dg, p = random_problem(3, 3, 3, (2, 3, 1, 2, 1, 2), "phase", seed=7)
-    u = np.random.default_rng(8).standard_normal(p.n_dofs)
-    dt = torch.float32 if prec == 1 else torch.float64
-    ut = torch.tensor(u, device="cuda", dtype=dt)
-    uin = ut.double().cpu().numpy()
-    outs = []
-    for variant in (0, 1):
-        dg.set_launch(prec, threads=256, cells_per_block=1, variant=variant)
-        f = dg.apply_adjoint if adjoint else dg.apply
-        outs.append(f(ut, prec=prec).double().cpu().numpy())
-        if adjoint:
-            err, scale = _dot_identity(dg, p, prec, seed=10 + variant)
-            assert err <= TOL32 * scale
-    dg.check()
-    scale = np.linalg.norm(p.apply_abs(uin))
-    if not adjoint:
-        ref = p.apply(uin)
-        for o in outs:
-            assert np.linalg.norm(o - ref) <= TOL32 * scale
-    assert np.linalg.norm(outs[0] - outs[1]) <= 4 * TOL32 * scale
+    for name, (dg, p) in _uniform_6d_problems():
+        assert dg.info.uniform_sides == 1, name
+        u = np.random.default_rng(8).standard_normal(p.n_dofs)
+        dt = torch.float32 if prec == 1 else torch.float64
+        ut = torch.tensor(u, device="cuda", dtype=dt)
+        uin = ut.double().cpu().numpy()
+        outs = []
+        for variant in (0, 1):
+            dg.set_launch(prec, threads=256, cells_per_block=1, variant=variant)
+            f = dg.apply_adjoint if adjoint else dg.apply
+            outs.append(f(ut, prec=prec).double().cpu().numpy())
+            if adjoint:
+                err, scale = _dot_identity(dg, p, prec, seed=10 + variant)
+                assert err <= TOL32 * scale, name
+        dg.check()
+        scale = np.linalg.norm(p.apply_abs(uin))
+        if not adjoint:
+            ref = p.apply(uin)
+            for o in outs:
+                assert np.linalg.norm(o - ref) <= TOL32 * scale, name
+        assert np.linalg.norm(outs[0] - outs[1]) <= 4 * TOL32 * scale, name
+        dg.close()
+
+
+def test_sign_change_inside_cells_uses_generic_path():
+    """A field whose speeds change sign inside cells is still applied exactly
+    (the specialised kernel is bypassed)."""
+    dg, p = random_problem(3, 3, 3, (2, 1, 2, 2, 1, 3), "phase", seed=5)
+    assert dg.info.uniform_sides == 0
+    u = np.random.default_rng(1).standard_normal(p.n_dofs)
+    out = dg.apply(torch.tensor(u, device="cuda", dtype=torch.float32), prec=1)
+    ref = p.apply(u.astype(np.float32).astype(np.float64))
+    assert np.linalg.norm(out.double().cpu().numpy() - ref) <= TOL32 * np.linalg.norm(p.apply_abs(u))
     dg.close()
 
 
