@@ -229,6 +229,34 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
 dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream);
 
 /*
+ * The integrals of dg_integrals() for callers that cannot allocate device
+ * memory -- for example code that runs while a CUDA graph is being captured,
+ * code inside a framework whose allocator owns all device memory, or a long
+ * run that must not call cudaMalloc after start-up (it synchronises the
+ * device and can fail on a fragmented heap).  It needs no handle and calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
+ * array of 98,328 bytes compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart to this entry point.
+ *
+ * u: device vector of n_cells * (degree+1)^dim FP64 values in the layout of
+ * this header (16-byte aligned); det_jacobian: |J| of every cell
+ * (dg_info.det_jacobian); out: host array of 3 doubles, receives
+ * (int u, int u^2, max |u_i|).  At most 2^32 DoFs per call: larger vectors
+ * are rejected with DG_ERR_INVALID_ARG (use dg_integrals).  Synchronises
+ * ``stream``.
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the one array and a call
+ * leaves its partial sums there; calls that overlap on the GPU (for instance
+ * on two streams at once) race on it, so serialise them.  Every slot a call
+ * reads is written by that call first, so nothing needs clearing.
+ */
+dg_status dg_integrals_noalloc(const double* u, long long n_cells, int dim, int degree,
+                               double det_jacobian, double* out, void* stream);
+
+/*
  * Synchronise ``stream`` and report device-side errors latched since the
  * last check: DG_ERR_TIMEOUT if a kernel's bounded wait for an asynchronous
  * copy gave up (its results are invalid), else DG_ERR_NONFINITE if any kernel

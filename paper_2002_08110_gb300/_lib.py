@@ -76,6 +76,7 @@ def load():
         "dg_rk_stage": (i, [vp, vp, vp, vp, i, d, i, i, vp]),
         "dg_rk_step": (i, [vp, vp, vp, vp, d, i, i, i, vp]),
         "dg_integrals": (i, [vp, vp, c_double_p, vp]),
+        "dg_integrals_noalloc": (i, [vp, ll, i, i, d, c_double_p, vp]),
         "dg_check": (i, [vp, vp]),
         "dg_get_launch": (i, [vp, i, ctypes.POINTER(Launch)]),
         "dg_set_launch": (i, [vp, i, ctypes.POINTER(Launch)]),

@@ -328,6 +328,8 @@ dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
 
 namespace dg {
 
+dg_status report(dg_status s, const char* msg) { return fail(s, "%s", msg); }
+
 size_t generic_smem_bytes(int d, int n, int combo, int cells_per_block) {
   const size_t tb = combo == kDDD ? 8 : 4;
   const size_t b = static_cast<size_t>(ipow(n, d)) * tb * 2 * cells_per_block;

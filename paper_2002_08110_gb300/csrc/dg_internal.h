@@ -106,6 +106,9 @@ cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStr
 // Uploads the n = 4 tables of the specialised kernel (they depend on n only).
 cudaError_t init_cell6d_tables(const Tab1D<float>& t);
 
+// Records the thread's last-error message and returns s (dg_api.cu).
+dg_status report(dg_status s, const char* msg);
+
 // Small kernels (dg_misc.cu).
 cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s);
 cudaError_t launch_integrals(const KParams& p, int n, const double* u, double* partial,
