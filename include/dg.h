@@ -296,6 +296,17 @@ dg_status dg_batch_rk_step(dg_batch b, double* const* u, void* const* w0, void* 
                            const double* dt, int nsteps, int prec, void* stream);
 /* Number of work tiles and total DoFs of a batch (host outputs, may be NULL). */
 dg_status dg_batch_info(dg_batch b, long long* tiles, long long* n_dofs);
+/* dg_check for a batch: synchronise and report non-finite results. */
+dg_status dg_batch_check(dg_batch b, void* stream);
+/* Tile size (DoFs per work tile, whole cells, >= one cell) and threads per
+ * block of the batched kernel (defaults 4096 and 256). */
+dg_status dg_batch_set_launch(dg_batch b, int tile_dofs, int threads);
+/* Autotuner of the batched launch: times one LSRK step for each candidate
+ * tile size and block size on the caller's vectors (which are advanced by
+ * those steps) and keeps the fastest; best_ms (may be NULL) receives its time
+ * per step. */
+dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void* const* w1,
+                            const double* dt, int prec, void* stream, double* best_ms);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,7 @@ autograd wrapper of the adjoint.
 """
 from ._lib import PREC_FP32, PREC_FP64, PREC_MIXED, DGError  # noqa: F401
 
-__all__ = ["DG", "DGError", "PREC_FP64", "PREC_FP32", "PREC_MIXED", "reference_nodes",
+__all__ = ["DG", "DGBatch", "DGError", "PREC_FP64", "PREC_FP32", "PREC_MIXED", "reference_nodes",
            "build_library"]
 
 
@@ -21,10 +21,10 @@ def build_library(verbose=False):
 
 def __getattr__(name):
     # torch-dependent parts are imported lazily
-    if name in ("DG", "reference_nodes", "from_spec"):
+    if name in ("DG", "DGBatch", "reference_nodes", "from_spec"):
         from . import api
         return getattr(api, name)
-    if name in ("MisfitGradient", "adjoint_gradient", "RKForward"):
+    if name in ("RKForward", "final_state", "misfit_gradient", "CheckpointMismatch"):
         from . import autograd
         return getattr(autograd, name)
     raise AttributeError(name)

@@ -86,6 +86,10 @@ def load():
         "dg_batch_rk_step": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                  c_double_p, i, i, vp]),
         "dg_batch_info": (i, [vp, ctypes.POINTER(ll), ctypes.POINTER(ll)]),
+        "dg_batch_check": (i, [vp, vp]),
+        "dg_batch_set_launch": (i, [vp, i, i]),
+        "dg_batch_autotune": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                  c_double_p, i, vp, c_double_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -186,3 +186,62 @@ class DG:
 def from_spec(spec, e_nodes=None):
     """Build a DG from a plain description (dict with the constructor's keys)."""
     return DG(e_nodes=e_nodes, **spec)
+
+
+class DGBatch:
+    """Independent constant-velocity problems (d = 3 or 4) advanced together:
+    one persistent launch per LSRK stage over all members, replayed from a
+    CUDA graph.  The member handles stay owned by the caller."""
+
+    def __init__(self, members):
+        self.lib = _lib.load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.handle for m in self.members])
+        h = ctypes.c_void_p()
+        check(self.lib.dg_batch_create(len(self.members), arr, ctypes.byref(h)))
+        self.handle = h
+        tiles, nd = ctypes.c_longlong(), ctypes.c_longlong()
+        check(self.lib.dg_batch_info(self.handle, ctypes.byref(tiles), ctypes.byref(nd)))
+        self.tiles, self.n_dofs = int(tiles.value), int(nd.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.dg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arrays(self, us, w0s, w1s, dts, prec):
+        n = len(self.members)
+        if not (len(us) == len(w0s) == len(w1s) == len(dts) == n):
+            raise ValueError("one u, w0, w1 and dt per member")
+        for m, u, a, b in zip(self.members, us, w0s, w1s):
+            m._vec(u, PREC_FP64, "u")
+            m._vec(a, prec, "w0")
+            m._vec(b, prec, "w1")
+        U = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+        A = (ctypes.c_void_p * n)(*[w.data_ptr() for w in w0s])
+        B = (ctypes.c_void_p * n)(*[w.data_ptr() for w in w1s])
+        D = (ctypes.c_double * n)(*[float(x) for x in dts])
+        return U, A, B, D
+
+    def rk_step(self, us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32):
+        U, A, B, D = self._arrays(us, w0s, w1s, dts, prec)
+        check(self.lib.dg_batch_rk_step(self.handle, U, A, B, D, int(nsteps), prec, _stream()))
+
+    def set_launch(self, tile_dofs, threads):
+        check(self.lib.dg_batch_set_launch(self.handle, int(tile_dofs), int(threads)))
+
+    def autotune(self, us, w0s, w1s, dts, prec=PREC_FP32):
+        U, A, B, D = self._arrays(us, w0s, w1s, dts, prec)
+        best = ctypes.c_double()
+        check(self.lib.dg_batch_autotune(self.handle, U, A, B, D, prec, _stream(),
+                                         ctypes.byref(best)))
+        return float(best.value)
+
+    def check(self):
+        check(self.lib.dg_batch_check(self.handle, _stream()))

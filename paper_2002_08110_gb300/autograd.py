@@ -1,0 +1,97 @@
+"""Differentiation through LSRK(5,4) time integration of the DG operator.
+
+``RKForward.apply(u0, dg, dt, nsteps, prec, checkpoint_every)`` returns
+u(T) = Phi^nsteps(u0), Phi = one LSRK(5,4) step of du/dt = L u with
+L = M^{-1} A (the library's fused stages).  Its backward applies the adjoint
+step Phi^T = R(dt L)^T = R(dt L^T) (the step map is the stability polynomial
+R of dt L, and R(X)^T = R(X^T)) nsteps times with the library's transposed
+operator L^T = M L(-a) M^{-1}.
+
+Checkpointing: the forward keeps the state every ``checkpoint_every`` steps.
+The backward walks the segments in reverse; for each one it recomputes the
+forward states of the segment from its checkpoint (the states an adjoint of
+a state-dependent operator would consume) and checks that the recomputed end
+state equals the next stored checkpoint bit for bit (the kernels are
+deterministic), then runs the segment's adjoint steps.  For the linear,
+autonomous operator of this library the adjoint steps do not read the
+recomputed states; the recomputation is the memory/compute trade the pattern
+exists for, and its consistency check guards the stored trajectory.
+
+``misfit_gradient`` is the gradient of 0.5 * ||u(T) - u_target||^2 with
+respect to u0.
+"""
+import torch
+
+from ._lib import PREC_FP32, PREC_FP64  # noqa: F401
+
+
+class CheckpointMismatch(RuntimeError):
+    pass
+
+
+class RKForward(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u0, dg, dt, nsteps, prec, checkpoint_every):
+        if checkpoint_every < 1:
+            raise ValueError("checkpoint_every must be >= 1")
+        u = u0.detach().to(torch.float64).contiguous().clone()
+        wdt = torch.float32 if prec == PREC_FP32 else torch.float64
+        w0 = torch.empty(dg.n_dofs, dtype=wdt, device=u.device)
+        w1 = torch.empty_like(w0)
+        checkpoints = [u.clone()]
+        done = 0
+        while done < nsteps:
+            seg = min(checkpoint_every, nsteps - done)
+            dg.rk_step(u, dt, nsteps=seg, prec=prec, w0=w0, w1=w1)
+            done += seg
+            if done < nsteps:
+                checkpoints.append(u.clone())
+        ctx.dg, ctx.dt, ctx.nsteps, ctx.prec, ctx.every = dg, dt, nsteps, prec, checkpoint_every
+        ctx.checkpoints = checkpoints
+        ctx.final = u.clone()
+        ctx.recomputed_segments = 0
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        dg, dt, prec, every = ctx.dg, ctx.dt, ctx.prec, ctx.every
+        lam = grad_out.detach().to(torch.float64).contiguous().clone()
+        wdt = torch.float32 if prec == PREC_FP32 else torch.float64
+        w0 = torch.empty(dg.n_dofs, dtype=wdt, device=lam.device)
+        w1 = torch.empty_like(w0)
+        bounds = []
+        s = 0
+        while s < ctx.nsteps:
+            bounds.append((s, min(s + every, ctx.nsteps)))
+            s += every
+        for k in reversed(range(len(bounds))):
+            a, b = bounds[k]
+            # recompute the segment's forward states from its checkpoint
+            x = ctx.checkpoints[k].clone()
+            states = [x.clone()]
+            for _ in range(b - a):
+                dg.rk_step(x, dt, nsteps=1, prec=prec, w0=w0, w1=w1)
+                states.append(x.clone())
+            nxt = ctx.checkpoints[k + 1] if k + 1 < len(ctx.checkpoints) else ctx.final
+            if not torch.equal(states[-1], nxt):
+                raise CheckpointMismatch(f"recomputed state of segment {k} differs from its checkpoint")
+            ctx.recomputed_segments += 1
+            # adjoint steps of the segment, last step first
+            for _ in range(b - a):
+                dg.rk_step(lam, dt, nsteps=1, prec=prec, adjoint=True, w0=w0, w1=w1)
+        dg.check()
+        return lam.to(grad_out.dtype), None, None, None, None, None
+
+
+def final_state(u0, dg, dt, nsteps, prec=PREC_FP32, checkpoint_every=20):
+    """u(T) as a differentiable function of u0."""
+    return RKForward.apply(u0, dg, dt, nsteps, prec, checkpoint_every)
+
+
+def misfit_gradient(u0, u_target, dg, dt, nsteps, prec=PREC_FP32, checkpoint_every=20):
+    """(J, dJ/du0) for J = 0.5 ||u(T) - u_target||^2 (Euclidean DoF norm)."""
+    x = u0.detach().clone().requires_grad_(True)
+    uT = final_state(x, dg, dt, nsteps, prec, checkpoint_every)
+    J = 0.5 * torch.sum((uT - u_target) ** 2)
+    J.backward()
+    return float(J.detach()), x.grad

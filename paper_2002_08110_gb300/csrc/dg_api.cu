@@ -330,6 +330,11 @@ namespace dg {
 
 dg_status report(dg_status s, const char* msg) { return fail(s, "%s", msg); }
 
+void lsrk_coefficients(double* a4, double* b5) {
+  for (int i = 0; i < 4; ++i) a4[i] = kRkA[i];
+  for (int i = 0; i < 5; ++i) b5[i] = kRkB[i];
+}
+
 size_t generic_smem_bytes(int d, int n, int combo, int cells_per_block) {
   const size_t tb = combo == kDDD ? 8 : 4;
   const size_t b = static_cast<size_t>(ipow(n, d)) * tb * 2 * cells_per_block;

@@ -108,6 +108,8 @@ cudaError_t init_cell6d_tables(const Tab1D<float>& t);
 
 // Records the thread's last-error message and returns s (dg_api.cu).
 dg_status report(dg_status s, const char* msg);
+// LSRK(5,4) coefficients a_1..a_4 and b_1..b_5 (dg_api.cu).
+void lsrk_coefficients(double* a4, double* b5);
 
 // Small kernels (dg_misc.cu).
 cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s);

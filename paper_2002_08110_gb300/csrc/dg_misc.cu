@@ -1,4 +1,5 @@
 // Small kernels: stage-vector initialisation and the quadrature integrals.
+#include "dg_convert.cuh"
 #include "dg_internal.h"
 
 namespace dg {
@@ -7,7 +8,7 @@ template <typename TW>
 __global__ void k_convert(const double* __restrict__ u, TW* __restrict__ w, long long n) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
-    w[i] = static_cast<TW>(u[i]);
+    w[i] = cvt<TW>(u[i]);  // the same rounding as the fused stages' FP32 stage vectors
 }
 
 cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s) {
