@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-reps", type=int, default=2)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 2D, 4D, batched and adjoint configurations")
     ap.add_argument("--step-kind", default="stage",
                     choices=["stage", "apply_fp32", "apply_fp32_fp64io", "apply_fp64"],
                     help="what one timed step is (default: the fused LSRK stage)")
@@ -259,6 +261,114 @@ def reference_arm(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+# the other workloads (2D, 4D, batched, adjoint)
+# ---------------------------------------------------------------------------
+def _timed(torch, fn, reps):
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_configs(torch, hbm_peak):
+    """Throughput of the other synthetic workloads, GDoF/s per LSRK stage
+    (each stage = one operator application fused with the state update)."""
+    import workloads as W
+    from paper_2002_08110_gb300 import DG, DGBatch, PREC_FP32, PREC_FP64, reference_nodes
+    from paper_2002_08110_gb300.autograd import misfit_gradient
+    out = {}
+
+    def make(w):
+        zeta, _ = reference_nodes(w.k)
+        return DG(e_nodes=W.e_table(w, zeta), **W.dg_kwargs(w)), zeta
+
+    def stage_entry(dg, ms_step, prec):
+        bpd = 32 if prec == PREC_FP64 else 24
+        st = ms_step / 5
+        gbs = bpd * dg.n_dofs / (st * 1e-3) / 1e9
+        return {"ms_per_step": ms_step, "GDoF/s_per_stage": dg.n_dofs / (st * 1e-3) / 1e9,
+                "frac_hbm": gbs / hbm_peak, "bytes_per_dof": bpd}
+
+    # 2D: one period (T = 2, 240 steps), FP64
+    w = W.config_2d()
+    dg, zeta = make(w)
+    dt, steps = W.time_step(w)
+    u = W.separable_state(w, zeta, xp=torch, device="cuda")
+    ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=PREC_FP64), 1)
+    dg.check()
+    out["2d"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                 **stage_entry(dg, ms / steps, PREC_FP64)}
+    dg.close()
+
+    # 4D sheared phase space: 200 steps, FP64 and FP32 sweeps / FP64 state
+    w = W.config_4d()
+    dg, zeta = make(w)
+    dt, steps = W.time_step(w)
+    u0 = torch.tensor(W.initial_state(w, zeta), device="cuda")
+    for prec, name in ((PREC_FP64, "4d_fp64"), (PREC_FP32, "4d_fp32_fp64state")):
+        u = u0.clone()
+        dg.rk_step(u, dt, nsteps=1, prec=prec)
+        ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=prec), 1)
+        dg.check()
+        out[name] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                     **stage_entry(dg, ms / steps, prec)}
+    dg.close()
+    del u0, u
+
+    # batched: 64 instances, one persistent launch per stage, autotuned
+    ws = W.batched_instances()
+    dgs = [DG(**W.dg_kwargs(w)) for w in ws]
+    batch = DGBatch(dgs)
+    us = [W.separable_state(w, reference_nodes(w.k)[0], xp=torch, device="cuda") for w in ws]
+    w0s = [torch.empty(w.n_dofs, device="cuda", dtype=torch.float32) for w in ws]
+    w1s = [torch.empty(w.n_dofs, device="cuda", dtype=torch.float32) for w in ws]
+    dts = [W.time_step(w)[0] for w in ws]
+    best = batch.autotune(us, w0s, w1s, dts, prec=PREC_FP32)
+    reps = 4
+    ms = _timed(torch, lambda: batch.rk_step(us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32), reps)
+    batch.check()
+    st = ms / 5
+    out["batched"] = {"workload": "64 instances, d in {3,4}, k in {2..5}, 8..24 cells/dir",
+                      "dofs": batch.n_dofs, "tiles": batch.tiles, "ms_per_step": ms,
+                      "GDoF/s_per_stage": batch.n_dofs / (st * 1e-3) / 1e9,
+                      "frac_hbm": 24 * batch.n_dofs / (st * 1e-3) / 1e9 / hbm_peak,
+                      "autotuned_ms_per_step": best}
+    batch.close()
+    for dg in dgs:
+        dg.close()
+    del us, w0s, w1s
+
+    # adjoint: gradient of the final-time misfit over 200 steps, checkpoints every 20
+    w = W.config_adjoint()
+    dg, zeta = make(w)
+    dt, steps = W.time_step(w)
+    u0 = torch.tensor(W.separable_state(w, zeta), device="cuda")
+    tgt = u0 + torch.tensor(W.noise(w), device="cuda")
+    dg.rk_step(tgt, dt, nsteps=steps, prec=PREC_FP32)
+    every = w.extra["checkpoint_every"]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    J, g = misfit_gradient(u0, tgt, dg, dt, steps, prec=PREC_FP32, checkpoint_every=every)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # forward (200) + recomputation (200) + adjoint (200) steps
+    out["adjoint"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                      "checkpoint_every": every, "ms_total": ms, "misfit": J,
+                      "grad_norm": float(torch.linalg.vector_norm(g)),
+                      "GDoF/s_per_stage": 3 * steps * 5 * dg.n_dofs / (ms * 1e-3) / 1e9}
+    dg.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -393,6 +503,12 @@ def main():
                "ms_per_step": ms}
         del h_w, h_u
 
+    others = None
+    if not args.no_configs:
+        del u0, u, w0, w1
+        torch.cuda.empty_cache()
+        others = measure_configs(torch, hbm_peak)
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         res = oracle_sample(args.cells, 1000, 1)
@@ -416,6 +532,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
             "variants": variants,
+            "configs": others,
             "launch": dg.get_launch(PREC_FP32),
         }
         print(json.dumps(line), flush=True)

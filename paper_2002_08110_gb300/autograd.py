@@ -9,9 +9,9 @@ operator L^T = M L(-a) M^{-1}.
 
 Checkpointing: the forward keeps the state every ``checkpoint_every`` steps.
 The backward walks the segments in reverse; for each one it recomputes the
-forward states of the segment from its checkpoint (the states an adjoint of
-a state-dependent operator would consume) and checks that the recomputed end
-state equals the next stored checkpoint bit for bit (the kernels are
+segment forward from its checkpoint (where an adjoint of a state-dependent
+operator would take its states) and checks that the recomputed end state
+equals the next stored checkpoint bit for bit (the kernels are
 deterministic), then runs the segment's adjoint steps.  For the linear,
 autonomous operator of this library the adjoint steps do not read the
 recomputed states; the recomputation is the memory/compute trade the pattern
@@ -64,21 +64,20 @@ class RKForward(torch.autograd.Function):
         while s < ctx.nsteps:
             bounds.append((s, min(s + every, ctx.nsteps)))
             s += every
+        x = torch.empty_like(lam)
         for k in reversed(range(len(bounds))):
             a, b = bounds[k]
-            # recompute the segment's forward states from its checkpoint
-            x = ctx.checkpoints[k].clone()
-            states = [x.clone()]
-            for _ in range(b - a):
-                dg.rk_step(x, dt, nsteps=1, prec=prec, w0=w0, w1=w1)
-                states.append(x.clone())
+            # recompute the segment from its checkpoint (one graph-replayed
+            # call); its end state must reproduce the next checkpoint exactly
+            x.copy_(ctx.checkpoints[k])
+            dg.rk_step(x, dt, nsteps=b - a, prec=prec, w0=w0, w1=w1)
             nxt = ctx.checkpoints[k + 1] if k + 1 < len(ctx.checkpoints) else ctx.final
-            if not torch.equal(states[-1], nxt):
+            if not torch.equal(x, nxt):
                 raise CheckpointMismatch(f"recomputed state of segment {k} differs from its checkpoint")
             ctx.recomputed_segments += 1
-            # adjoint steps of the segment, last step first
-            for _ in range(b - a):
-                dg.rk_step(lam, dt, nsteps=1, prec=prec, adjoint=True, w0=w0, w1=w1)
+            # the segment's adjoint steps (identical steps R(dt L^T) for this
+            # autonomous operator, so one call runs all of them)
+            dg.rk_step(lam, dt, nsteps=b - a, prec=prec, adjoint=True, w0=w0, w1=w1)
         dg.check()
         return lam.to(grad_out.dtype), None, None, None, None, None
 

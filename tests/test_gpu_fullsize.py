@@ -1,0 +1,165 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times, on sampled cells the oracle evaluates one by one, and an
+invariant that holds at any size.
+
+6D: 8^6 cells, k = 3 (1.07e9 DoFs), the specialised kernel: fused LSRK stage
+(FP32 sweeps, FP32 stage vector, FP64 state), FP32 apply and FP64-I/O apply.
+4D: 16^4 cells, sheared, FP64 apply.  5D adjoint workload: L^T on a sampled
+cell against the oracle's transposed blocks.  Mass conservation of FP64 steps
+on the full 6D mesh.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W  # noqa: E402
+from dg_helpers import oracle_for  # noqa: E402
+from oracle import lsrk  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as entry
+    entry.build()
+
+
+class DeviceVector:
+    """Read-only view of a device tensor for the oracle: slices are copied to
+    the host on demand, so only the cells the oracle touches move."""
+
+    def __init__(self, t):
+        self.t = t
+        self.shape = (t.numel(),)
+
+    def __getitem__(self, s):
+        return self.t[s].double().cpu().numpy()
+
+
+def _sample_cells(p, count, seed):
+    rng = np.random.default_rng(seed)
+    cells = set(int(c) for c in rng.choice(p.ncells, size=count, replace=False))
+    cells.add(0)                    # a corner cell (periodic wrap in every direction)
+    cells.add(p.ncells - 1)
+    return sorted(cells)
+
+
+def _oracle_cells(p, u, cells):
+    K = [p.apply_mass_inverse(p.cell_residual(u, e)).reshape(-1, order="F") for e in cells]
+    S = [p.apply_mass_inverse(p.cell_residual(u, e, absolute=True)).reshape(-1, order="F")
+         for e in cells]
+    return K, S
+
+
+@pytest.fixture(scope="module")
+def six():
+    from paper_2002_08110_gb300 import DG, reference_nodes
+    w = W.config_6d()
+    zeta, _ = reference_nodes(w.k)
+    dg = DG(e_nodes=W.e_table(w, zeta), **W.dg_kwargs(w))
+    assert dg.info.uniform_sides == 1          # the specialised kernel runs
+    # the oracle evaluates the same field and state functions at its own nodes
+    p = oracle_for(w)
+    u = W.separable_state(w, zeta, xp=torch, device="cuda")
+    yield w, dg, p, u
+    dg.close()
+
+
+def test_6d_fused_stage_sampled(six):
+    from paper_2002_08110_gb300 import PREC_FP32
+    w, dg, p, u = six
+    npc = p.dofs_per_cell
+    dt, _ = W.time_step(w)
+    w_in = u.float()
+    w_out = torch.empty_like(w_in)
+    uu = u.clone()
+    stage = 1
+    dg.rk_stage(w_in, w_out, uu, stage, dt, prec=PREC_FP32)
+    dg.check()
+    cells = _sample_cells(p, 3, seed=0)
+    K, S = _oracle_cells(p, DeviceVector(w_in), cells)
+    for e, Ke, Se in zip(cells, K, S):
+        sl = slice(e * npc, (e + 1) * npc)
+        u_old = u[sl].cpu().numpy()
+        u_ref = u_old + lsrk.B[stage] * dt * Ke
+        w_ref = u_old + lsrk.A[stage] * dt * Ke
+        err_u = np.abs(uu[sl].cpu().numpy() - u_ref)
+        err_w = np.abs(w_out[sl].double().cpu().numpy() - w_ref)
+        assert np.linalg.norm(err_u) <= 1e-5 * dt * np.linalg.norm(Se) + 1e-15 * np.linalg.norm(u_old)
+        assert np.all(err_w <= 1e-5 * dt * np.abs(Se).max() + 2.5e-7 * (np.abs(u_old) + np.abs(
+            lsrk.A[stage] * dt * Ke)) + 1e-30)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_6d_apply_sampled(six, prec):
+    w, dg, p, u = six
+    npc = p.dofs_per_cell
+    src = u.float() if prec == 1 else u
+    out = dg.apply(src, prec=prec)
+    dg.check()
+    cells = _sample_cells(p, 3, seed=1)
+    K, S = _oracle_cells(p, DeviceVector(src), cells)
+    for e, Ke, Se in zip(cells, K, S):
+        got = out[e * npc:(e + 1) * npc].double().cpu().numpy()
+        assert np.linalg.norm(got - Ke) <= 1e-5 * np.linalg.norm(Se)
+
+
+def test_6d_mass_conserved_fp64(six):
+    from paper_2002_08110_gb300 import PREC_FP64
+    w, dg, p, u = six
+    dt, _ = W.time_step(w)
+    x = u.clone()
+    m0, l0, _ = dg.integrals(x)
+    dg.rk_step(x, dt, nsteps=1, prec=PREC_FP64)
+    dg.check()
+    m1, l1, _ = dg.integrals(x)
+    assert abs(m1 - m0) <= 1e-12 * abs(m0)
+    assert l1 <= l0 * (1 + 1e-13)
+
+
+def test_4d_fullsize_apply_sampled():
+    from paper_2002_08110_gb300 import DG, PREC_FP64, reference_nodes
+    w = W.config_4d()
+    zeta, _ = reference_nodes(w.k)
+    dg = DG(e_nodes=W.e_table(w, zeta), **W.dg_kwargs(w))
+    p = oracle_for(w)
+    u = torch.tensor(W.initial_state(w, zeta), device="cuda")
+    out = dg.apply(u, prec=PREC_FP64)
+    dg.check()
+    npc = p.dofs_per_cell
+    cells = _sample_cells(p, 20, seed=2)
+    K, _ = _oracle_cells(p, DeviceVector(u), cells)
+    for e, Ke in zip(cells, K):
+        got = out[e * npc:(e + 1) * npc].cpu().numpy()
+        assert np.linalg.norm(got - Ke) <= 1e-12 * np.linalg.norm(Ke)
+    dg.close()
+
+
+def test_5d_adjoint_fullsize_sampled():
+    from paper_2002_08110_gb300 import DG, PREC_FP32, reference_nodes
+    w = W.config_adjoint()
+    zeta, _ = reference_nodes(w.k)
+    dg = DG(e_nodes=W.e_table(w, zeta), **W.dg_kwargs(w))
+    p = oracle_for(w)
+    y = torch.tensor(W.initial_state(w, zeta), device="cuda", dtype=torch.float32)
+    out = dg.apply_adjoint(y, prec=PREC_FP32)
+    dg.check()
+    npc = p.dofs_per_cell
+    yv = DeviceVector(y)
+    e = 12345
+    rows = {e} | {p.neighbour(e, j, s) for j in range(p.d) for s in (1, -1)}
+    ref = np.zeros(npc)
+    scale = np.zeros(npc)
+    for r in rows:
+        blocks = p.dense_cell_blocks(r)
+        if e in blocks:
+            yr = yv[slice(r * npc, (r + 1) * npc)]
+            ref += blocks[e].T @ yr
+            scale += np.abs(blocks[e].T) @ np.abs(yr)
+    got = out[e * npc:(e + 1) * npc].double().cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 4e-5 * np.linalg.norm(scale)
+    dg.close()
