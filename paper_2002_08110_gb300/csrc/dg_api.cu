@@ -107,6 +107,7 @@ KParams base_params(const dg_ctx* h, int prec) {
   p.cv_tab = f ? static_cast<const void*>(h->cv_d32) : static_cast<const void*>(h->cv_d64);
   p.scratch = h->scratch;
   p.err = h->err_d;
+  p.work = h->work_d;
   p.t64 = h->tables.t64;
   p.t32 = h->tables.t32;
   return p;
@@ -238,6 +239,7 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->cv_d64);
   cudaFree(h->cv_d32);
   cudaFree(h->err_d);
+  cudaFree(h->work_d);
   cudaFree(h->scratch);
   cudaFree(h->partial);
   delete h;
@@ -491,6 +493,7 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
       (e = upload(h->cv_host, &h->cv_d32)) != cudaSuccess ||
       (e = cudaMalloc(&h->err_d, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(h->err_d, 0, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&h->work_d, 16 * sizeof(unsigned))) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     free_ctx(h);
     return cuda_fail(e, "dg_create");

@@ -76,12 +76,19 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
+// L2 policy that keeps the stage vector resident: every cell of it is read
+// by up to six downstream neighbours after its own block has read it.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         unsigned long long* bar) {
+                                         unsigned long long* bar, unsigned long long pol) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
 // Orders this thread's earlier generic-proxy accesses of shared memory before
@@ -157,23 +164,17 @@ __constant__ float c_G[2][16];
 __constant__ float c_Ln[2][4];
 __constant__ float c_lw[2][4];
 
-// One direction J of the thread's block: traces of the upwind neighbour's 16
-// lines from the landing buffer, then the 16 line contractions.  The upwind
-// side is chosen at run time; the 1D matrices of that side (scaled by c) are
-// held in registers so that one body serves both signs.
+// Traces, on the shared face, of the upwind neighbour's 16 lines along local
+// direction J, read from a landing buffer (row or column view).  With the
+// adjoint the neighbour values are scaled by M^{-1}: the element factor here,
+// the thread factor by the caller (tscale of lines_dir).
 template <int J, bool ROWS, bool ADJ>
-__device__ __forceinline__ void direction(float (&r)[64], const float (&u)[64], const float* nbv,
-                                          float c, float wthread, const Tab1D<float>& T) {
+__device__ __forceinline__ void nb_traces(float (&tr)[16], const float* nbv, float c,
+                                          const Tab1D<float>& T) {
   const int side = c > 0.f ? 0 : 1;
-  float lw[4], Ln[4], G[16];
+  float lw[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    lw[i] = c_lw[side][i];
-    Ln[i] = c * c_Ln[side][i];
-  }
-#pragma unroll
-  for (int i = 0; i < 16; ++i) G[i] = c * c_G[side][i];
-  float tr[16];
+  for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
 #pragma unroll
   for (int i = 0; i < 16; ++i) tr[i] = 0.f;
 #pragma unroll
@@ -191,11 +192,44 @@ __device__ __forceinline__ void direction(float (&r)[64], const float (&u)[64], 
         tr[l1 + 4 * l2] = fmaf(lw[pp], x, tr[l1 + 4 * l2]);
       }
     }
+}
+
+// Traces of the thread's own 16 lines along J on the outflow face: for the
+// cell downstream they are exactly the inflow traces of its upwind neighbour.
+template <int J>
+__device__ __forceinline__ void own_traces(float (&tr)[16], const float (&u)[64], float c) {
+  const int side = c > 0.f ? 0 : 1;
+  float lw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
 #pragma unroll
   for (int l2 = 0; l2 < 4; ++l2)
 #pragma unroll
     for (int l1 = 0; l1 < 4; ++l1) {
-      const float t = ADJ ? wthread * tr[l1 + 4 * l2] : tr[l1 + 4 * l2];
+      float s = 0.f;
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) s = fmaf(lw[pp], u[eidx<J>(l1, l2, pp)], s);
+      tr[l1 + 4 * l2] = s;
+    }
+}
+
+// The 16 line contractions of direction J: r += c (G u + L_nb t_nb).  The
+// upwind side is chosen at run time; the 1D matrices of that side (scaled by
+// c) come from constant memory into registers, so one body serves both signs.
+template <int J>
+__device__ __forceinline__ void lines_dir(float (&r)[64], const float (&u)[64],
+                                          const float (&tr)[16], float c, float tscale) {
+  const int side = c > 0.f ? 0 : 1;
+  float Ln[4], G[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) G[i] = c * c_G[side][i];
+#pragma unroll
+  for (int l2 = 0; l2 < 4; ++l2)
+#pragma unroll
+    for (int l1 = 0; l1 < 4; ++l1) {
+      const float t = tscale * tr[l1 + 4 * l2];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float acc = fmaf(Ln[q], t, r[eidx<J>(l1, l2, q)]);
@@ -204,6 +238,14 @@ __device__ __forceinline__ void direction(float (&r)[64], const float (&u)[64], 
         r[eidx<J>(l1, l2, q)] = acc;
       }
     }
+}
+
+template <int J, bool ROWS, bool ADJ>
+__device__ __forceinline__ void direction(float (&r)[64], const float (&u)[64], const float* nbv,
+                                          float c, float wthread, const Tab1D<float>& T) {
+  float tr[16];
+  nb_traces<J, ROWS, ADJ>(tr, nbv, c, T);
+  lines_dir<J>(r, u, tr, c, ADJ ? wthread : 1.f);
 }
 
 struct Pipe {
@@ -220,12 +262,13 @@ struct Mover {
   float* sm;
   Pipe* pp;
   unsigned phase = 0;  // parity bit per buffer
+  unsigned long long pol = l2_evict_last();
 
   __device__ __forceinline__ void issue(int b, const TIN* cellp, int t) {
     float* d = sm + b * kCellSmem + t * kPad;
     if constexpr (sizeof(TIN) == 4) {
       if (t == 0) mbar_expect_tx(&pp->bar[b], 4096 * 4);
-      bulk_g2s(d, cellp + t * 64, 256, &pp->bar[b]);
+      bulk_g2s(d, cellp + t * 64, 256, &pp->bar[b], pol);
     } else {
       const TIN* g = cellp + t * 64;
 #pragma unroll
@@ -254,26 +297,30 @@ template <typename TIN, typename TW, bool ADJ>
 __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
   extern __shared__ __align__(128) float sm6[];
   __shared__ Pipe pipe;
+  __shared__ unsigned s_item;
   const int t = threadIdx.x;
   const Tab1D<float>& T = p.t32;
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
-  const unsigned ncells = static_cast<unsigned>(p.ncells);
   const unsigned ncx = static_cast<unsigned>(p.ncx);
+  const unsigned S3 = static_cast<unsigned>(p.cstride[5]);   // pencils along v3
+  const int N3 = p.ncell[5];
+  const unsigned npencils = S3;
   const float winv_t = ADJ ? wprod(T.winv, t) : 1.f;
   const float w_t = ADJ ? wprod(T.w, t) : 1.f;
+  // the thread's outflow traces along v3, carried to the next cell of the pencil
+  float* carried = sm6 + 3 * kCellSmem + t * 17;
   int bad = 0;
 
-  unsigned cell = blockIdx.x;
-  if (cell >= ncells) return;
   if (t == 0) {
     for (int b = 0; b < kNumBuf; ++b) mbar_init(&pipe.bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_item = atomicAdd(p.work, 1u);
   }
   __syncthreads();
+  unsigned item = s_item;
+  if (item >= npencils) return;
   Mover<TIN> mv{sm6, &pipe};
   auto cellp = [&](unsigned c) { return src + static_cast<size_t>(c) * 4096; };
-  // speeds and upwind neighbours (x speeds depend on the v node t, v speeds
-  // on the x node t; the upwind side is the same for all threads)
   auto setup = [&](unsigned c, float (&sp)[6], unsigned (&nbr)[6]) {
     const unsigned cv = c / ncx, cx = c - cv * ncx;
     const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * 64 + t) * 3;
@@ -290,22 +337,48 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
       nbr[j] = nb32(p, c, j, sp[j] > 0.f ? -1 : 1);
     }
   };
+  // v3 direction of a pencil (the same for all its cells and threads)
+  auto pencil_forward = [&](unsigned it) {
+    const unsigned cx = it % ncx;
+    float c5 = static_cast<const float*>(p.cv_tab)[(static_cast<size_t>(cx) * 64) * 3 + 2];
+    if (ADJ) c5 = -c5;
+    return c5 >= 0.f;
+  };
+  auto pencil_cell = [&](unsigned it, int i, bool fwd) {
+    return it + static_cast<unsigned>(fwd ? i : N3 - 1 - i) * S3;
+  };
 
-  // buffers: A = 0 holds the current cell, B = 1 and C = 2 are landing
-  // buffers; the next cell lands in A once phase V has its values in
-  // registers.
-  constexpr int A = 0, B = 1, C = 2;
+  // buffers: A = 0 holds the current cell, P and Q (1 and 2) are landing
+  // buffers holding the x1 and x2 neighbours at the top of an iteration
+  constexpr int A = 0;
+  int P = 1, Q = 2;
+  bool fwd = pencil_forward(item);
+  int i = 0;
+  unsigned cell = pencil_cell(item, 0, fwd);
   float sp[6];
   unsigned nbr[6];
   setup(cell, sp, nbr);
   mv.issue(A, cellp(cell), t);
-  mv.issue(B, cellp(nbr[0]), t);
-  mv.issue(C, cellp(nbr[1]), t);
+  mv.issue(P, cellp(nbr[0]), t);
+  mv.issue(Q, cellp(nbr[1]), t);
   bool ok = true;
+  __syncthreads();
+  if (t == 0) s_item = atomicAdd(p.work, 1u);      // the item after this pencil
+  __syncthreads();
 
   for (;;) {
-    const unsigned next = cell + gridDim.x;
-    const bool has_next = next < ncells;
+    // next cell: along the pencil, else the first cell of the next item
+    unsigned next_item = item;
+    bool next_fwd = fwd;
+    int next_i = i + 1;
+    if (next_i >= N3) {
+      next_item = s_item;           // read by all threads before it changes (barriers below)
+      next_i = 0;
+      if (next_item < npencils) next_fwd = pencil_forward(next_item);
+    }
+    const bool has_next = next_item < npencils;
+    const unsigned next = has_next ? pencil_cell(next_item, next_i, next_fwd) : 0u;
+    const bool need_v3 = i == 0;    // the first cell's upwind v3 neighbour is not carried
     float spn[6];
     unsigned nbn[6];
     if (has_next) setup(next, spn, nbn);
@@ -320,62 +393,81 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
 #pragma unroll
       for (int e = 0; e < 64; ++e) u[e] *= winv_t * wprod(T.winv, e);
     }
-    ok &= mv.wait(B, p.err);
-    direction<0, true, ADJ>(r, u, view<true>(sm6 + B * kCellSmem, t), sp[0], winv_t, T);
+    ok &= mv.wait(P, p.err);
+    direction<0, true, ADJ>(r, u, view<true>(sm6 + P * kCellSmem, t), sp[0], winv_t, T);
     fence_async_smem();
     __syncthreads();
-    mv.issue(B, cellp(nbr[2]), t);               // x3
-    ok &= mv.wait(C, p.err);
-    direction<1, true, ADJ>(r, u, view<true>(sm6 + C * kCellSmem, t), sp[1], winv_t, T);
+    mv.issue(P, cellp(nbr[2]), t);               // x3
+    ok &= mv.wait(Q, p.err);
+    direction<1, true, ADJ>(r, u, view<true>(sm6 + Q * kCellSmem, t), sp[1], winv_t, T);
     fence_async_smem();
     __syncthreads();
-    mv.issue(C, cellp(nbr[3]), t);               // v1
-    ok &= mv.wait(B, p.err);
-    direction<2, true, ADJ>(r, u, view<true>(sm6 + B * kCellSmem, t), sp[2], winv_t, T);
-    __syncthreads();                             // B is free: it takes the phase X result
+    mv.issue(Q, cellp(nbr[3]), t);               // v1
+    ok &= mv.wait(P, p.err);
+    direction<2, true, ADJ>(r, u, view<true>(sm6 + P * kCellSmem, t), sp[2], winv_t, T);
+    __syncthreads();                             // P is free: it takes the phase X result
     {
-      float* rb = sm6 + B * kCellSmem + t * kPad;
+      float* rb = sm6 + P * kCellSmem + t * kPad;
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        *reinterpret_cast<float4*>(rb + 4 * i) =
-            make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+      for (int k = 0; k < 16; ++k)
+        *reinterpret_cast<float4*>(rb + 4 * k) =
+            make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
     }
     __syncthreads();
 
     // ---- phase V: columns, directions v1, v2, v3
     load_block<false>(u, view<false>(sm6 + A * kCellSmem, t));
-    load_block<false>(r, view<false>(sm6 + B * kCellSmem, t));
+    load_block<false>(r, view<false>(sm6 + P * kCellSmem, t));
     if (ADJ) {
 #pragma unroll
       for (int e = 0; e < 64; ++e) u[e] *= winv_t * wprod(T.winv, e);
     }
     fence_async_smem();
-    __syncthreads();                             // A and B are free
+    __syncthreads();                             // A and P are free
     if (has_next) mv.issue(A, cellp(next), t);   // the next cell
-    mv.issue(B, cellp(nbr[4]), t);               // v2
-    ok &= mv.wait(C, p.err);
-    direction<0, false, ADJ>(r, u, view<false>(sm6 + C * kCellSmem, t), sp[3], winv_t, T);
+    mv.issue(P, cellp(nbr[4]), t);               // v2
+    ok &= mv.wait(Q, p.err);
+    direction<0, false, ADJ>(r, u, view<false>(sm6 + Q * kCellSmem, t), sp[3], winv_t, T);
     fence_async_smem();
     __syncthreads();
-    mv.issue(C, cellp(nbr[5]), t);               // v3
-    ok &= mv.wait(B, p.err);
-    direction<1, false, ADJ>(r, u, view<false>(sm6 + B * kCellSmem, t), sp[4], winv_t, T);
+    if (need_v3)
+      mv.issue(Q, cellp(nbr[5]), t);             // v3 (wrapped, not carried)
+    else if (has_next)
+      mv.issue(Q, cellp(nbn[0]), t);             // x1 of the next cell
+    ok &= mv.wait(P, p.err);
+    direction<1, false, ADJ>(r, u, view<false>(sm6 + P * kCellSmem, t), sp[4], winv_t, T);
     fence_async_smem();
     __syncthreads();
-    if (has_next) mv.issue(B, cellp(nbn[0]), t);   // x1 of the next cell
-    ok &= mv.wait(C, p.err);
+    if (has_next) mv.issue(P, cellp(need_v3 ? nbn[0] : nbn[1]), t);  // x1 or x2 of the next cell
+    float tr[16];
+    if (need_v3) {
+      ok &= mv.wait(Q, p.err);
+      nb_traces<2, false, ADJ>(tr, view<false>(sm6 + Q * kCellSmem, t), sp[5], T);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) tr[k] *= ADJ ? winv_t : 1.f;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) tr[k] = carried[k];
+    }
+    {
+      // this cell's outflow traces become the next cell's inflow traces
+      float to[16];
+      own_traces<2>(to, u, sp[5]);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) carried[k] = to[k];
+    }
 
     // ---- last direction fused with step 5: scatter / LSRK stage update
     const size_t g0 = static_cast<size_t>(cell) * 4096 + t;
     if (p.mode == 0) {
-      direction<2, false, ADJ>(r, u, view<false>(sm6 + C * kCellSmem, t), sp[5], winv_t, T);
+      lines_dir<2>(r, u, tr, sp[5], 1.f);
       TW* dst = static_cast<TW*>(p.dst);
 #pragma unroll
       for (int m = 0; m < 64; ++m) {
         float K = r[m];
         if (ADJ) K *= w_t * wprod(T.w, m);
         bad |= !isfinite(K);
-        dst[g0 + 64 * m] = cvt<TW>(K);
+        __stcs(dst + g0 + 64 * m, cvt<TW>(K));   // streamed: not read again by this launch
       }
     } else {
       // the FP64 state of the first half of the cell is loaded while the
@@ -384,7 +476,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
       double uo[32];
 #pragma unroll
       for (int m = 0; m < 32; ++m) uo[m] = __ldcs(uu + g0 + 64 * m);
-      direction<2, false, ADJ>(r, u, view<false>(sm6 + C * kCellSmem, t), sp[5], winv_t, T);
+      lines_dir<2>(r, u, tr, sp[5], 1.f);
       TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
       const float af = static_cast<float>(p.a_dt);
@@ -404,18 +496,31 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
           // one FP64 add per value; everything else in FP32 / integer arithmetic
           const double un = uo[mm] + f32_to_f64(bf * K);
           __stcs(uu + g, un);
+          // the next stage vector is streamed out (not read by this launch)
           if constexpr (sizeof(TW) == 4) {
-            dst[g] = p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(uo[mm]));
+            __stcs(dst + g, p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(uo[mm])));
           } else {
-            dst[g] = p.last_stage ? un : uo[mm] + p.a_dt * f32_to_f64(K);
+            __stcs(dst + g, p.last_stage ? un : uo[mm] + p.a_dt * f32_to_f64(K));
           }
         }
       }
     }
     fence_async_smem();
-    __syncthreads();                             // C is free
+    __syncthreads();                             // Q is free; s_item was read by all threads
     if (!ok || !has_next) break;
-    mv.issue(C, cellp(nbn[1]), t);               // x2 of the next cell
+    if (need_v3) mv.issue(Q, cellp(nbn[1]), t);  // x2 of the next cell
+    else {
+      const int tmp = P;                         // x1 landed in Q, x2 in P
+      P = Q;
+      Q = tmp;
+    }
+    if (next_item != item) {          // block-uniform
+      item = next_item;
+      fwd = next_fwd;
+      if (t == 0) s_item = atomicAdd(p.work, 1u);
+      __syncthreads();
+    }
+    i = next_i;
     cell = next;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -438,7 +543,8 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
 template <typename TIN, typename TW, bool ADJ>
 cudaError_t launch6(KParams& p, cudaStream_t s) {
   auto kern = k_cell6d4<TIN, TW, ADJ>;
-  const size_t smem = static_cast<size_t>(kNumBuf) * kCellSmem * sizeof(float);
+  // three cell buffers and the carried v3 traces (17 floats per thread)
+  const size_t smem = (static_cast<size_t>(kNumBuf) * kCellSmem + 64 * 17) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -448,7 +554,11 @@ cudaError_t launch6(KParams& p, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const long long grid = std::min<long long>(p.ncells, static_cast<long long>(sms) * per_sm);
+  const long long npencils = p.cstride[5];
+  const long long grid = std::min<long long>(npencils, static_cast<long long>(sms) * per_sm);
+  // work items (v3 pencils) are handed out in order by an atomic counter
+  e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
   kern<<<static_cast<unsigned>(grid), 64, smem, s>>>(p);
   return cudaGetLastError();
 }

@@ -67,6 +67,7 @@ struct KParams {
   double* u;                // FP64 state (stage mode)
   void* scratch;            // per-block accumulators (large cells)
   int* err;                 // device error latch
+  unsigned* work;           // work-queue counter of the persistent kernels
   int mode;                 // 0 = apply, 1 = LSRK stage
   int adjoint;              // 1: L^T = M L(-a) M^{-1}
   int last_stage;           // stage mode: w_out = u_new
@@ -142,6 +143,7 @@ struct dg_ctx {
   double* cx_d64 = nullptr; float* cx_d32 = nullptr;
   double* cv_d64 = nullptr; float* cv_d32 = nullptr;
   int* err_d = nullptr;
+  unsigned* work_d = nullptr;   // work-queue counter
   void* scratch = nullptr; size_t scratch_bytes = 0;
   double* partial = nullptr; int partial_blocks = 0;
   cudaStream_t capture_stream = nullptr;
