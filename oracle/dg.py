@@ -410,6 +410,28 @@ class Problem:
         W = _outer_weights([self.T.w] * self.d).reshape(-1, order="F")
         return np.tile(W * self.detJ, self.ncells)
 
+    # -- Vlasov-Poisson coupling (Sec. 6) -------------------------------------
+    def charge_density(self, u, x_cells=None):
+        """rho(x_q) = 1 - int f(x_q, v) dv at every x node, from the definition:
+        the v integral by the cell quadrature of the v mesh (|J_v| times the
+        product of the 1D weights), collocation basis.  Returns an array of
+        shape (x cells, x nodes) with x cells and nodes lexicographic (only
+        the rows of ``x_cells`` if given)."""
+        assert self.basis == "gl"
+        dx, dv, n = self.dx, self.dv, self.n
+        ncx = int(np.prod(self.cells[:dx]))
+        ncv = int(np.prod(self.cells[dx:]))
+        detJv = float(np.prod(self.h[dx:] / 2))
+        Wv = _outer_weights([self.T.w] * dv).reshape(-1, order="F")
+        rows = range(ncx) if x_cells is None else list(x_cells)
+        rho = np.ones((len(rows), n ** dx))
+        for r, cx in enumerate(rows):
+            for cv in range(ncv):
+                e = cx + ncx * cv
+                f = self.cell_tensor(u, e).reshape(n ** dx, n ** dv, order="F")
+                rho[r] -= detJv * (f @ Wv)
+        return rho
+
     # -- integrals -----------------------------------------------------------
     def integrals(self, u):
         """(int u, int u^2, max |u| at nodes) with the cell quadrature."""

@@ -391,3 +391,157 @@ def test_one_period_return_2d_config():
     # mass conserved to round-off, energy non-increasing
     assert abs(Md @ u - Md @ u0) < 1e-13
     assert u @ (Md * u) <= u0 @ (Md * u0)
+
+
+# ---------------------------------------------------------------------------
+# Vlasov-Poisson charge density rho = 1 - int f dv (Sec. 6)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dx,dv,k", [(1, 1, 2), (1, 2, 3), (2, 2, 1), (2, 3, 2)])
+def test_charge_density_closed_form(dx, dv, k):
+    """f = g(x) prod_j (a_j + b_j v_j^2 + c_j v_j^3): the Gauss rule of a v
+    cell is exact for degree 2k+1 >= 3, so int f dv = g(x) prod_j I_j with
+    I_j the integral over [v_lo_j, v_hi_j] written out by hand."""
+    rng = np.random.default_rng(11 + 7 * dx + dv + k)
+    cells_x = [3, 2][:dx]
+    cells_v = [3, 2, 2][:dv]
+    v_lo = -rng.uniform(1.0, 3.0, dv)
+    v_hi = rng.uniform(1.0, 3.0, dv)
+    p = Problem(dx, dv, k, cells_x, cells_v, [0.0] * dx, [2 * np.pi] * dx, v_lo, v_hi,
+                ConstantField([1.0] * (dx + dv)))
+    a, b, c = rng.uniform(0.5, 1.5, dv), rng.uniform(-1, 1, dv), rng.uniform(-1, 1, dv)
+    kx = np.arange(1, dx + 1)
+
+    def g(yx):
+        return 0.3 + np.cos(yx @ kx + 0.2)
+
+    def f(yx, v):
+        return g(yx) * np.prod(a + b * v ** 2 + c * v ** 3, axis=-1)
+
+    u = p.interpolate(f)
+    rho = p.charge_density(u)
+    I = np.prod(a * (v_hi - v_lo) + b * (v_hi ** 3 - v_lo ** 3) / 3 + c * (v_hi ** 4 - v_lo ** 4) / 4)
+    ncx = int(np.prod(cells_x))
+    for cx in range(ncx):
+        # the first v cell shares this x cell's x nodes
+        yx, _ = p.node_coordinates(cx)
+        gx = g(yx)[(slice(None),) * dx + (0,) * dv].reshape(-1, order="F")
+        np.testing.assert_allclose(rho[cx], 1.0 - gx * I, rtol=0, atol=1e-12 * abs(I) + 1e-14)
+
+
+def test_charge_density_maxwellian():
+    """A Landau-damping profile (1 + alpha cos(kx)) e^{-v^2/2} / sqrt(2 pi)^dv on
+    a wide v box: rho = -alpha cos(kx) up to the quadrature error and the
+    Gaussian tail beyond +-8."""
+    alpha, kk = 0.01, 0.5
+    p = Problem(1, 2, 3, [4], [16, 16], [0.0], [2 * np.pi / kk], [-8.0] * 2, [8.0] * 2,
+                ConstantField([1.0, 1.0, 1.0]))
+
+    def f(yx, v):
+        return (1 + alpha * np.cos(kk * yx[..., 0])) * np.exp(-0.5 * np.sum(v ** 2, -1)) / (2 * np.pi)
+
+    rho = p.charge_density(p.interpolate(f))
+    for cx in range(4):
+        yx, _ = p.node_coordinates(cx)
+        x = yx[:, 0, 0, 0]
+        np.testing.assert_allclose(rho[cx], -alpha * np.cos(kk * x), atol=2e-6)
+
+
+def test_charge_density_layout_x_cells_and_nodes():
+    """Brute force on a tiny mesh: rho at (x cell, x node) sums exactly the
+    DoFs with that x cell and x node, weighted by the v quadrature."""
+    p = Problem(2, 2, 1, [2, 3], [2, 2], [0, 0], [1, 1], [-1, -1], [1, 1], ConstantField([1] * 4))
+    u = np.random.default_rng(3).standard_normal(p.n_dofs)
+    rho = p.charge_density(u)
+    n, npc = p.n, p.dofs_per_cell
+    wv = p.T.w
+    ref = np.ones((6, n * n))
+    for e in range(p.ncells):
+        cc = p.cell_coords(e)
+        cx = cc[0] + 2 * cc[1]
+        for q in range(npc):
+            q0, q1, q2, q3 = q % n, (q // n) % n, (q // n ** 2) % n, q // n ** 3
+            w = wv[q2] * wv[q3] * (p.h[2] / 2) * (p.h[3] / 2)
+            ref[cx, q0 + n * q1] -= w * u[e * npc + q]
+    np.testing.assert_allclose(rho, ref, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Vlasov-Poisson for dim_x = 1 (Sec. 6)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k,shear", [(1, None), (3, None), (2, [[1.7]]), (5, [[-0.8]])])
+def test_poisson_periodic_closed_form(k, shear):
+    """rho = c0 + alpha cos(kappa x) on the period: E = alpha sin(kappa x) /
+    kappa (E' = rho - c0, zero mean), up to the interpolation error of rho."""
+    from oracle.vp import poisson_periodic_1d
+    s = 1.0 if shear is None else shear[0][0]
+    kappa, alpha, c0 = 0.5, 0.3, 0.7
+    L = 2 * np.pi / kappa
+    ncx = 24
+    p = Problem(1, 1, k, [ncx], [2], [0.0], [L / s], [-1.0], [1.0], ConstantField([1.0, 1.0]),
+                shear=shear)
+    xs = np.array([p.node_coordinates(c)[0][:, 0, 0] * s for c in range(ncx)])   # physical x
+    rho = c0 + alpha * np.cos(kappa * xs)
+    E, nodal = poisson_periodic_1d(p, rho)
+    tol = {1: 3e-3, 2: 2e-4, 3: 1e-5, 5: 1e-8}[k]
+    np.testing.assert_allclose(nodal, alpha * np.sin(kappa * xs) / kappa, atol=tol)
+    # the callable agrees with the nodal values and is continuous and periodic
+    ys = np.array([p.node_coordinates(c)[0][:, 0, 0] for c in range(ncx)])
+    np.testing.assert_allclose(E(ys), nodal, atol=1e-14)
+    edges = p.lo[0] + p.h[0] * np.arange(ncx + 1)
+    left = E(edges[1:-1] - 1e-12)
+    right = E(edges[1:-1] + 1e-12)
+    np.testing.assert_allclose(left, right, atol=1e-9)
+    np.testing.assert_allclose(E(np.array([edges[0]])), E(np.array([edges[-1] - 1e-13])), atol=1e-9)
+
+
+def test_poisson_periodic_polynomial_exact():
+    """A charge density that is a single polynomial of degree k in every cell
+    and already neutral: E is exact to rounding (degree k+1 antiderivative),
+    checked against the antiderivative written out by hand."""
+    from oracle.vp import poisson_periodic_1d
+    k = 3
+    p = Problem(1, 1, k, [4], [1], [0.0], [4.0], [-1.0], [1.0], ConstantField([1.0, 1.0]))
+    # on each unit cell [c, c+1]: rho = (t - 1/2)^3 with t = x - c (zero mean per cell);
+    # E = ((t - 1/2)^4 - 1/16) / 4 + const, the const making the mean zero
+    xs = np.array([p.node_coordinates(c)[0][:, 0, 0] for c in range(4)])
+    t = xs - np.floor(xs)
+    rho = (t - 0.5) ** 3
+    _, nodal = poisson_periodic_1d(p, rho)
+    exact = ((t - 0.5) ** 4 - 1.0 / 16) / 4
+    exact -= (1.0 / 80 - 1.0 / 16) / 4        # int_0^1 ((t - 1/2)^4 - 1/16) dt = 1/80 - 1/16
+    np.testing.assert_allclose(nodal, exact, atol=1e-14)
+
+
+def test_vp_uniform_maxwellian_is_stationary():
+    """A spatially uniform, neutral Maxwellian has rho = 0 up to its
+    quadrature error, hence E = 0 exactly (the mean is removed) and no
+    x-gradient: one step leaves it unchanged."""
+    from oracle.vp import vp_step
+    p = Problem(1, 1, 3, [4], [12], [0.0], [4 * np.pi], [-6.0], [6.0], ConstantField([1.0, 1.0]))
+    u = p.interpolate(lambda yx, v: np.exp(-0.5 * v[..., 0] ** 2) / np.sqrt(2 * np.pi))
+    u1 = vp_step(p, u, 0.05)
+    np.testing.assert_allclose(u1, u, atol=1e-14)
+
+
+def test_vp_field_uses_minus_e_and_conserves_mass():
+    """With a density bump the field is (v, -E): the operator of vp_rhs equals
+    the advection operator with a_v = -E(y) written with the closed-form E of
+    the nodal rho; the step conserves mass."""
+    from oracle.vp import field_from, poisson_periodic_1d, vp_step
+    p = Problem(1, 1, 2, [6], [8], [0.0], [2 * np.pi], [-4.0], [4.0], ConstantField([1.0, 1.0]))
+    f = lambda yx, v: (1 + 0.2 * np.cos(yx[..., 0])) * np.exp(-0.5 * v[..., 0] ** 2) / np.sqrt(2 * np.pi)
+    u = p.interpolate(f)
+    rho = p.charge_density(u)
+    E, nodal = poisson_periodic_1d(p, rho)
+    fld = field_from(p, u)
+    ys = np.linspace(0.0, 2 * np.pi, 7, endpoint=False)[:, None]
+    a = fld(ys, np.zeros((7, 1)))
+    np.testing.assert_allclose(a[:, 1], -E(ys[:, 0]), atol=0)
+    np.testing.assert_allclose(a[:, 0], 0.0, atol=0)
+    # rho = 1 - int f dv is close to -0.2 cos(x) (the Maxwellian integrates to ~1)
+    xs = np.array([p.node_coordinates(c)[0][:, 0, 0] for c in range(6)])
+    np.testing.assert_allclose(rho, -0.2 * np.cos(xs), atol=2e-3)
+    np.testing.assert_allclose(nodal, -0.2 * np.sin(xs), atol=5e-3)
+    m0 = p.integrals(u)[0]
+    u1 = vp_step(p, u, 0.02)
+    assert abs(p.integrals(u1)[0] - m0) <= 1e-13 * abs(m0)
