@@ -294,6 +294,38 @@ def measure_configs(torch, hbm_peak):
         return {"ms_per_step": ms_step, "GDoF/s_per_stage": dg.n_dofs / (st * 1e-3) / 1e9,
                 "frac_hbm": gbs / hbm_peak, "bytes_per_dof": bpd}
 
+    # 6D: FP32 sweeps / FP64 state against the plain FP64 path on the same
+    # GPU -- error per operator application and after a number of steps
+    w = W.config_6d()
+    dg, zeta = make(w)
+    dt, _ = W.time_step(w)
+    u0 = W.separable_state(w, zeta, xp=torch, device="cuda")
+    k64 = dg.apply(u0, prec=PREC_FP64)
+    k32 = dg.apply(u0.float(), prec=PREC_FP32).double()
+    rel_apply = float(torch.linalg.vector_norm(k32 - k64) / torch.linalg.vector_norm(k64))
+    del k32
+    nacc = 10
+    u64 = u0.clone()
+    ms64 = _timed(torch, lambda: dg.rk_step(u64, dt, nsteps=nacc, prec=PREC_FP64), 1)
+    u32 = u0.clone()
+    ms32 = _timed(torch, lambda: dg.rk_step(u32, dt, nsteps=nacc, prec=PREC_FP32), 1)
+    dg.check()
+    m0 = dg.integrals(u0)[0]
+    out["6d_fp32_vs_fp64"] = {
+        "workload": w.name, "steps": nacc,
+        "apply_rel_l2_diff": rel_apply,
+        "state_rel_l2_diff_after_steps": float(torch.linalg.vector_norm(u32 - u64) /
+                                               torch.linalg.vector_norm(u64)),
+        "mass_drift_fp64": (dg.integrals(u64)[0] - m0) / m0,
+        "mass_drift_fp32_fp64state": (dg.integrals(u32)[0] - m0) / m0,
+        "ms_per_step_fp64": ms64 / nacc, "ms_per_step_fp32_fp64state": ms32 / nacc,
+        "note": "K of the FP64 path matches the FP64 oracle to 1e-12 (tests); the plain relative "
+                "difference of K is large for smooth data (K << its terms); see tests for the "
+                "term-scale error"}
+    dg.close()
+    del u0, u64, u32, k64
+    torch.cuda.empty_cache()
+
     # 2D: one period (T = 2, 240 steps), FP64
     w = W.config_2d()
     dg, zeta = make(w)

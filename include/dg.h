@@ -229,6 +229,61 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
 dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream);
 
 /*
+ * Charge density of the Vlasov-Poisson coupling (Sec. 6, Eq. vp:close):
+ * rho(x) = 1 - int f(x, v) dv at every x node, the velocity integral taken
+ * with the cell quadrature of the v mesh (|J_v| times the product of the GL
+ * weights).  f: device vector (FP64 for DG_PREC_FP64, FP32 for
+ * DG_PREC_FP32); rho: device array of n_xcells * (k+1)^dim_x doubles in the
+ * layout of dg_geometry.e_nodes without the component index (x cell, x node;
+ * both lexicographic, x_1 fastest).  Accumulates in FP64.  Stream-ordered.
+ * (Computing E from rho -- the Poisson solve -- is outside this library;
+ * dg_set_field takes the result.)
+ */
+dg_status dg_charge_density(dg_handle h, const void* f, int prec, double* rho, void* stream);
+
+/*
+ * Periodic Poisson problem of Sec. 6 (Eq. vp:close) for dim_x = 1:
+ * -phi'' = rho, E = -phi', i.e. E' = rho in the physical coordinate
+ * x = S y.  Periodicity needs a neutral rho: its mean is removed first.  E is
+ * the exact antiderivative of the nodal degree-k polynomial of rho - mean in
+ * each cell (a continuous piecewise polynomial of degree k+1) with zero mean
+ * over the period, written at the x nodes.  rho, e: device arrays of
+ * n_xcells * (k+1) doubles (x cell, x node), not overlapping.  One block;
+ * deterministic.  Stream-ordered.  Errors: UNSUPPORTED if dim_x != 1.
+ * (The paper solves this with geometric multigrid in dim_x = 2, 3; that
+ * solver is not part of this library.)
+ */
+dg_status dg_poisson_periodic_1d(dg_handle h, const double* rho, double* e, void* stream);
+
+/*
+ * Replace the v part of the velocity field of a DG_FIELD_PHASE_SPACE handle
+ * from DEVICE memory: a_v = scale * e at every x node, e laid out (x cell,
+ * x node, component) with ``components`` (1..dim_v) values per node; the
+ * remaining components are zero.  For the Vlasov field (v, -E) pass the
+ * electric field and scale = -1 (Sec. 6).  Stream-ordered.  For d = 6, k = 3
+ * the sign pattern of the field selects the kernel, so the call reads one
+ * flag back and synchronises ``stream``; otherwise it does not synchronise.
+ * Non-finite values are latched and reported by dg_check (DG_ERR_NONFINITE).
+ * dg_info's uniform_sides reflects the field for d = 6, k = 3 and reads 0
+ * otherwise.
+ */
+dg_status dg_set_field_device(dg_handle h, const double* e, int components, double scale,
+                              void* stream);
+
+/*
+ * nsteps LSRK(5,4) steps of the Vlasov-Poisson system (Sec. 6) for dim_x = 1
+ * on the FP64 state f = u (in place).  Every stage evaluates, on its input
+ * stage vector: the charge density (dg_charge_density), the electric field
+ * (dg_poisson_periodic_1d), the field a_v = (-E, 0, ...) (dg_set_field_device)
+ * and the fused advection stage (dg_rk_stage).  Arguments as dg_rk_step; the
+ * handle owns the two x-node scratch arrays (allocated on first use).  Not
+ * replayed from a graph.  Errors: UNSUPPORTED if dim_x != 1, INVALID_ARG for
+ * a constant-field handle.
+ */
+dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
+                        void* stream);
+
+/*
  * The integrals of dg_integrals() for callers that cannot allocate device
  * memory -- for example code that runs while a CUDA graph is being captured,
  * code inside a framework whose allocator owns all device memory, or a long

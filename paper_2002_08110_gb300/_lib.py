@@ -78,6 +78,10 @@ def load():
         "dg_integrals": (i, [vp, vp, c_double_p, vp]),
         "dg_integrals_noalloc": (i, [vp, ll, i, i, d, c_double_p, vp]),
         "dg_check": (i, [vp, vp]),
+        "dg_charge_density": (i, [vp, vp, i, vp, vp]),
+        "dg_poisson_periodic_1d": (i, [vp, vp, vp, vp]),
+        "dg_set_field_device": (i, [vp, vp, i, ctypes.c_double, vp]),
+        "dg_vp_rk_step": (i, [vp, vp, vp, vp, ctypes.c_double, i, i, vp]),
         "dg_get_launch": (i, [vp, i, ctypes.POINTER(Launch)]),
         "dg_set_launch": (i, [vp, i, ctypes.POINTER(Launch)]),
         "dg_autotune": (i, [vp, vp, vp, i, vp, c_double_p]),

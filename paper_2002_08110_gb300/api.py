@@ -157,6 +157,51 @@ class DG:
                                     out.ctypes.data_as(_lib.c_double_p), _stream()))
         return tuple(float(x) for x in out)
 
+    def charge_density(self, f, prec=PREC_FP64, rho=None):
+        """rho = 1 - int f dv at the x nodes, shape (n_xcells * (k+1)^dim_x,) FP64."""
+        nrho = int(self.info.n_xcells) * (self.degree + 1) ** self.dim_x
+        if rho is None:
+            rho = torch.empty(nrho, dtype=torch.float64, device=f.device)
+        if rho.numel() != nrho or rho.dtype != torch.float64 or not rho.is_contiguous():
+            raise ValueError(f"rho must be a contiguous FP64 tensor of {nrho} elements")
+        check(self.lib.dg_charge_density(self.handle, self._vec(f, prec, "f"), prec, _ptr(rho),
+                                         _stream()))
+        return rho
+
+    def poisson_periodic_1d(self, rho, e=None):
+        """E at the x nodes with E' = rho - mean(rho), zero mean (dim_x = 1)."""
+        if e is None:
+            e = torch.empty_like(rho)
+        for name, t in (("rho", rho), ("e", e)):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                    and t.numel() == int(self.info.n_xcells) * (self.degree + 1)):
+                raise ValueError(f"{name} must be a contiguous CUDA FP64 tensor of one value per x node")
+        check(self.lib.dg_poisson_periodic_1d(self.handle, _ptr(rho), _ptr(e), _stream()))
+        return e
+
+    def set_field_device(self, e, components=None, scale=1.0):
+        """a_v = scale * e from a device tensor (x cell, x node, component)."""
+        comps = self.dim_v if components is None else int(components)
+        nx = int(self.info.n_xcells) * (self.degree + 1) ** self.dim_x
+        if not (e.is_cuda and e.dtype == torch.float64 and e.is_contiguous()
+                and e.numel() == nx * comps):
+            raise ValueError(f"e must be a contiguous CUDA FP64 tensor of {nx * comps} values")
+        check(self.lib.dg_set_field_device(self.handle, _ptr(e), comps, float(scale), _stream()))
+        info = _lib.Info()
+        check(self.lib.dg_info(self.handle, ctypes.byref(info)))
+        self.info = info
+
+    def vp_rk_step(self, u, dt, nsteps=1, prec=PREC_FP64, w0=None, w1=None):
+        """Vlasov-Poisson LSRK(5,4) steps (dim_x = 1): the field follows f at every stage."""
+        if w0 is None:
+            w0 = self.empty(prec, u.device)
+        if w1 is None:
+            w1 = self.empty(prec, u.device)
+        check(self.lib.dg_vp_rk_step(self.handle, self._vec(u, PREC_FP64, "u"),
+                                     self._vec(w0, prec, "w0"), self._vec(w1, prec, "w1"),
+                                     float(dt), int(nsteps), prec, _stream()))
+        return u
+
     def check(self):
         """Synchronise and raise DGError(DG_ERR_NONFINITE) if a kernel saw NaN/Inf."""
         check(self.lib.dg_check(self.handle, _stream()))

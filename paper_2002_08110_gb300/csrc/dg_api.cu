@@ -88,6 +88,16 @@ dg_status check_vec(const void* ptr, const char* name) {
   return DG_OK;
 }
 
+// Captured LSRK graphs hold kernel choices and scratch pointers: dropped
+// whenever either changes.
+void drop_graphs(dg_ctx* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) {
+      cudaGraphExecDestroy(h->gexec[i]);
+      h->gexec[i] = nullptr;
+    }
+}
+
 KParams base_params(const dg_ctx* h, int prec) {
   KParams p;
   std::memset(&p, 0, sizeof(p));
@@ -122,11 +132,7 @@ dg_status ensure_scratch(dg_ctx* h, int prec) {
                       compute_bytes(prec);
   if (h->scratch_bytes >= need) return DG_OK;
   // captured graphs hold the old scratch pointer
-  for (int i = 0; i < 2; ++i)
-    if (h->gexec[i]) {
-      cudaGraphExecDestroy(h->gexec[i]);
-      h->gexec[i] = nullptr;
-    }
+  drop_graphs(h);
   if (h->scratch) cudaFree(h->scratch);
   h->scratch = nullptr;
   h->scratch_bytes = 0;
@@ -242,6 +248,9 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->work_d);
   cudaFree(h->scratch);
   cudaFree(h->partial);
+  cudaFree(h->field_flags_d);
+  cudaFree(h->vp_rho);
+  cudaFree(h->vp_e);
   delete h;
 }
 
@@ -310,7 +319,8 @@ dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
       }
     return true;
   };
-  h->uniform_sides = uniform(h->cx_host, h->ncv, h->nqv, dx) && uniform(h->cv_host, h->ncx, h->nqx, dv);
+  h->cx_uniform = uniform(h->cx_host, h->ncv, h->nqv, dx);
+  h->uniform_sides = h->cx_uniform && uniform(h->cv_host, h->ncx, h->nqx, dv);
   double sum = 0.0;
   for (int j = 0; j < h->d; ++j) {
     double mx = 0.0;
@@ -563,8 +573,10 @@ dg_status dg_set_field(dg_handle h, const double* e_nodes, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
   if (h->field_kind != DG_FIELD_PHASE_SPACE)
     return fail(DG_ERR_INVALID_ARG, "dg_set_field needs a phase-space handle");
+  const bool was_uniform = h->uniform_sides;
   dg_status s = compute_speeds(h, e_nodes);
   if (s != DG_OK) return s;
+  if (h->uniform_sides != was_uniform) drop_graphs(h);   // they hold the other kernel
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<float> f(h->cv_host.begin(), h->cv_host.end());
   cudaError_t e;
@@ -574,7 +586,113 @@ dg_status dg_set_field(dg_handle h, const double* e_nodes, void* stream) {
           cudaSuccess ||
       (e = cudaMemcpy(h->cv_d32, f.data(), f.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "dg_set_field");
-  // graphs captured with the old field stay valid (tables are read at run time)
+  // graphs captured with the same kernel stay valid (tables are read at run time)
+  return DG_OK;
+}
+
+// The specialised 6D kernel is chosen on the host from uniform_sides; a field
+// set on the device records its sign pattern in field_flags_d.  Only where
+// that kernel could run is the flag read back (a synchronisation).
+dg_status set_field_device(dg_ctx* h, const double* e, int comps, double scale, cudaStream_t s) {
+  cudaError_t err;
+  if (h->field_flags_d == nullptr && (err = cudaMalloc(&h->field_flags_d, sizeof(int))) != cudaSuccess)
+    return cuda_fail(err, "field flag allocation");
+  double two_over_h[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < h->dv; ++j) two_over_h[j] = 2.0 / h->h[h->dx + j];
+  if ((err = cudaMemsetAsync(h->field_flags_d, 0, sizeof(int), s)) != cudaSuccess ||
+      (err = launch_field_speeds(e, comps, scale, h->ncx, h->nqx, h->dv, two_over_h, h->cv_d64,
+                                 h->cv_d32, h->field_flags_d, h->err_d, s)) != cudaSuccess)
+    return cuda_fail(err, "field speeds");
+  const bool was_uniform = h->uniform_sides;
+  if (h->d == 6 && h->n == 4) {
+    int flags = 0;
+    if ((err = cudaMemcpyAsync(&flags, h->field_flags_d, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(err, "field flag read-back");
+    h->uniform_sides = h->cx_uniform && !(flags & 1);
+  } else {
+    h->uniform_sides = false;   // not inspected; no specialised kernel for this (d, k)
+  }
+  if (h->uniform_sides != was_uniform) drop_graphs(h);
+  return DG_OK;
+}
+
+dg_status dg_set_field_device(dg_handle h, const double* e, int components, double scale,
+                              void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->field_kind != DG_FIELD_PHASE_SPACE)
+    return fail(DG_ERR_INVALID_ARG, "dg_set_field_device needs a phase-space handle");
+  if (e == nullptr || reinterpret_cast<uintptr_t>(e) % 8 != 0)
+    return fail(DG_ERR_INVALID_ARG, "e is NULL or not 8-byte aligned");
+  if (components < 1 || components > h->dv)
+    return fail(DG_ERR_INVALID_ARG, "components must be in [1, dim_v]");
+  if (!std::isfinite(scale)) return fail(DG_ERR_INVALID_ARG, "scale is not finite");
+  return set_field_device(h, e, components, scale, static_cast<cudaStream_t>(stream));
+}
+
+dg_status dg_poisson_periodic_1d(dg_handle h, const double* rho, double* e, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "the Poisson solve needs dim_x = 1");
+  if (rho == nullptr || e == nullptr || reinterpret_cast<uintptr_t>(rho) % 8 != 0 ||
+      reinterpret_cast<uintptr_t>(e) % 8 != 0)
+    return fail(DG_ERR_INVALID_ARG, "rho and e must be non-NULL and 8-byte aligned");
+  const size_t bytes = static_cast<size_t>(h->ncx) * h->n * sizeof(double);
+  if (ranges_overlap(rho, e, bytes)) return fail(DG_ERR_INVALID_ARG, "rho and e overlap");
+  PoissonTab t;
+  std::memset(&t, 0, sizeof(t));
+  for (int q = 0; q < h->n; ++q) {
+    t.w[q] = h->tables.w[q];
+    for (int p = 0; p < h->n; ++p) t.Iq[q * kMaxN + p] = h->tables.Iq[q][p];
+  }
+  const double hphys = h->S[0] * h->h[0];   // x = S y (1 x 1 shear)
+  cudaError_t err = launch_poisson_1d(rho, e, h->ncx, h->n, t, hphys,
+                                      static_cast<cudaStream_t>(stream));
+  if (err != cudaSuccess) return cuda_fail(err, "Poisson kernel");
+  return DG_OK;
+}
+
+dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
+                        void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need dim_x = 1");
+  if (h->field_kind != DG_FIELD_PHASE_SPACE)
+    return fail(DG_ERR_INVALID_ARG, "Vlasov-Poisson steps need a phase-space handle");
+  if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  dg_status st;
+  if ((st = check_vec(u, "u")) != DG_OK || (st = check_vec(w0, "w0")) != DG_OK ||
+      (st = check_vec(w1, "w1")) != DG_OK)
+    return st;
+  const size_t wb = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
+  const size_t ub = static_cast<size_t>(h->n_dofs) * 8;
+  if (ranges_overlap(w0, w1, wb) || ranges_overlap(w0, wb, u, ub) ||
+      ranges_overlap(w1, wb, u, ub))
+    return fail(DG_ERR_INVALID_ARG, "u, w0 and w1 must not overlap");
+  if (nsteps == 0) return DG_OK;
+  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  cudaError_t err;
+  const size_t xb = static_cast<size_t>(h->ncx) * h->nqx * sizeof(double);
+  if (h->vp_rho == nullptr && ((err = cudaMalloc(&h->vp_rho, xb)) != cudaSuccess ||
+                               (err = cudaMalloc(&h->vp_e, xb)) != cudaSuccess))
+    return cuda_fail(err, "Vlasov-Poisson scratch");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((err = launch_convert(u, w0, prec == DG_PREC_FP32, h->n_dofs, s)) != cudaSuccess)
+    return cuda_fail(err, "stage-vector initialisation");
+  const int fprec = prec == DG_PREC_FP32 ? DG_PREC_FP32 : DG_PREC_FP64;
+  for (int i = 0; i < nsteps; ++i) {
+    void* w[2] = {i % 2 ? w1 : w0, i % 2 ? w0 : w1};
+    for (int sg = 0; sg < 5; ++sg) {
+      const void* w_in = w[sg % 2];
+      // Sec. 6, steps 1-4 on the stage's input, then the advection stage
+      if ((st = dg_charge_density(h, w_in, fprec, h->vp_rho, s)) != DG_OK) return st;
+      if ((st = dg_poisson_periodic_1d(h, h->vp_rho, h->vp_e, s)) != DG_OK) return st;
+      if ((st = set_field_device(h, h->vp_e, 1, -1.0, s)) != DG_OK) return st;   // a_v = -E
+      if ((st = enqueue_stage(h, w_in, w[(sg + 1) % 2], u, sg, dt, prec, 0, s)) != DG_OK)
+        return st;
+    }
+  }
   return DG_OK;
 }
 
@@ -697,6 +815,26 @@ dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream) 
   return DG_OK;
 }
 
+dg_status dg_charge_density(dg_handle h, const void* f, int prec, double* rho, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
+    return fail(DG_ERR_INVALID_ARG, "f must be FP64 (DG_PREC_FP64) or FP32 (DG_PREC_FP32)");
+  dg_status st;
+  if ((st = check_vec(f, "f")) != DG_OK) return st;
+  if (rho == nullptr) return fail(DG_ERR_INVALID_ARG, "rho is NULL");
+  if (ranges_overlap(f, static_cast<size_t>(h->n_dofs) * elem_bytes(prec), rho,
+                     static_cast<size_t>(h->ncx) * h->nqx * sizeof(double)))
+    return fail(DG_ERR_INVALID_ARG, "f and rho overlap");
+  if (h->ncx > 0x7fffffffLL) return fail(DG_ERR_INVALID_ARG, "too many x cells");
+  double detJv = 1.0;
+  for (int j = h->dx; j < h->d; ++j) detJv *= h->h[j] / 2.0;
+  cudaError_t e = launch_charge_density(f, prec == DG_PREC_FP32, h->ncx, h->ncv, h->npc, h->nqx,
+                                        h->nqv, h->dv, h->n, h->tables.t64, detJv, rho,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "charge density kernel");
+  return DG_OK;
+}
+
 dg_status dg_check(dg_handle h, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -733,11 +871,7 @@ dg_status dg_set_launch(dg_handle h, int prec, const dg_launch* cfg) {
   dg_status s = validate_cfg(h, prec, c);
   if (s != DG_OK) return s;
   h->cfg[prec] = c;
-  for (int i = 0; i < 2; ++i)
-    if (h->gexec[i]) {
-      cudaGraphExecDestroy(h->gexec[i]);
-      h->gexec[i] = nullptr;
-    }
+  drop_graphs(h);
   return DG_OK;
 }
 
@@ -816,11 +950,7 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->cfg[prec] = best_cfg;
-  for (int i = 0; i < 2; ++i)
-    if (h->gexec[i]) {
-      cudaGraphExecDestroy(h->gexec[i]);
-      h->gexec[i] = nullptr;
-    }
+  drop_graphs(h);
   if (best_ms) *best_ms = best;
   if (st != DG_OK) return st;
   cudaError_t e = cudaStreamSynchronize(s);

@@ -45,6 +45,7 @@ struct HostTables {
   double zeta[kMaxN], w[kMaxN];
   double D[kMaxN][kMaxN];  // D[p][i] = phi_i'(zeta_p)
   double lp[kMaxN], lm[kMaxN];
+  double Iq[kMaxN][kMaxN];  // Iq[q][i] = int_{-1}^{zeta_q} phi_i (1D Poisson solve)
   Tab1D<double> t64;
   Tab1D<float> t32;
 };
@@ -116,6 +117,22 @@ void lsrk_coefficients(double* a4, double* b5);
 cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s);
 cudaError_t launch_integrals(const KParams& p, int n, const double* u, double* partial,
                              int blocks, double detJ, cudaStream_t s);
+// Zero-mean periodic antiderivative of rho - mean(rho) on a 1D mesh (the
+// Poisson solve of Sec. 6 for dim_x = 1), and contravariant v speeds from a
+// device field (dg_misc.cu).
+struct PoissonTab {
+  double Iq[kMaxN * kMaxN];   // [q][i]
+  double w[kMaxN];
+};
+cudaError_t launch_poisson_1d(const double* rho, double* e, long long ncx, int n,
+                              const PoissonTab& t, double hphys, cudaStream_t s);
+cudaError_t launch_field_speeds(const double* e, int comps, double scale, long long ncx, int nq,
+                                int dv, const double* two_over_hv, double* cv64, float* cv32,
+                                int* flags, int* err, cudaStream_t s);
+cudaError_t launch_charge_density(const void* f, int f_is_float, long long ncx, long long ncv,
+                                  int npc, int nqx, int nqv, int dv, int n,
+                                  const Tab1D<double>& t, double detJv, double* rho,
+                                  cudaStream_t s);
 
 }  // namespace dg
 
@@ -137,6 +154,7 @@ struct dg_ctx {
   // every cell has a single upwind side per direction (no speed component
   // changes sign inside a cell): required by the specialised kernels
   bool uniform_sides = true;
+  bool cx_uniform = true;       // the x-direction part of uniform_sides (fixed by the v mesh)
   int device = 0;
   dg::HostTables tables;
   std::vector<double> cx_host, cv_host;   // contravariant speeds (FP64)
@@ -144,6 +162,9 @@ struct dg_ctx {
   double* cv_d64 = nullptr; float* cv_d32 = nullptr;
   int* err_d = nullptr;
   unsigned* work_d = nullptr;   // work-queue counter
+  int* field_flags_d = nullptr; // device-fed field: bit 0 mixed upwind side in a cell, bit 1 non-finite
+  double* vp_rho = nullptr;     // Vlasov-Poisson scratch: rho and E at the x nodes
+  double* vp_e = nullptr;
   void* scratch = nullptr; size_t scratch_bytes = 0;
   double* partial = nullptr; int partial_blocks = 0;
   cudaStream_t capture_stream = nullptr;

@@ -74,3 +74,211 @@ cudaError_t launch_integrals(const KParams& p, int n, const double* u, double* p
 }
 
 }  // namespace dg
+
+namespace dg {
+
+// Charge density rho = 1 - int f dv at every x node (Sec. 6: the reduction
+// over velocity space that feeds the Poisson problem).  One block per x cell;
+// thread (qx, lane) handles x node qx and every lanes-th (v cell, v node) pair
+// in turn, accumulating |J_v| W_v(q_v) f in FP64; the lanes are then summed
+// in a fixed order (deterministic).  A warp reads contiguous runs of the x
+// nodes of consecutive v nodes.  n^dv <= 216 (degree <= 5, dim_v <= 3).
+constexpr int kMaxNqv = 216;
+
+template <typename TF>
+__global__ void k_charge_density(const TF* __restrict__ f, long long ncx, long long ncv, int npc,
+                                 int nqx, int nqv, int dv, int n, Tab1D<double> t, double detJv,
+                                 double* __restrict__ rho) {
+  __shared__ double s_w[kMaxNqv];
+  extern __shared__ double s_part[];
+  for (int q = threadIdx.x; q < nqv; q += blockDim.x) {
+    double w = detJv;
+    int r = q;
+    for (int k = 0; k < dv; ++k) {
+      w *= t.w[r % n];
+      r /= n;
+    }
+    s_w[q] = w;
+  }
+  __syncthreads();
+  const long long cx = blockIdx.x;
+  const int lanes = blockDim.x / nqx;            // threads per x node (blockDim.x = lanes * nqx)
+  const int qx = threadIdx.x % nqx;
+  const int lane = threadIdx.x / nqx;
+  double acc = 0.0;
+  long long cv = lane / nqv;
+  int qv = lane % nqv;
+  const int step_cv = lanes / nqv, step_qv = lanes % nqv;
+  while (cv < ncv) {
+    acc += s_w[qv] * static_cast<double>(f[(cx + ncx * cv) * npc + qx + nqx * qv]);
+    qv += step_qv;
+    cv += step_cv;
+    if (qv >= nqv) {
+      qv -= nqv;
+      ++cv;
+    }
+  }
+  s_part[threadIdx.x] = acc;
+  __syncthreads();
+  if (lane == 0) {
+    double s = 0.0;
+    for (int l = 0; l < lanes; ++l) s += s_part[l * nqx + qx];
+    rho[cx * nqx + qx] = 1.0 - s;
+  }
+}
+
+cudaError_t launch_charge_density(const void* f, int f_is_float, long long ncx, long long ncv,
+                                  int npc, int nqx, int nqv, int dv, int n,
+                                  const Tab1D<double>& t, double detJv, double* rho,
+                                  cudaStream_t s) {
+  if (nqv > kMaxNqv || nqx > 256) return cudaErrorInvalidValue;
+  const int threads = (256 / nqx) * nqx;         // a multiple of the x nodes per cell
+  const size_t smem = sizeof(double) * threads;
+  if (f_is_float)
+    k_charge_density<float><<<static_cast<unsigned>(ncx), threads, smem, s>>>(
+        static_cast<const float*>(f), ncx, ncv, npc, nqx, nqv, dv, n, t, detJv, rho);
+  else
+    k_charge_density<double><<<static_cast<unsigned>(ncx), threads, smem, s>>>(
+        static_cast<const double*>(f), ncx, ncv, npc, nqx, nqv, dv, n, t, detJv, rho);
+  return cudaGetLastError();
+}
+
+}  // namespace dg
+
+namespace dg {
+
+// Deterministic sum over the block (fixed shuffle tree, then the warp sums in
+// order by thread 0); the result is returned to every thread.
+__device__ double block_sum(double v, double* s_warp) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();                 // s_warp may still be read from the last call
+  if (lane == 0) s_warp[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i) s += s_warp[i];
+    s_warp[32] = s;
+  }
+  __syncthreads();
+  return s_warp[32];
+}
+
+// Periodic 1D Poisson problem of Sec. 6 (dim_x = 1): with E = -phi' and
+// -phi'' = rho, E' = rho; periodicity needs the mean of rho removed and fixes
+// E up to a constant, taken so that E has zero mean (phi periodic).  rho is
+// the degree-k nodal polynomial of each cell; E is its exact antiderivative,
+//   E(x_iq) = P_i + (h/2) sum_p Iq[q][p] (rho_ip - rho_bar),
+// P_i = sum_{j<i} (h/2) sum_p w_p (rho_jp - rho_bar), evaluated at the nodes.
+// One block: a chunked exclusive scan over the cells in a fixed order.
+__global__ void k_poisson_1d(const double* __restrict__ rho, double* __restrict__ e,
+                             long long ncx, int n, PoissonTab t, double hphys) {
+  __shared__ double s_warp[33];
+  __shared__ double s_scan[32];
+  double loc = 0.0;
+  for (long long c = threadIdx.x; c < ncx; c += blockDim.x)
+    for (int p = 0; p < n; ++p) loc += t.w[p] * rho[c * n + p];
+  // sum_c sum_p w_p rho = 2 ncx rho_bar (the cells' reference measure is 2)
+  const double rho_bar = block_sum(loc, s_warp) / (2.0 * static_cast<double>(ncx));
+  const double hh = 0.5 * hphys;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double carry = 0.0, emean = 0.0;
+  for (long long base = 0; base < ncx; base += blockDim.x) {
+    const long long c = base + threadIdx.x;
+    double r[kMaxN] = {0.0};
+    double ci = 0.0;
+    if (c < ncx) {
+      for (int p = 0; p < n; ++p) {
+        r[p] = rho[c * n + p] - rho_bar;
+        ci += t.w[p] * r[p];
+      }
+      ci *= hh;
+    }
+    // inclusive scan of ci over the chunk
+    double incl = ci;
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_scan[wid] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double run = 0.0;
+      for (int i = 0; i < nw; ++i) {
+        const double v = s_scan[i];
+        s_scan[i] = run;
+        run += v;
+      }
+      s_warp[32] = run;            // chunk total
+    }
+    __syncthreads();
+    const double prefix = carry + s_scan[wid] + incl - ci;
+    if (c < ncx) {
+      double m = 0.0;
+      for (int q = 0; q < n; ++q) {
+        double s = 0.0;
+        for (int p = 0; p < n; ++p) s += t.Iq[q * kMaxN + p] * r[p];
+        const double eq = prefix + hh * s;
+        e[c * n + q] = eq;
+        m += t.w[q] * eq;
+      }
+      emean += 0.5 * m;
+    }
+    carry += s_warp[32];
+    __syncthreads();               // s_scan and s_warp[32] are rewritten next chunk
+  }
+  const double e_bar = block_sum(emean, s_warp) / static_cast<double>(ncx);
+  for (long long i = threadIdx.x; i < ncx * n; i += blockDim.x) e[i] -= e_bar;
+}
+
+cudaError_t launch_poisson_1d(const double* rho, double* e, long long ncx, int n,
+                              const PoissonTab& t, double hphys, cudaStream_t s) {
+  k_poisson_1d<<<1, 1024, 0, s>>>(rho, e, ncx, n, t, hphys);
+  return cudaGetLastError();
+}
+
+struct Scale3 {
+  double v[3];
+};
+
+// Contravariant v speeds from a device field: a_v = scale * e (the first
+// comps components; the others zero), c_j = (2 / h_j) a_j at every x node.
+// One thread per (x cell, v direction) also records whether the sign of
+// c_j changes inside the cell (flag bit 0).  Non-finite values latch the
+// handle's error word (bit 0, reported as non-finite by dg_check).
+__global__ void k_field_speeds(const double* __restrict__ e, int comps, double scale,
+                               long long ncx, int nq, int dv, Scale3 two_over_h,
+                               double* __restrict__ cv64, float* __restrict__ cv32,
+                               int* __restrict__ flags, int* __restrict__ err) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= ncx * dv) return;
+  const long long cx = i / dv;
+  const int j = static_cast<int>(i - cx * dv);
+  bool pos = false, neg = false, bad = false;
+  for (int q = 0; q < nq; ++q) {
+    const long long node = cx * nq + q;
+    const double a = j < comps ? scale * e[node * comps + j] : 0.0;
+    const double c = two_over_h.v[j] * a;
+    bad |= !isfinite(c);
+    pos |= c > 0.0;
+    neg |= c < 0.0;
+    cv64[node * dv + j] = c;
+    cv32[node * dv + j] = static_cast<float>(c);
+  }
+  if (pos && neg) atomicOr(flags, 1);
+  if (bad) atomicOr(err, 1);
+}
+
+cudaError_t launch_field_speeds(const double* e, int comps, double scale, long long ncx, int nq,
+                                int dv, const double* two_over_hv, double* cv64, float* cv32,
+                                int* flags, int* err, cudaStream_t s) {
+  Scale3 sc{{0.0, 0.0, 0.0}};
+  for (int j = 0; j < dv; ++j) sc.v[j] = two_over_hv[j];
+  const long long n = ncx * dv;
+  const long long blocks = (n + 255) / 256;
+  k_field_speeds<<<static_cast<unsigned>(blocks), 256, 0, s>>>(e, comps, scale, ncx, nq, dv, sc,
+                                                               cv64, cv32, flags, err);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -75,6 +75,22 @@ void build_tables(int n, HostTables* t) {
     t->lp[i] = a;
     t->lm[i] = b;
   }
+  // Iq[q][i] = int_{-1}^{zeta_q} phi_i: the n-point Gauss rule mapped onto
+  // [-1, zeta_q] is exact for the degree n - 1 integrand.
+  for (int q = 0; q < n; ++q) {
+    const double half = 0.5 * (x[q] + 1.0);
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int r = 0; r < n; ++r) {
+        const double xi = -1.0 + half * (x[r] + 1.0);
+        double phi = 1.0;
+        for (int m = 0; m < n; ++m)
+          if (m != i) phi *= (xi - x[m]) / (x[i] - x[m]);
+        s += t->w[r] * phi;
+      }
+      t->Iq[q][i] = half * s;
+    }
+  }
   Tab1D<double>& d = t->t64;
   for (int q = 0; q < n; ++q) {
     d.lp[q] = t->lp[q];
