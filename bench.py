@@ -519,13 +519,16 @@ def main():
         h_u.copy_(u)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h_w2 = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        # untimed first call: the library allocates its device staging once
+        dg.rk_stage_host(h_w, h_w2, h_u, 0, 0.0, prec=PREC_FP32)
+        h_u.copy_(u)
+        torch.cuda.synchronize()
         e0.record(stream)
         for i in range(steps_e2e):
-            w0.copy_(h_w, non_blocking=True)
-            u.copy_(h_u, non_blocking=True)
-            dg.rk_stage(w0, w1, u, i % 5, dt, prec=PREC_FP32)
-            h_u.copy_(u, non_blocking=True)
-            h_w.copy_(w1, non_blocking=True)
+            # the public host-buffer call: copies in, fused stage, copies out
+            src, dst = (h_w, h_w2) if i % 2 == 0 else (h_w2, h_w)
+            dg.rk_stage_host(src, dst, h_u, i % 5, dt, prec=PREC_FP32)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps_e2e
@@ -533,7 +536,7 @@ def main():
         e2e = {"value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": n * (4 + 8), "d2h_bytes_per_step": n * (8 + 4),
                "ms_per_step": ms}
-        del h_w, h_u
+        del h_w, h_w2, h_u
 
     others = None
     if not args.no_configs:

@@ -209,6 +209,19 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
                       double dt, int prec, int adjoint, void* stream);
 
 /*
+ * dg_rk_stage with HOST buffers: w_in, w_out (type by prec) and u (FP64) live
+ * in host memory (pinned for asynchronous copies; pageable works but the
+ * copies then synchronise).  The call copies w_in and u to device staging
+ * buffers owned by the handle (n_dofs * (8 + 2 * element size) bytes,
+ * allocated on first use, kept until dg_destroy), runs the fused stage and
+ * copies u and w_out back, all ordered on ``stream``.  The host buffers must
+ * stay valid until the stream reaches the end of the call.  This is the
+ * end-to-end form of one stage for callers whose state lives on the host.
+ */
+dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
+                           double dt, int prec, void* stream);
+
+/*
  * nsteps full LSRK(5,4) steps of size dt on the FP64 state u (in place),
  * using the caller's stage vectors w0 and w1 (type by prec; contents on entry
  * ignored, on exit unspecified).  Copies u into w0, then runs 5 fused stages

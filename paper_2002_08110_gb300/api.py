@@ -139,6 +139,16 @@ class DG:
                                    self._vec(u, PREC_FP64, "u"), int(stage), float(dt), prec,
                                    int(bool(adjoint)), _stream()))
 
+    def rk_stage_host(self, w_in, w_out, u, stage, dt, prec=PREC_FP32):
+        """One fused stage on host (CPU, preferably pinned) tensors; the library
+        stages them through device memory it owns."""
+        for name, t, want in (("w_in", w_in, _WDTYPE[prec]), ("w_out", w_out, _WDTYPE[prec]),
+                              ("u", u, torch.float64)):
+            if t.is_cuda or t.dtype != want or not t.is_contiguous() or t.numel() != self.n_dofs:
+                raise ValueError(f"{name} must be a contiguous host tensor of {self.n_dofs} {want}")
+        check(self.lib.dg_rk_stage_host(self.handle, _ptr(w_in), _ptr(w_out), _ptr(u), int(stage),
+                                        float(dt), prec, _stream()))
+
     def rk_step(self, u, dt, nsteps=1, prec=PREC_FP64, adjoint=False, w0=None, w1=None):
         """Advance the FP64 state u in place by nsteps LSRK(5,4) steps."""
         if w0 is None:

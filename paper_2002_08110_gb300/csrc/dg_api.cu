@@ -251,6 +251,7 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->field_flags_d);
   cudaFree(h->vp_rho);
   cudaFree(h->vp_e);
+  cudaFree(h->host_stage);
   delete h;
 }
 
@@ -722,6 +723,47 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
   if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
   return enqueue_stage(h, w_in, w_out, u, stage, dt, prec, adjoint ? 1 : 0,
                        static_cast<cudaStream_t>(stream));
+}
+
+dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
+                           double dt, int prec, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  if (stage < 0 || stage > 4) return fail(DG_ERR_INVALID_ARG, "stage must be in [0, 4]");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  if (w_in == nullptr || w_out == nullptr || u == nullptr)
+    return fail(DG_ERR_INVALID_ARG, "w_in, w_out and u must not be NULL");
+  const size_t wb = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
+  const size_t ub = static_cast<size_t>(h->n_dofs) * 8;
+  if (ranges_overlap(w_in, w_out, wb) || ranges_overlap(w_in, wb, u, ub) ||
+      ranges_overlap(w_out, wb, u, ub))
+    return fail(DG_ERR_INVALID_ARG, "w_in, w_out and u must not overlap");
+  dg_status st;
+  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  // staging: u, then two stage vectors, each 256-byte aligned
+  auto round_up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t need = round_up(ub) + 2 * round_up(wb);
+  cudaError_t e;
+  if (h->host_stage_bytes < need) {
+    cudaFree(h->host_stage);
+    h->host_stage = nullptr;
+    h->host_stage_bytes = 0;
+    if ((e = cudaMalloc(&h->host_stage, need)) != cudaSuccess) return cuda_fail(e, "staging");
+    h->host_stage_bytes = need;
+  }
+  char* base = static_cast<char*>(h->host_stage);
+  double* du = reinterpret_cast<double*>(base);
+  void* dw_in = base + round_up(ub);
+  void* dw_out = base + round_up(ub) + round_up(wb);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(dw_in, w_in, wb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(du, u, ub, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "host-to-device copy");
+  if ((st = enqueue_stage(h, dw_in, dw_out, du, stage, dt, prec, 0, s)) != DG_OK) return st;
+  if ((e = cudaMemcpyAsync(u, du, ub, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(w_out, dw_out, wb, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "device-to-host copy");
+  return DG_OK;
 }
 
 dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,

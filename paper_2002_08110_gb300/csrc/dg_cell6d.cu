@@ -293,6 +293,30 @@ struct Mover {
   }
 };
 
+// First cell (v3 = 0) of work item ``item``.  Items cover the cells of the
+// v3 = 0 slab in tiles of 2 cells per direction (1 where the cell count is
+// odd), tiles in lexicographic order, so that the pencils in flight at one
+// time are close in all five other directions and more of their upwind
+// neighbours are still in L2 when read.
+__device__ __forceinline__ unsigned pencil_base(const KParams& p, unsigned item) {
+  unsigned tsz = 1;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) tsz *= (p.ncell[j] & 1) ? 1u : 2u;
+  unsigned tile = item / tsz, r = item - (item / tsz) * tsz;
+  unsigned base = 0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const unsigned bj = (p.ncell[j] & 1) ? 1u : 2u;
+    const unsigned off = r % bj;
+    r /= bj;
+    const unsigned nt = static_cast<unsigned>(p.ncell[j]) / bj;
+    const unsigned tj = tile % nt;
+    tile /= nt;
+    base += (tj * bj + off) * static_cast<unsigned>(p.cstride[j]);
+  }
+  return base;
+}
+
 template <typename TIN, typename TW, bool ADJ>
 __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
   extern __shared__ __align__(128) float sm6[];
@@ -338,23 +362,24 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     }
   };
   // v3 direction of a pencil (the same for all its cells and threads)
-  auto pencil_forward = [&](unsigned it) {
-    const unsigned cx = it % ncx;
+  auto pencil_forward = [&](unsigned b) {
+    const unsigned cx = b % ncx;
     float c5 = static_cast<const float*>(p.cv_tab)[(static_cast<size_t>(cx) * 64) * 3 + 2];
     if (ADJ) c5 = -c5;
     return c5 >= 0.f;
   };
-  auto pencil_cell = [&](unsigned it, int i, bool fwd) {
-    return it + static_cast<unsigned>(fwd ? i : N3 - 1 - i) * S3;
+  auto pencil_cell = [&](unsigned b, int i, bool fwd) {
+    return b + static_cast<unsigned>(fwd ? i : N3 - 1 - i) * S3;
   };
 
   // buffers: A = 0 holds the current cell, P and Q (1 and 2) are landing
   // buffers holding the x1 and x2 neighbours at the top of an iteration
   constexpr int A = 0;
   int P = 1, Q = 2;
-  bool fwd = pencil_forward(item);
+  unsigned base = pencil_base(p, item);
+  bool fwd = pencil_forward(base);
   int i = 0;
-  unsigned cell = pencil_cell(item, 0, fwd);
+  unsigned cell = pencil_cell(base, 0, fwd);
   float sp[6];
   unsigned nbr[6];
   setup(cell, sp, nbr);
@@ -368,16 +393,19 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
 
   for (;;) {
     // next cell: along the pencil, else the first cell of the next item
-    unsigned next_item = item;
+    unsigned next_item = item, next_base = base;
     bool next_fwd = fwd;
     int next_i = i + 1;
     if (next_i >= N3) {
       next_item = s_item;           // read by all threads before it changes (barriers below)
       next_i = 0;
-      if (next_item < npencils) next_fwd = pencil_forward(next_item);
+      if (next_item < npencils) {
+        next_base = pencil_base(p, next_item);
+        next_fwd = pencil_forward(next_base);
+      }
     }
     const bool has_next = next_item < npencils;
-    const unsigned next = has_next ? pencil_cell(next_item, next_i, next_fwd) : 0u;
+    const unsigned next = has_next ? pencil_cell(next_base, next_i, next_fwd) : 0u;
     const bool need_v3 = i == 0;    // the first cell's upwind v3 neighbour is not carried
     float spn[6];
     unsigned nbn[6];
@@ -516,6 +544,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     }
     if (next_item != item) {          // block-uniform
       item = next_item;
+      base = next_base;
       fwd = next_fwd;
       if (t == 0) s_item = atomicAdd(p.work, 1u);
       __syncthreads();

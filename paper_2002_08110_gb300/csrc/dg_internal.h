@@ -165,6 +165,8 @@ struct dg_ctx {
   int* field_flags_d = nullptr; // device-fed field: bit 0 mixed upwind side in a cell, bit 1 non-finite
   double* vp_rho = nullptr;     // Vlasov-Poisson scratch: rho and E at the x nodes
   double* vp_e = nullptr;
+  // device staging of the host-buffer stage call: u (FP64) and two stage vectors
+  void* host_stage = nullptr; size_t host_stage_bytes = 0;
   void* scratch = nullptr; size_t scratch_bytes = 0;
   double* partial = nullptr; int partial_blocks = 0;
   cudaStream_t capture_stream = nullptr;

@@ -169,3 +169,28 @@ def test_host_argument_errors():
     with pytest.raises(DGError):
         dg.set_launch(0, threads=64, cells_per_block=1, order=[0, 0])
     dg.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_buffer_stage_equals_device_stage(prec):
+    """dg_rk_stage_host (pinned host buffers, library-owned staging) gives the
+    same bits as dg_rk_stage on device buffers, twice in a row (the staging is
+    reused)."""
+    dg, p = random_problem(2, 2, 3, [3, 4, 3, 5], "phase", seed=9)
+    rng = np.random.default_rng(4)
+    wdt = torch.float64 if prec == 0 else torch.float32
+    u0 = torch.tensor(rng.standard_normal(dg.n_dofs))
+    w_in = torch.tensor(rng.standard_normal(dg.n_dofs)).to(wdt)
+    for stage in (1, 4):
+        du, dw_in = u0.cuda(), w_in.cuda()
+        dw_out = torch.empty_like(dw_in)
+        dg.rk_stage(dw_in, dw_out, du, stage, 0.01, prec=prec)
+        hu = u0.clone().pin_memory()
+        hw_in = w_in.clone().pin_memory()
+        hw_out = torch.empty_like(hw_in).pin_memory()
+        dg.rk_stage_host(hw_in, hw_out, hu, stage, 0.01, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(hu, du.cpu())
+        assert torch.equal(hw_out, dw_out.cpu())
+    dg.check()
+    dg.close()
