@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=8, help="cells per direction (default 8)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--kernel-variant", type=int, default=None,
+                    help="6D cell kernel for the FP32-sweep paths (1: 64 threads per cell, "
+                         "2: 128 threads per cell); default: the library's choice")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-reps", type=int, default=2)
@@ -420,6 +423,10 @@ def main():
     zeta, _ = reference_nodes(w.k)
     E = W.e_table(w, zeta)
     dg = DG(e_nodes=E, **W.dg_kwargs(w))
+    if args.kernel_variant is not None:
+        for prec in (PREC_FP32, PREC_MIXED):
+            c = dg.get_launch(prec)
+            dg.set_launch(prec, c["threads"], c["cells_per_block"], c["order"], args.kernel_variant)
     n = dg.n_dofs
     dt, _ = W.time_step(w)
     u0 = W.separable_state(w, zeta, xp=torch, device=dev)

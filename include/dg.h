@@ -123,7 +123,9 @@ typedef struct {
     int threads;              /* threads per block                          */
     int cells_per_block;      /* cells handled by one block (small cells)   */
     int order[6];             /* order in which the d directions are swept  */
-    int variant;              /* 0 = generic, 1 = specialised (if present)  */
+    int variant;              /* 0 = generic; 6D, k = 3, FP32 sweeps: 1 = specialised,
+                                 64 threads per cell; 2 = specialised, 128 threads per
+                                 cell (default)                              */
 } dg_launch;
 
 /* Library version (DG_ABI_VERSION). */

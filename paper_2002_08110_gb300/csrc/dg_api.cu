@@ -144,7 +144,7 @@ dg_status ensure_scratch(dg_ctx* h, int prec) {
 
 cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
                         cudaStream_t s) {
-  if (cfg.variant == 1 && h->d == 6 && h->n == 4 && h->uniform_sides) {
+  if (cfg.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides) {
     cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
     if (e != cudaErrorNotSupported) return e;
   }
@@ -215,7 +215,7 @@ void default_cfg(dg_ctx* h) {
     while (cpb > 1 && generic_smem_bytes(h->d, h->n, combo_of(prec), cpb) == 0) --cpb;
     c.cells_per_block = cpb;
     if (h->npc >= 1024) c.threads = 512;
-    if (h->d == 6 && h->n == 4 && prec != DG_PREC_FP64) c.variant = 1;
+    if (h->d == 6 && h->n == 4 && prec != DG_PREC_FP64) c.variant = 2;
   }
 }
 
@@ -224,7 +224,7 @@ dg_status validate_cfg(const dg_ctx* h, int prec, const LaunchCfg& c) {
     return fail(DG_ERR_INVALID_ARG, "threads must be a multiple of 32 in [32, 512]");
   if (c.cells_per_block < 1 || c.cells_per_block > 4096)
     return fail(DG_ERR_INVALID_ARG, "cells_per_block out of range");
-  if (c.variant < 0 || c.variant > 1) return fail(DG_ERR_INVALID_ARG, "unknown variant");
+  if (c.variant < 0 || c.variant > 2) return fail(DG_ERR_INVALID_ARG, "unknown variant");
   bool seen[kMaxDim] = {false};
   for (int j = 0; j < h->d; ++j) {
     if (c.order[j] < 0 || c.order[j] >= h->d || seen[c.order[j]])
@@ -935,8 +935,8 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
     if (static_cast<long long>(c) * h->npc <= 8192 &&
         (generic_smem_bytes(h->d, h->n, combo, c) != 0 || c == 1))
       cpbs.push_back(c);
-  for (int variant = 0; variant < 2; ++variant) {
-    if (variant == 1 && !(h->d == 6 && h->n == 4 && prec != DG_PREC_FP64)) continue;
+  for (int variant = 0; variant < 3; ++variant) {
+    if (variant >= 1 && !(h->d == 6 && h->n == 4 && prec != DG_PREC_FP64)) continue;
     for (int rev = 0; rev < 2; ++rev)
       for (int t : threads_c)
         for (int c : cpbs) {
@@ -948,7 +948,7 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
           if (rev)
             for (int j = 0; j < h->d; ++j) cfg.order[j] = h->d - 1 - j;
           // the specialised kernel fixes 64 threads per cell and its sweep order
-          if (variant == 1 && (c > 2 || rev || t != 128)) continue;
+          if (variant >= 1 && (c > 2 || rev || t != 128)) continue;
           cands.push_back(cfg);
         }
   }

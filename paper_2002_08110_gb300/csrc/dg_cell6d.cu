@@ -91,6 +91,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
+// Brings `bytes` (a multiple of 16, 16-byte aligned) into L2 ahead of use,
+// marked evict-first: the FP64 state is read once per stage.
+__device__ __forceinline__ void prefetch_l2_once(const void* src, unsigned bytes) {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src),
+               "r"(bytes), "l"(pol)
+               : "memory");
+}
+
 // Orders this thread's earlier generic-proxy accesses of shared memory before
 // later async-proxy (TMA) writes to it; every reuse of a buffer by the TMA is
 // preceded by this fence in all threads and then a block barrier.
@@ -592,6 +602,546 @@ cudaError_t launch6(KParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Pair variant: 128 threads per cell, two threads per block of 64 values.
+//
+// Thread T (warp w, lane L) works on block t = 16 w + (L & 7) + 8 (L >> 4) and
+// holds the 32 elements of that block whose middle digit has parity
+// h = (L >> 3) & 1: local index k = a + 4 b + 8 c is element
+// e = a + 4 (h + 2 b) + 16 c.  Lines along the first and last digit are
+// thread-local (8 lines each); lines along the middle digit are split between
+// the thread and its partner (lane L ^ 8, same t, other h), which exchange
+// their halves by warp shuffles.  Half the registers per thread of the
+// 64-thread variant give twice the warps per SM.  With this lane mapping each
+// group of 8 lanes reads 8 different 16-byte rows (phase X) and the two halves
+// of a warp read columns 4 rows apart (phase V), so both views stay free of
+// bank conflicts with the 68-float padding.
+constexpr unsigned kFull = 0xffffffffu;
+
+// element offset (relative to the half's base, 4 h) of local index k
+__device__ __forceinline__ constexpr int poff(int k) { return (k & 3) + 8 * ((k >> 2) & 1) + 16 * (k >> 3); }
+
+template <bool ROWS>
+__device__ __forceinline__ const float* pview(const float* buf, int t, int h) {
+  return ROWS ? buf + t * kPad + 4 * h : buf + t + 4 * h * kPad;
+}
+template <bool ROWS>
+__device__ __forceinline__ float pval(const float* v, int off) {
+  return ROWS ? v[off] : v[off * kPad];
+}
+template <bool ROWS>
+__device__ __forceinline__ void load_half(float (&x)[32], const float* v) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {          // i = b + 2 c: four values along the first digit
+    const int off = poff(4 * i);
+    if constexpr (ROWS) {
+      const float4 a = *reinterpret_cast<const float4*>(v + off);
+      x[4 * i] = a.x;
+      x[4 * i + 1] = a.y;
+      x[4 * i + 2] = a.z;
+      x[4 * i + 3] = a.w;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[4 * i + a] = v[(off + a) * kPad];
+    }
+  }
+}
+
+// weight product of element e = a + 4 (h + 2 b) + 16 c
+__device__ __forceinline__ float wprod_p(const float* w, int k, int h) {
+  return w[k & 3] * w[h + 2 * ((k >> 2) & 1)] * w[k >> 3];
+}
+
+// local index of point p on line l: J = 0 (first digit, lines (b, c)),
+// J = 2 (last digit, lines (a, b)); J = 1 (middle digit): lines (a, c), the
+// thread's own points b = 0, 1
+template <int J>
+__device__ __forceinline__ constexpr int pk(int l, int p) {
+  return J == 0 ? p + 4 * (l & 1) + 8 * (l >> 1) : (J == 2 ? (l & 3) + 4 * (l >> 2) + 8 * p
+                                                          : (l & 3) + 4 * p + 8 * (l >> 2));
+}
+
+// Upwind neighbour traces of the thread's lines along J from a landing
+// buffer view (J = 0, 2: 8 lines; J = 1: 16 lines, partial sums over the two
+// halves added across the pair).
+template <int J, bool ROWS, bool ADJ>
+__device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, float c, int h,
+                                            const Tab1D<float>& T) {
+  const int side = c > 0.f ? 0 : 1;
+  float lw[4];
+  if constexpr (J == 1) {
+    lw[0] = c_lw[side][h];
+    lw[1] = c_lw[side][h + 2];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
+  }
+#pragma unroll
+  for (int l = 0; l < 16; ++l) tr[l] = 0.f;
+  // the neighbour's values arrive four at a time (first digit a = 0..3 at
+  // fixed b, c) and are folded into the traces at once
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int b = i & 1, cc = i >> 1;
+    const int off = poff(4 * i);
+    float x[4];
+    if constexpr (ROWS) {
+      const float4 v = *reinterpret_cast<const float4*>(nbv + off);
+      x[0] = v.x;
+      x[1] = v.y;
+      x[2] = v.z;
+      x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) x[a] = nbv[(off + a) * kPad];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (ADJ) x[a] *= wprod_p(T.winv, 4 * i + a, h);
+      if constexpr (J == 0) tr[b + 2 * cc] = fmaf(lw[a], x[a], tr[b + 2 * cc]);
+      else if constexpr (J == 2) tr[a + 4 * b] = fmaf(lw[cc], x[a], tr[a + 4 * b]);
+      else tr[a + 4 * cc] = fmaf(lw[b], x[a], tr[a + 4 * cc]);
+    }
+  }
+  if constexpr (J == 1) {
+#pragma unroll
+    for (int l = 0; l < 16; ++l) tr[l] += __shfl_xor_sync(kFull, tr[l], 8);
+  }
+}
+
+// r += c (G u + L_nb t) on the thread's 8 local lines along J = 0 or 2, for
+// the upwind side SIDE (compile time: the 1D matrices are then constant-bank
+// operands and take no registers).  The side is uniform over a block (one
+// upwind side per cell and direction), so the branch in lines_p does not
+// diverge.
+template <int J, int SIDE>
+__device__ __forceinline__ void lines_local(float (&r)[32], const float (&u)[32],
+                                            const float (&tr)[16], float c, float tscale) {
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    const float t = tscale * tr[l];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = c_Ln[SIDE][q] * t;
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) acc = fmaf(c_G[SIDE][q * 4 + pp], u[pk<J>(l, pp)], acc);
+      r[pk<J>(l, q)] = fmaf(c, acc, r[pk<J>(l, q)]);
+    }
+  }
+}
+
+// The 16 split lines along the middle digit: the thread owns rows q = h and
+// h + 2 and receives the partner's two values of each line by shuffles.  The
+// rows depend on h, so their entries (scaled by c) are loaded into registers.
+__device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32],
+                                            const float (&tr)[16], float c, float tscale, int h) {
+  const int side = c > 0.f ? 0 : 1;
+  // columns ordered (own b = 0, own b = 1, partner b = 0, partner b = 1)
+  float G[2][4], Ln[2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int q = h + 2 * b;
+    G[b][0] = c * c_G[side][q * 4 + h];
+    G[b][1] = c * c_G[side][q * 4 + h + 2];
+    G[b][2] = c * c_G[side][q * 4 + 1 - h];
+    G[b][3] = c * c_G[side][q * 4 + 3 - h];
+    Ln[b] = c * c_Ln[side][q];
+  }
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    const float u0 = u[pk<1>(l, 0)], u1 = u[pk<1>(l, 1)];
+    const float v0 = __shfl_xor_sync(kFull, u0, 8), v1 = __shfl_xor_sync(kFull, u1, 8);
+    const float t = tscale * tr[l];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int k = pk<1>(l, b);
+      float acc = fmaf(Ln[b], t, r[k]);
+      acc = fmaf(G[b][0], u0, acc);
+      acc = fmaf(G[b][1], u1, acc);
+      acc = fmaf(G[b][2], v0, acc);
+      acc = fmaf(G[b][3], v1, acc);
+      r[k] = acc;
+    }
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], const float (&tr)[16],
+                                        float c, float tscale, int h) {
+  if constexpr (J == 1) {
+    lines_split(r, u, tr, c, tscale, h);
+  } else {
+    if (c > 0.f)
+      lines_local<J, 0>(r, u, tr, c, tscale);
+    else
+      lines_local<J, 1>(r, u, tr, c, tscale);
+  }
+}
+
+// own outflow traces along the last digit (8 local lines)
+__device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32], float c) {
+  const int side = c > 0.f ? 0 : 1;
+  float lw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) {
+    float s = 0.f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) s = fmaf(lw[p], u[pk<2>(l, p)], s);
+    to[l] = s;
+  }
+}
+
+template <int J, bool ROWS, bool ADJ>
+__device__ __forceinline__ void direction_p(float (&r)[32], const float (&u)[32], const float* nbv,
+                                            float c, float wthread, int h, const Tab1D<float>& T) {
+  float tr[16];
+  nb_traces_p<J, ROWS, ADJ>(tr, nbv, c, h, T);
+  lines_p<J>(r, u, tr, c, ADJ ? wthread : 1.f, h);
+}
+
+// Block-uniform description of a work item (a v3 pencil), kept in shared
+// memory so that per-cell neighbour indices need no integer division.
+struct PencilInfo {
+  unsigned base;       // first cell (v3 = 0)
+  unsigned cx, cvb;    // x cell, and v cell of the first cell
+  unsigned coord[5];   // cell coordinates in x1, x2, x3, v1, v2
+  unsigned fwd;        // walk direction along v3 (upwind first)
+};
+
+template <bool ADJ>
+__device__ __forceinline__ void pencil_info(const KParams& p, unsigned item, PencilInfo& pi) {
+  unsigned tsz = 1;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) tsz *= (p.ncell[j] & 1) ? 1u : 2u;
+  unsigned tile = item / tsz, r = item - (item / tsz) * tsz;
+  unsigned base = 0;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const unsigned bj = (p.ncell[j] & 1) ? 1u : 2u;
+    const unsigned off = r % bj;
+    r /= bj;
+    const unsigned nt = static_cast<unsigned>(p.ncell[j]) / bj;
+    const unsigned tj = tile % nt;
+    tile /= nt;
+    pi.coord[j] = tj * bj + off;
+    base += pi.coord[j] * static_cast<unsigned>(p.cstride[j]);
+  }
+  const unsigned ncx = static_cast<unsigned>(p.ncx);
+  pi.base = base;
+  pi.cx = base % ncx;
+  pi.cvb = base / ncx;
+  float c5 = static_cast<const float*>(p.cv_tab)[(static_cast<size_t>(pi.cx) * 64) * 3 + 2];
+  if (ADJ) c5 = -c5;
+  pi.fwd = c5 >= 0.f ? 1u : 0u;
+}
+
+// upwind neighbour along j of a cell at coordinate cj (periodic wrap)
+__device__ __forceinline__ unsigned nb_c(const KParams& p, unsigned cell, unsigned cj, int j,
+                                         float c) {
+  const unsigned st = static_cast<unsigned>(p.cstride[j]);
+  const unsigned nj = static_cast<unsigned>(p.ncell[j]);
+  if (c > 0.f) return cj == 0 ? cell + (nj - 1) * st : cell - st;
+  return cj == nj - 1 ? cell - (nj - 1) * st : cell + st;
+}
+
+// MODE 0: operator application (dst = K); MODE 1: fused LSRK stage.
+template <typename TIN, typename TW, bool ADJ, int MODE>
+__global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
+  extern __shared__ __align__(128) float sm6[];
+  __shared__ Pipe pipe;
+  __shared__ unsigned s_item;
+  __shared__ PencilInfo s_pi[2];      // current and next item
+  const int T_ = threadIdx.x;
+  const int lane = T_ & 31;
+  const int h = (lane >> 3) & 1;
+  const int t = 16 * (T_ >> 5) + (lane & 7) + 8 * (lane >> 4);
+  const bool issuer = h == 0;          // one thread per block row issues its copies
+  const Tab1D<float>& T = p.t32;
+  const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
+  const unsigned S3 = static_cast<unsigned>(p.cstride[5]);   // pencils along v3
+  const unsigned SV3 = S3 / static_cast<unsigned>(p.ncx);    // v-cell stride of v3
+  const int N3 = p.ncell[5];
+  const unsigned npencils = S3;
+  const float winv_t = ADJ ? wprod(T.winv, t) : 1.f;
+  const float w_t = ADJ ? wprod(T.w, t) : 1.f;
+  // the thread's outflow traces along v3, carried to the next cell of the pencil
+  float* carried = sm6 + 3 * kCellSmem + T_ * 8;
+  int bad = 0;
+
+  if (T_ == 0) {
+    for (int b = 0; b < kNumBuf; ++b) mbar_init(&pipe.bar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const unsigned it = atomicAdd(p.work, 1u);
+    s_item = it;
+    if (it < npencils) pencil_info<ADJ>(p, it, s_pi[0]);
+  }
+  __syncthreads();
+  unsigned item = s_item;
+  if (item >= npencils) return;
+  Mover<TIN> mv{sm6, &pipe};
+  int slot = 0;
+  auto cellp = [&](unsigned c) { return src + static_cast<size_t>(c) * 4096; };
+  auto issue = [&](int b, unsigned c) {
+    if (issuer) mv.issue(b, cellp(c), t);
+  };
+  auto v3c = [&](const PencilInfo& pi, int i) {
+    return pi.fwd ? static_cast<unsigned>(i) : static_cast<unsigned>(N3 - 1 - i);
+  };
+  // speeds of the thread's nodes and the upwind neighbours of cell i of a pencil
+  auto setup = [&](const PencilInfo& pi, int i, unsigned& cell, float (&sp)[6],
+                   unsigned (&nbr)[6]) {
+    const unsigned c5 = v3c(pi, i);
+    cell = pi.base + c5 * S3;
+    const unsigned cv = pi.cvb + c5 * SV3;
+    const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * 64 + t) * 3;
+    const float* ctv = static_cast<const float*>(p.cv_tab) + (static_cast<size_t>(pi.cx) * 64 + t) * 3;
+    sp[0] = ctx[0];
+    sp[1] = ctx[1];
+    sp[2] = ctx[2];
+    sp[3] = ctv[0];
+    sp[4] = ctv[1];
+    sp[5] = ctv[2];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (ADJ) sp[j] = -sp[j];
+      nbr[j] = nb_c(p, cell, j < 5 ? pi.coord[j] : c5, j, sp[j]);
+    }
+  };
+
+  constexpr int A = 0;
+  int P = 1, Q = 2;
+  int i = 0;
+  unsigned cell;
+  float sp[6];
+  unsigned nbr[6];
+  setup(s_pi[slot], 0, cell, sp, nbr);
+  issue(A, cell);
+  issue(P, nbr[0]);
+  issue(Q, nbr[1]);
+  bool ok = true;
+  __syncthreads();
+  if (T_ == 0) {                                 // the item after this pencil
+    const unsigned it = atomicAdd(p.work, 1u);
+    s_item = it;
+    if (it < npencils) pencil_info<ADJ>(p, it, s_pi[1]);
+  }
+  __syncthreads();
+
+  for (;;) {
+    unsigned next_item = item;
+    int next_slot = slot;
+    int next_i = i + 1;
+    if (next_i >= N3) {
+      next_item = s_item;           // read by all threads before it changes (barriers below)
+      next_slot = slot ^ 1;
+      next_i = 0;
+    }
+    const bool has_next = next_item < npencils;
+    const bool need_v3 = i == 0;    // the first cell's upwind v3 neighbour is not carried
+    // the next cell's upwind x1 and x2 neighbours (prefetched during phase V);
+    // its full setup follows at the end of this iteration
+    unsigned next = 0, nx0 = 0, nx1 = 0;
+    if (has_next) {
+      const PencilInfo& pn = s_pi[next_slot];
+      const unsigned c5 = v3c(pn, next_i);
+      next = pn.base + c5 * S3;
+      const unsigned cv = pn.cvb + c5 * SV3;
+      const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * 64 + t) * 3;
+      float c0 = ctx[0], c1 = ctx[1];
+      if (ADJ) {
+        c0 = -c0;
+        c1 = -c1;
+      }
+      nx0 = nb_c(p, next, pn.coord[0], 0, c0);
+      nx1 = nb_c(p, next, pn.coord[1], 1, c1);
+    }
+    // the cell's FP64 state is needed only in the epilogue: ask L2 for it now
+    // (one 512-byte row per issuing thread)
+    if (MODE == 1 && issuer) prefetch_l2_once(p.u + static_cast<size_t>(cell) * 4096 + t * 64, 512);
+    float u[32], r[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) r[e] = 0.f;
+
+    // ---- phase X: rows, directions x1, x2 (split), x3
+    ok &= mv.wait(A, p.err);
+    load_half<true>(u, pview<true>(sm6 + A * kCellSmem, t, h));
+    if (ADJ) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) u[k] *= winv_t * wprod_p(T.winv, k, h);
+    }
+    ok &= mv.wait(P, p.err);
+    direction_p<0, true, ADJ>(r, u, pview<true>(sm6 + P * kCellSmem, t, h), sp[0], winv_t, h, T);
+    fence_async_smem();
+    __syncthreads();
+    issue(P, nbr[2]);                            // x3
+    ok &= mv.wait(Q, p.err);
+    direction_p<1, true, ADJ>(r, u, pview<true>(sm6 + Q * kCellSmem, t, h), sp[1], winv_t, h, T);
+    fence_async_smem();
+    __syncthreads();
+    issue(Q, nbr[3]);                            // v1
+    ok &= mv.wait(P, p.err);
+    direction_p<2, true, ADJ>(r, u, pview<true>(sm6 + P * kCellSmem, t, h), sp[2], winv_t, h, T);
+    __syncthreads();                             // P is free: it takes the phase X result
+    {
+      float* rb = sm6 + P * kCellSmem + t * kPad + 4 * h;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        *reinterpret_cast<float4*>(rb + poff(4 * k)) =
+            make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+    }
+    __syncthreads();
+
+    // ---- phase V: columns, directions v1, v2 (split), v3
+    load_half<false>(u, pview<false>(sm6 + A * kCellSmem, t, h));
+    load_half<false>(r, pview<false>(sm6 + P * kCellSmem, t, h));
+    if (ADJ) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) u[k] *= winv_t * wprod_p(T.winv, k, h);
+    }
+    fence_async_smem();
+    __syncthreads();                             // A and P are free
+    if (has_next) issue(A, next);                // the next cell
+    issue(P, nbr[4]);                            // v2
+    ok &= mv.wait(Q, p.err);
+    direction_p<0, false, ADJ>(r, u, pview<false>(sm6 + Q * kCellSmem, t, h), sp[3], winv_t, h, T);
+    fence_async_smem();
+    __syncthreads();
+    if (need_v3)
+      issue(Q, nbr[5]);                          // v3 (wrapped, not carried)
+    else if (has_next)
+      issue(Q, nx0);                             // x1 of the next cell
+    ok &= mv.wait(P, p.err);
+    direction_p<1, false, ADJ>(r, u, pview<false>(sm6 + P * kCellSmem, t, h), sp[4], winv_t, h, T);
+    fence_async_smem();
+    __syncthreads();
+    if (has_next) issue(P, need_v3 ? nx0 : nx1);        // x1 or x2 of the next cell
+    float tr[16];
+    if (need_v3) {
+      ok &= mv.wait(Q, p.err);
+      nb_traces_p<2, false, ADJ>(tr, pview<false>(sm6 + Q * kCellSmem, t, h), sp[5], h, T);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tr[k] *= ADJ ? winv_t : 1.f;
+    } else {
+      const float4 c0 = *reinterpret_cast<const float4*>(carried);
+      const float4 c1 = *reinterpret_cast<const float4*>(carried + 4);
+      tr[0] = c0.x; tr[1] = c0.y; tr[2] = c0.z; tr[3] = c0.w;
+      tr[4] = c1.x; tr[5] = c1.y; tr[6] = c1.z; tr[7] = c1.w;
+    }
+    {
+      float to[8];
+      own_traces_p(to, u, sp[5]);
+      *reinterpret_cast<float4*>(carried) = make_float4(to[0], to[1], to[2], to[3]);
+      *reinterpret_cast<float4*>(carried + 4) = make_float4(to[4], to[5], to[6], to[7]);
+    }
+
+    // ---- last direction fused with step 5: scatter / LSRK stage update
+    const size_t g0 = static_cast<size_t>(cell) * 4096 + t + 256 * h;
+    if constexpr (MODE == 0) {
+      lines_p<2>(r, u, tr, sp[5], 1.f, h);
+      TW* dst = static_cast<TW*>(p.dst);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        float K = r[k];
+        if (ADJ) K *= w_t * wprod_p(T.w, k, h);
+        bad |= !isfinite(K);
+        __stcs(dst + g0 + 64 * poff(k), cvt<TW>(K));
+      }
+    } else {
+      // the FP64 state streams through in chunks of 8 values, each chunk's
+      // loads issued while the previous one is used
+      double* uu = p.u;
+      double ua[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) ua[k] = __ldcs(uu + g0 + 64 * poff(k));
+      lines_p<2>(r, u, tr, sp[5], 1.f, h);
+      TW* dst = static_cast<TW*>(p.dst);
+      const float bf = static_cast<float>(p.b_dt);
+      const float af = static_cast<float>(p.a_dt);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        double ub[8];
+        if (ch < 3) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) ub[k] = __ldcs(uu + g0 + 64 * poff(8 * (ch + 1) + k));
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int k = 8 * ch + kk;
+          float K = r[k];
+          if (ADJ) K *= w_t * wprod_p(T.w, k, h);
+          bad |= !isfinite(K);
+          const size_t g = g0 + 64 * poff(k);
+          const double un = ua[kk] + f32_to_f64(bf * K);
+          __stcs(uu + g, un);
+          if constexpr (sizeof(TW) == 4) {
+            __stcs(dst + g, p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(ua[kk])));
+          } else {
+            __stcs(dst + g, p.last_stage ? un : ua[kk] + p.a_dt * f32_to_f64(K));
+          }
+        }
+        if (ch < 3) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) ua[k] = ub[k];
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();                             // Q is free; s_item was read by all threads
+    if (!ok || !has_next) break;
+    if (need_v3) issue(Q, nx1);                  // x2 of the next cell
+    else {
+      const int tmp = P;                         // x1 landed in Q, x2 in P
+      P = Q;
+      Q = tmp;
+    }
+    if (next_item != item) {          // block-uniform
+      item = next_item;
+      slot = next_slot;
+      if (T_ == 0) {
+        const unsigned it = atomicAdd(p.work, 1u);
+        s_item = it;
+        if (it < npencils) pencil_info<ADJ>(p, it, s_pi[slot ^ 1]);
+      }
+      __syncthreads();
+    }
+    i = next_i;
+    setup(s_pi[slot], i, cell, sp, nbr);
+  }
+  if (!ok && sizeof(TIN) == 4) {
+    for (int b = 0; b < kNumBuf; ++b) {
+      const long long t0 = clock64();
+      while (clock64() - t0 < kWaitCycles)
+        if (mbar_try_wait(&pipe.bar[b], (mv.phase >> b) & 1u)) break;
+    }
+  }
+  if (bad) atomicOr(p.err, 1);
+}
+
+template <typename TIN, typename TW, bool ADJ>
+cudaError_t launch6p(KParams& p, cudaStream_t s) {
+  auto kern = p.mode == 0 ? k_cell6d4p<TIN, TW, ADJ, 0> : k_cell6d4p<TIN, TW, ADJ, 1>;
+  // three cell buffers and the carried v3 traces (8 floats per thread)
+  const size_t smem = (static_cast<size_t>(kNumBuf) * kCellSmem + 128 * 8) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const long long npencils = p.cstride[5];
+  const long long grid = std::min<long long>(npencils, static_cast<long long>(sms) * per_sm);
+  e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  kern<<<static_cast<unsigned>(grid), 128, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t init_cell6d_tables(const Tab1D<float>& t) {
@@ -613,8 +1163,14 @@ cudaError_t init_cell6d_tables(const Tab1D<float>& t) {
 }
 
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
-  (void)cfg;
   if (p.dx != 3 || p.dv != 3 || p.ncells >= (1LL << 31)) return cudaErrorNotSupported;
+  if (cfg.variant == 2) {
+    if (combo == kFFF)
+      return p.adjoint ? launch6p<float, float, true>(p, s) : launch6p<float, float, false>(p, s);
+    if (combo == kFDD)
+      return p.adjoint ? launch6p<double, double, true>(p, s) : launch6p<double, double, false>(p, s);
+    return cudaErrorNotSupported;
+  }
   if (combo == kFFF)
     return p.adjoint ? launch6<float, float, true>(p, s) : launch6<float, float, false>(p, s);
   if (combo == kFDD)

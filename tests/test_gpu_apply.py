@@ -141,7 +141,7 @@ def test_specialised_6d_kernel_matches_generic(prec, adjoint):
         ut = torch.tensor(u, device="cuda", dtype=dt)
         uin = ut.double().cpu().numpy()
         outs = []
-        for variant in (0, 1):
+        for variant in (0, 1, 2):
             dg.set_launch(prec, threads=256, cells_per_block=1, variant=variant)
             f = dg.apply_adjoint if adjoint else dg.apply
             outs.append(f(ut, prec=prec).double().cpu().numpy())
@@ -154,7 +154,8 @@ def test_specialised_6d_kernel_matches_generic(prec, adjoint):
             ref = p.apply(uin)
             for o in outs:
                 assert np.linalg.norm(o - ref) <= TOL32 * scale, name
-        assert np.linalg.norm(outs[0] - outs[1]) <= 4 * TOL32 * scale, name
+        for o in outs[1:]:
+            assert np.linalg.norm(outs[0] - o) <= 4 * TOL32 * scale, name
         dg.close()
 
 

@@ -23,16 +23,20 @@ def _lib():
 
 
 @pytest.mark.parametrize("case", [(1, 1, 3, (6, 5)), (2, 2, 2, (2, 3, 2, 2)),
-                                  (3, 3, 3, (2, 1, 2, 1, 2, 2)), "6d_uniform"],
+                                  (3, 3, 3, (2, 1, 2, 1, 2, 2)), "6d_uniform", "6d_uniform_v1"],
                          ids=lambda c: c if isinstance(c, str) else f"{c[0]}x{c[1]}v_k{c[2]}")
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("stage", [0, 2, 4])
 def test_fused_stage(case, prec, stage):
     """K = L(w); u <- u + b_s dt K; w_out = u_old + a_s dt K (s < 4) or u_new.
-    "6d_uniform" runs the specialised 6D kernel (no sign change inside cells)."""
-    if case == "6d_uniform":
+    "6d_uniform*" run the specialised 6D kernels (no sign change inside cells)."""
+    if case.__class__ is str:
+        # the specialised 6D kernels: 128 threads per cell (default) or 64 ("_v1")
         dg, p = dg_for(W.shrink(W.config_6d(), cells_x=(2, 2, 2), cells_v=(2, 2, 2)))
         assert dg.info.uniform_sides == 1
+        if case.endswith("_v1") and prec != 0:
+            c = dg.get_launch(prec)
+            dg.set_launch(prec, c["threads"], c["cells_per_block"], c["order"], 1)
     else:
         dx, dv, k, cells = case
         dg, p = random_problem(dx, dv, k, cells, "phase", seed=11)
