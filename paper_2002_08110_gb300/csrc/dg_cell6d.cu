@@ -2,7 +2,9 @@
 // FP32 sweeps and fluxes.
 //
 // A cell has 4096 values, q = q_x + 64 q_v with q_x = (q1,q2,q3), q_v = (q4,q5,q6)
-// (x_1 fastest).  One block of 64 threads processes one cell at a time, in two
+// (x_1 fastest).  Two variants: 64 threads per cell (described here) and 128
+// threads per cell (the "pair variant" below, the default).  In the first, one
+// block of 64 threads processes one cell at a time, in two
 // phases that follow Algorithm 2's split of the cell work into the x-space
 // part and the v-space part:
 //   phase X: thread t owns the v node q_v = t and holds the 4x4x4 x-block of
@@ -40,6 +42,10 @@
 // (u += b dt K in FP64; w_out = u + a dt K).  Adjoint: L^T = M L(-a) M^{-1}.
 // FP64 input (DG_PREC_MIXED) is converted while the threads copy it into
 // shared memory themselves.
+#include <cstring>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "dg_convert.cuh"
 #include "dg_generic.cuh"
 
@@ -613,38 +619,66 @@ cudaError_t launch6(KParams& p, cudaStream_t s) {
 // thread-local (8 lines each); lines along the middle digit are split between
 // the thread and its partner (lane L ^ 8, same t, other h), which exchange
 // their halves by warp shuffles.  Half the registers per thread of the
-// 64-thread variant give twice the warps per SM.  With this lane mapping each
-// group of 8 lanes reads 8 different 16-byte rows (phase X) and the two halves
-// of a warp read columns 4 rows apart (phase V), so both views stay free of
-// bank conflicts with the 68-float padding.
+// 64-thread variant give twice the warps per SM.
+//
+// Data movement: each cell arrives by one tensor copy (cp.async.bulk.tensor,
+// two 8 KB boxes issued by a single thread, mbarrier completion) into an
+// unpadded buffer with the 128-byte swizzle, instead of 64 per-thread bulk
+// copies into padded rows: the per-lane copies serialise in the copy unit and
+// cost the issuing warps more than their compute.  With the lane mapping
+// above, each group of 8 lanes reads 8 rows with distinct swizzle phases
+// (phase X, 16-byte reads) and the two halves of a warp read columns in rows
+// 4 apart, whose chunks differ in the swizzle's top bit (phase V, 4-byte
+// reads), so both views are free of bank conflicts.
 constexpr unsigned kFull = 0xffffffffu;
 
 // element offset (relative to the half's base, 4 h) of local index k
 __device__ __forceinline__ constexpr int poff(int k) { return (k & 3) + 8 * ((k >> 2) & 1) + 16 * (k >> 3); }
 
+// Cell buffers hold the 64 x 64 values of a cell (row = v node, column = x
+// node) as the tensor copy writes them: two 8 KB halves (columns 0-31 and
+// 32-63), each 64 lines of 128 bytes, the 16-byte chunks of line r stored at
+// chunk index j ^ (r & 7) (128-byte swizzle).  Element (r, c) is at float
+//   (c >> 5) * 2048 + 32 r + 4 ((((c >> 2) & 7) ^ (r & 7))) + (c & 3).
+// The thread's offsets: phase X (row t) per (b, c & 1) for the four-value
+// groups of the first digit, phase V (column t) per first digit a.
+constexpr int kCellF = 4096;          // floats per cell buffer
+
+__device__ __forceinline__ void offsets_x(int (&o)[4], int t, int h) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int b = i & 1, cc = i >> 1;
+    o[i] = 32 * t + 4 * ((h + 2 * b + 4 * cc) ^ (t & 7));
+  }
+}
+__device__ __forceinline__ void offsets_v(int (&o)[4], int t, int h) {
+  const int jt = ((t >> 2) & 7) ^ (4 * h);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) o[a] = (t >> 5) * 2048 + (t & 3) + 128 * h + 32 * a + 4 * (jt ^ a);
+}
+// the four values of group i = b + 2 c (first digit a = 0..3)
 template <bool ROWS>
-__device__ __forceinline__ const float* pview(const float* buf, int t, int h) {
-  return ROWS ? buf + t * kPad + 4 * h : buf + t + 4 * h * kPad;
+__device__ __forceinline__ void load4(float (&x)[4], const float* buf, const int (&o)[4], int i) {
+  const int b = i & 1, cc = i >> 1;
+  if constexpr (ROWS) {
+    const float4 v = *reinterpret_cast<const float4*>(buf + o[b + 2 * (cc & 1)] + (cc >> 1) * 2048);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) x[a] = buf[o[a] + 256 * b + 512 * cc];
+  }
 }
 template <bool ROWS>
-__device__ __forceinline__ float pval(const float* v, int off) {
-  return ROWS ? v[off] : v[off * kPad];
-}
-template <bool ROWS>
-__device__ __forceinline__ void load_half(float (&x)[32], const float* v) {
+__device__ __forceinline__ void load_half(float (&x)[32], const float* buf, const int (&o)[4]) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {          // i = b + 2 c: four values along the first digit
-    const int off = poff(4 * i);
-    if constexpr (ROWS) {
-      const float4 a = *reinterpret_cast<const float4*>(v + off);
-      x[4 * i] = a.x;
-      x[4 * i + 1] = a.y;
-      x[4 * i + 2] = a.z;
-      x[4 * i + 3] = a.w;
-    } else {
+  for (int i = 0; i < 8; ++i) {
+    float v[4];
+    load4<ROWS>(v, buf, o, i);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) x[4 * i + a] = v[(off + a) * kPad];
-    }
+    for (int a = 0; a < 4; ++a) x[4 * i + a] = v[a];
   }
 }
 
@@ -666,7 +700,7 @@ __device__ __forceinline__ constexpr int pk(int l, int p) {
 // buffer view (J = 0, 2: 8 lines; J = 1: 16 lines, partial sums over the two
 // halves added across the pair).
 template <int J, bool ROWS, bool ADJ>
-__device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, float c, int h,
+__device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, const int (&o)[4], float c, int h,
                                             const Tab1D<float>& T) {
   const int side = c > 0.f ? 0 : 1;
   float lw[4];
@@ -684,18 +718,8 @@ __device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, f
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int b = i & 1, cc = i >> 1;
-    const int off = poff(4 * i);
     float x[4];
-    if constexpr (ROWS) {
-      const float4 v = *reinterpret_cast<const float4*>(nbv + off);
-      x[0] = v.x;
-      x[1] = v.y;
-      x[2] = v.z;
-      x[3] = v.w;
-    } else {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) x[a] = nbv[(off + a) * kPad];
-    }
+    load4<ROWS>(x, nbv, o, i);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       if (ADJ) x[a] *= wprod_p(T.winv, 4 * i + a, h);
@@ -707,27 +731,6 @@ __device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, f
   if constexpr (J == 1) {
 #pragma unroll
     for (int l = 0; l < 16; ++l) tr[l] += __shfl_xor_sync(kFull, tr[l], 8);
-  }
-}
-
-// r += c (G u + L_nb t) on the thread's 8 local lines along J = 0 or 2, for
-// the upwind side SIDE (compile time: the 1D matrices are then constant-bank
-// operands and take no registers).  The side is uniform over a block (one
-// upwind side per cell and direction), so the branch in lines_p does not
-// diverge.
-template <int J, int SIDE>
-__device__ __forceinline__ void lines_local(float (&r)[32], const float (&u)[32],
-                                            const float (&tr)[16], float c, float tscale) {
-#pragma unroll
-  for (int l = 0; l < 8; ++l) {
-    const float t = tscale * tr[l];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float acc = c_Ln[SIDE][q] * t;
-#pragma unroll
-      for (int pp = 0; pp < 4; ++pp) acc = fmaf(c_G[SIDE][q * 4 + pp], u[pk<J>(l, pp)], acc);
-      r[pk<J>(l, q)] = fmaf(c, acc, r[pk<J>(l, q)]);
-    }
   }
 }
 
@@ -772,10 +775,24 @@ __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], co
   if constexpr (J == 1) {
     lines_split(r, u, tr, c, tscale, h);
   } else {
-    if (c > 0.f)
-      lines_local<J, 0>(r, u, tr, c, tscale);
-    else
-      lines_local<J, 1>(r, u, tr, c, tscale);
+    // the 8 local lines along J = 0 or 2
+    const int side = c > 0.f ? 0 : 1;
+    float Ln[4], G[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) G[i] = c * c_G[side][i];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const float t = tscale * tr[l];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float acc = fmaf(Ln[q], t, r[pk<J>(l, q)]);
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) acc = fmaf(G[q * 4 + pp], u[pk<J>(l, pp)], acc);
+        r[pk<J>(l, q)] = acc;
+      }
+    }
   }
 }
 
@@ -796,11 +813,71 @@ __device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32
 
 template <int J, bool ROWS, bool ADJ>
 __device__ __forceinline__ void direction_p(float (&r)[32], const float (&u)[32], const float* nbv,
-                                            float c, float wthread, int h, const Tab1D<float>& T) {
+                                            const int (&o)[4], float c, float wthread, int h,
+                                            const Tab1D<float>& T) {
   float tr[16];
-  nb_traces_p<J, ROWS, ADJ>(tr, nbv, c, h, T);
+  nb_traces_p<J, ROWS, ADJ>(tr, nbv, o, c, h, T);
   lines_p<J>(r, u, tr, c, ADJ ? wthread : 1.f, h);
 }
+
+// Tensor copy of one cell into a swizzled buffer: two boxes of 32 x 1 x 64
+// (the column halves of its 64 rows) of the 3D view (32, 2, rows) of the
+// stage vector, counted on the buffer's mbarrier.
+__device__ __forceinline__ void tma_cell(float* dst, const CUtensorMap* tm, unsigned cell,
+                                         unsigned long long* bar, unsigned long long pol) {
+#pragma unroll
+  for (int h2 = 0; h2 < 2; ++h2)
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst + 2048 * h2)),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(0), "r"(h2), "r"(static_cast<int>(cell * 64u)),
+        "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// Moves cells into the swizzled buffers.  FP32 input: one thread issues the
+// tensor copy.  FP64 input: each row's thread loads, converts and stores it.
+template <typename TIN>
+struct Mover2 {
+  float* sm;
+  Pipe* pp;
+  const CUtensorMap* tm;
+  unsigned phase = 0;
+  unsigned long long pol = l2_evict_last();
+
+  __device__ __forceinline__ void issue(int b, unsigned cell, const TIN* src, int T_, int t, int h) {
+    float* d = sm + b * kCellF;
+    if constexpr (sizeof(TIN) == 4) {
+      if (T_ == 0) {
+        mbar_expect_tx(&pp->bar[b], 4096 * 4);
+        tma_cell(d, tm, cell, &pp->bar[b], pol);
+      }
+    } else {
+      if (h == 0) {
+        const TIN* g = src + static_cast<size_t>(cell) * 4096 + t * 64;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          *reinterpret_cast<float4*>(d + (j >> 3) * 2048 + 32 * t + 4 * ((j & 7) ^ (t & 7))) =
+              ld4(g + 4 * j);
+      }
+    }
+  }
+  __device__ __forceinline__ bool wait(int b, int* err) {
+    if constexpr (sizeof(TIN) == 4) {
+      const unsigned par = (phase >> b) & 1u;
+      phase ^= 1u << b;
+      if (mbar_try_wait(&pp->bar[b], par)) return true;
+      const long long t0 = clock64();
+      while (clock64() - t0 < kWaitCycles)
+        if (mbar_try_wait(&pp->bar[b], par)) return true;
+      atomicOr(err, 2);
+      return false;
+    } else {
+      __syncthreads();
+      return true;
+    }
+  }
+};
 
 // Block-uniform description of a work item (a v3 pencil), kept in shared
 // memory so that per-cell neighbour indices need no integer division.
@@ -849,8 +926,11 @@ __device__ __forceinline__ unsigned nb_c(const KParams& p, unsigned cell, unsign
 
 // MODE 0: operator application (dst = K); MODE 1: fused LSRK stage.
 template <typename TIN, typename TW, bool ADJ, int MODE>
-__global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
-  extern __shared__ __align__(128) float sm6[];
+__global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
+                                                      const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) float sm_raw[];
+  // swizzled buffers need 1024-byte alignment (one KB of slack is allocated)
+  float* const sm6 = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u) / 4;
   __shared__ Pipe pipe;
   __shared__ unsigned s_item;
   __shared__ PencilInfo s_pi[2];      // current and next item
@@ -868,7 +948,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
   const float winv_t = ADJ ? wprod(T.winv, t) : 1.f;
   const float w_t = ADJ ? wprod(T.w, t) : 1.f;
   // the thread's outflow traces along v3, carried to the next cell of the pencil
-  float* carried = sm6 + 3 * kCellSmem + T_ * 8;
+  float* carried = sm6 + 3 * kCellF + T_ * 8;
   int bad = 0;
 
   if (T_ == 0) {
@@ -881,12 +961,9 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
   __syncthreads();
   unsigned item = s_item;
   if (item >= npencils) return;
-  Mover<TIN> mv{sm6, &pipe};
+  Mover2<TIN> mv{sm6, &pipe, &tmap};
   int slot = 0;
-  auto cellp = [&](unsigned c) { return src + static_cast<size_t>(c) * 4096; };
-  auto issue = [&](int b, unsigned c) {
-    if (issuer) mv.issue(b, cellp(c), t);
-  };
+  auto issue = [&](int b, unsigned c) { mv.issue(b, c, src, T_, t, h); };
   auto v3c = [&](const PencilInfo& pi, int i) {
     return pi.fwd ? static_cast<unsigned>(i) : static_cast<unsigned>(N3 - 1 - i);
   };
@@ -966,37 +1043,42 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
     for (int e = 0; e < 32; ++e) r[e] = 0.f;
 
     // ---- phase X: rows, directions x1, x2 (split), x3
+    int o[4];
+    offsets_x(o, t, h);
     ok &= mv.wait(A, p.err);
-    load_half<true>(u, pview<true>(sm6 + A * kCellSmem, t, h));
+    load_half<true>(u, sm6 + A * kCellF, o);
     if (ADJ) {
 #pragma unroll
       for (int k = 0; k < 32; ++k) u[k] *= winv_t * wprod_p(T.winv, k, h);
     }
     ok &= mv.wait(P, p.err);
-    direction_p<0, true, ADJ>(r, u, pview<true>(sm6 + P * kCellSmem, t, h), sp[0], winv_t, h, T);
+    direction_p<0, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[0], winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     issue(P, nbr[2]);                            // x3
     ok &= mv.wait(Q, p.err);
-    direction_p<1, true, ADJ>(r, u, pview<true>(sm6 + Q * kCellSmem, t, h), sp[1], winv_t, h, T);
+    direction_p<1, true, ADJ>(r, u, sm6 + Q * kCellF, o, sp[1], winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     issue(Q, nbr[3]);                            // v1
     ok &= mv.wait(P, p.err);
-    direction_p<2, true, ADJ>(r, u, pview<true>(sm6 + P * kCellSmem, t, h), sp[2], winv_t, h, T);
+    direction_p<2, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[2], winv_t, h, T);
     __syncthreads();                             // P is free: it takes the phase X result
     {
-      float* rb = sm6 + P * kCellSmem + t * kPad + 4 * h;
+      float* rb = sm6 + P * kCellF;
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        *reinterpret_cast<float4*>(rb + poff(4 * k)) =
-            make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+      for (int i = 0; i < 8; ++i) {
+        const int b = i & 1, cc = i >> 1;
+        *reinterpret_cast<float4*>(rb + o[b + 2 * (cc & 1)] + (cc >> 1) * 2048) =
+            make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+      }
     }
     __syncthreads();
 
     // ---- phase V: columns, directions v1, v2 (split), v3
-    load_half<false>(u, pview<false>(sm6 + A * kCellSmem, t, h));
-    load_half<false>(r, pview<false>(sm6 + P * kCellSmem, t, h));
+    offsets_v(o, t, h);
+    load_half<false>(u, sm6 + A * kCellF, o);
+    load_half<false>(r, sm6 + P * kCellF, o);
     if (ADJ) {
 #pragma unroll
       for (int k = 0; k < 32; ++k) u[k] *= winv_t * wprod_p(T.winv, k, h);
@@ -1006,7 +1088,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
     if (has_next) issue(A, next);                // the next cell
     issue(P, nbr[4]);                            // v2
     ok &= mv.wait(Q, p.err);
-    direction_p<0, false, ADJ>(r, u, pview<false>(sm6 + Q * kCellSmem, t, h), sp[3], winv_t, h, T);
+    direction_p<0, false, ADJ>(r, u, sm6 + Q * kCellF, o, sp[3], winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     if (need_v3)
@@ -1014,14 +1096,14 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
     else if (has_next)
       issue(Q, nx0);                             // x1 of the next cell
     ok &= mv.wait(P, p.err);
-    direction_p<1, false, ADJ>(r, u, pview<false>(sm6 + P * kCellSmem, t, h), sp[4], winv_t, h, T);
+    direction_p<1, false, ADJ>(r, u, sm6 + P * kCellF, o, sp[4], winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     if (has_next) issue(P, need_v3 ? nx0 : nx1);        // x1 or x2 of the next cell
     float tr[16];
     if (need_v3) {
       ok &= mv.wait(Q, p.err);
-      nb_traces_p<2, false, ADJ>(tr, pview<false>(sm6 + Q * kCellSmem, t, h), sp[5], h, T);
+      nb_traces_p<2, false, ADJ>(tr, sm6 + Q * kCellF, o, sp[5], h, T);
 #pragma unroll
       for (int k = 0; k < 8; ++k) tr[k] *= ADJ ? winv_t : 1.f;
     } else {
@@ -1060,6 +1142,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
       TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
       const float af = static_cast<float>(p.a_dt);
+      float nanacc = 0.f;
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) {
         double ub[8];
@@ -1072,9 +1155,9 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
           const int k = 8 * ch + kk;
           float K = r[k];
           if (ADJ) K *= w_t * wprod_p(T.w, k, h);
-          bad |= !isfinite(K);
+          nanacc = fmaf(K, 0.f, nanacc);   // stays 0 unless K is Inf or NaN
           const size_t g = g0 + 64 * poff(k);
-          const double un = ua[kk] + f32_to_f64(bf * K);
+          const double un = ua[kk] + f32_to_f64_finite(bf * K);
           __stcs(uu + g, un);
           if constexpr (sizeof(TW) == 4) {
             __stcs(dst + g, p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(ua[kk])));
@@ -1087,6 +1170,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
           for (int k = 0; k < 8; ++k) ua[k] = ub[k];
         }
       }
+      bad |= nanacc != 0.f;
     }
     fence_async_smem();
     __syncthreads();                             // Q is free; s_item was read by all threads
@@ -1120,13 +1204,51 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p) {
   if (bad) atomicOr(p.err, 1);
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// 3D view (32 floats, 2 halves, 64 rows per cell) of an FP32 stage vector,
+// box 32 x 1 x 64, 128-byte swizzle.
+cudaError_t encode_cell_map(CUtensorMap* tm, const void* src, long long ncells) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {32, 2, static_cast<cuuint64_t>(ncells) * 64};
+  const cuuint64_t strides[2] = {128, 256};
+  const cuuint32_t box[3] = {32, 1, 64};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(src), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename TIN, typename TW, bool ADJ>
 cudaError_t launch6p(KParams& p, cudaStream_t s) {
   auto kern = p.mode == 0 ? k_cell6d4p<TIN, TW, ADJ, 0> : k_cell6d4p<TIN, TW, ADJ, 1>;
-  // three cell buffers and the carried v3 traces (8 floats per thread)
-  const size_t smem = (static_cast<size_t>(kNumBuf) * kCellSmem + 128 * 8) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  // cell coordinates of the tensor copies are 32-bit signed rows
+  if (p.ncells * 64 >= (1LL << 31)) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  cudaError_t e;
+  if constexpr (sizeof(TIN) == 4) {
+    if ((e = encode_cell_map(&tm, p.src, p.ncells)) != cudaSuccess) return e;
+  }
+  // 1 KB alignment slack, three cell buffers, the carried v3 traces (8 floats per thread)
+  const size_t smem = 1024 + (static_cast<size_t>(kNumBuf) * kCellF + 128 * 8) * sizeof(float);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -1138,7 +1260,7 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
   const long long grid = std::min<long long>(npencils, static_cast<long long>(sms) * per_sm);
   e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  kern<<<static_cast<unsigned>(grid), 128, smem, s>>>(p);
+  kern<<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
   return cudaGetLastError();
 }
 

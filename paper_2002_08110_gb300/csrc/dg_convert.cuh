@@ -48,6 +48,18 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __hiloint2double(static_cast<int>(hi | sign), static_cast<int>(lo));
 }
 
+// binary32 -> binary64 for finite inputs (exact for normal numbers; zero and
+// subnormals give zero).  Infinity and NaN are not preserved -- callers that
+// use it detect non-finite inputs themselves.
+__device__ __forceinline__ double f32_to_f64_finite(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned mag = b & 0x7fffffffu;
+  const bool tiny = mag < 0x00800000u;
+  const unsigned hi = tiny ? 0u : ((mag >> 3) + 0x38000000u) | (b & 0x80000000u);
+  const unsigned lo = tiny ? 0u : b << 29;
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
 template <typename TO, typename TI>
 __device__ __forceinline__ TO cvt(TI x) {
   if constexpr (sizeof(TO) == sizeof(TI)) {
