@@ -19,9 +19,11 @@ What is computed (arXiv 2002.08110):
   integrals with the neighbour's trace, apply M^{-1}, scatter.
 * Tensor-product quadrature (Sec. 2.5) with n_q = k + 1 Gauss-Legendre points.
 
-Two bases are available (see ``quadrature.Tables1D``): nodal at the
-Gauss-Legendre points ("gl", collocation, diagonal M) and nodal at the
-Gauss-Lobatto points with Gauss quadrature ("gll", the paper's default).
+Three bases are available (see ``quadrature.Tables1D``): nodal at the
+Gauss-Legendre points ("gl", collocation, diagonal M), nodal at the
+Gauss-Lobatto points with Gauss quadrature ("gll", the paper's default) and
+nodal at the Gauss-Lobatto points with Gauss-Lobatto quadrature ("gllc", the
+collocation variant).
 
 Readings taken where the paper is silent:
 * the reference cell is [-1, 1]^d;
@@ -287,7 +289,7 @@ class Problem:
 
     def apply_abs(self, u, cells=None):
         """Term scale |M^{-1}| |A| |u| (collocation basis: M^{-1} diagonal)."""
-        assert self.basis == "gl"
+        assert self.basis in ("gl", "gllc")   # collocation: diagonal mass
         u = np.asarray(u, dtype=np.float64)
         sel = range(self.ncells) if cells is None else cells
         out = [self.apply_mass_inverse(self._cell_residual_abs(u, e)).reshape(-1, order="F")
@@ -406,7 +408,7 @@ class Problem:
 
     def mass_diagonal(self):
         """Diagonal of M for the collocation basis (|J| times the weights)."""
-        assert self.basis == "gl"
+        assert self.basis in ("gl", "gllc")   # collocation: diagonal mass
         W = _outer_weights([self.T.w] * self.d).reshape(-1, order="F")
         return np.tile(W * self.detJ, self.ncells)
 
@@ -417,7 +419,7 @@ class Problem:
         product of the 1D weights), collocation basis.  Returns an array of
         shape (x cells, x nodes) with x cells and nodes lexicographic (only
         the rows of ``x_cells`` if given)."""
-        assert self.basis == "gl"
+        assert self.basis in ("gl", "gllc")   # collocation: diagonal mass
         dx, dv, n = self.dx, self.dv, self.n
         ncx = int(np.prod(self.cells[:dx]))
         ncv = int(np.prod(self.cells[dx:]))

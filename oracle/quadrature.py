@@ -75,6 +75,10 @@ class Tables1D:
     basis="gll": nodal basis at the Gauss-Lobatto points with n_q = k+1
                  Gauss-Legendre quadrature (the paper's default configuration,
                  Sec. 5.1), i.e. a non-trivial basis change.
+    basis="gllc": nodal basis at the n = k+1 Gauss-Lobatto points with the same
+                 points as quadrature (the collocation variant the paper
+                 mentions as an alternative, Sec. 5.1; exact to degree 2k-1,
+                 mass matrix diagonal).
 
     B[q, p]  = phi_p(zeta_q)      basis at quadrature points
     Bd[q, p] = phi_p'(zeta_q)     derivative at quadrature points
@@ -87,12 +91,15 @@ class Tables1D:
             raise ValueError("degree k >= 0 required")
         n = k + 1
         self.k, self.n, self.basis = k, n, basis
-        self.zeta, self.w = gauss_legendre(n)
-        if basis == "gl":
+        if basis in ("gll", "gllc") and n < 2:
+            raise ValueError("GLL basis needs k >= 1")
+        if basis == "gllc":
+            self.zeta, self.w = gauss_lobatto(n)
+        else:
+            self.zeta, self.w = gauss_legendre(n)
+        if basis in ("gl", "gllc"):
             self.nodes = self.zeta.copy()
         elif basis == "gll":
-            if n < 2:
-                raise ValueError("GLL basis needs k >= 1")
             self.nodes, _ = gauss_lobatto(n)
         else:
             raise ValueError(basis)

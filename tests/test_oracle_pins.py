@@ -166,17 +166,19 @@ def _small_workloads():
     ]
 
 
+@pytest.mark.parametrize("basis", ["gl", "gllc"])
 @pytest.mark.parametrize("w", _small_workloads(), ids=lambda w: w.name)
-def test_annihilates_constants(w):
-    p = _problem(w)
+def test_annihilates_constants(w, basis):
+    p = _problem(w, basis=basis)
     r = p.apply(np.ones(p.n_dofs))
     scale = np.max(np.abs(p.apply(np.random.default_rng(0).standard_normal(p.n_dofs))))
     assert np.max(np.abs(r)) <= 1e-13 * scale
 
 
+@pytest.mark.parametrize("basis", ["gl", "gllc"])
 @pytest.mark.parametrize("w", _small_workloads(), ids=lambda w: w.name)
-def test_conserves_mass(w):
-    p = _problem(w)
+def test_conserves_mass(w, basis):
+    p = _problem(w, basis=basis)
     u = np.random.default_rng(1).standard_normal(p.n_dofs)
     Mdiag = p.mass_diagonal()
     Lu = p.apply(u)
@@ -190,14 +192,17 @@ def _independent_traces(vals, nodes):
     return P.polyval(-1.0, c), P.polyval(1.0, c)
 
 
+@pytest.mark.parametrize("basis", ["gl", "gllc"])
 @pytest.mark.parametrize("w", _small_workloads()[:3], ids=lambda w: w.name)
-def test_energy_identity(w):
+def test_energy_identity(w, basis):
     """u^T M L u = -1/2 sum over faces of |J| W_perp |c_n| [u]^2 (upwind flux,
-    divergence-free speed that does not vary along its own direction)."""
-    p = _problem(w)
+    divergence-free speed that does not vary along its own direction).  For
+    the Gauss-Lobatto collocation it holds because that rule integrates
+    u du/dx (degree 2k-1) exactly: the summation-by-parts property."""
+    p = _problem(w, basis=basis)
     u = np.random.default_rng(2).standard_normal(p.n_dofs)
     lhs = u @ (p.mass_diagonal() * p.apply(u))
-    zeta, wq = npleg.leggauss(p.n)
+    zeta, wq = npleg.leggauss(p.n) if basis == "gl" else gauss_lobatto(p.n)
     d, n = p.d, p.n
     h = np.array(w.h)
     S = np.eye(w.dx) if w.shear is None else np.array(w.shear).reshape(w.dx, w.dx)
@@ -545,3 +550,58 @@ def test_vp_field_uses_minus_e_and_conserves_mass():
     m0 = p.integrals(u)[0]
     u1 = vp_step(p, u, 0.02)
     assert abs(p.integrals(u1)[0] - m0) <= 1e-13 * abs(m0)
+
+
+# ---------------------------------------------------------------------------
+# Gauss-Lobatto collocation (the paper's alternative basis, Sec. 5.1)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("a", [2.0, -1.5])
+def test_gllc_k1_operator_by_hand(a):
+    """k = 1, nodes -1, +1, weights 1, 1, speed c = 2a/h along x only.  Worked
+    by hand from the weak form: with the upwind neighbour's facing node value
+    u_nb, c > 0: K = c (u_nb - (u0+u1)/2, (u0-u1)/2);
+    c < 0: K = c ((u0-u1)/2, (u0+u1)/2 - u_nb)."""
+    h = 1.0
+    p = Problem(1, 1, 1, [3], [1], [0.0], [3.0], [-1.0], [1.0], ConstantField([a, 0.0]),
+                basis="gllc")
+    u = np.random.default_rng(5).standard_normal(p.n_dofs)
+    K = p.apply(u).reshape(3, 2, 2)        # cell, v node, x node
+    U = u.reshape(3, 2, 2)
+    c = 2 * a / h
+    for e in range(3):
+        for qv in range(2):
+            u0, u1 = U[e, qv]
+            if c > 0:
+                unb = U[(e - 1) % 3, qv, 1]
+                ref = (c * (unb - (u0 + u1) / 2), c * (u0 - u1) / 2)
+            else:
+                unb = U[(e + 1) % 3, qv, 0]
+                ref = (c * (u0 - u1) / 2, c * ((u0 + u1) / 2 - unb))
+            np.testing.assert_allclose(K[e, qv], ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_gllc_convergence_order(k):
+    """Gauss-Lobatto collocation transports a product of sines at order k+1."""
+    from oracle.quadrature import gauss_lobatto as gl_nodes
+    errs = []
+    for N in (4, 8, 16):
+        w = W.config_2d(cells=N)
+        w = W.Workload(**{**w.__dict__, "k": k, "final_time": 0.25})
+        p = _problem(w, basis="gllc")
+        zeta = gl_nodes(w.n)[0]
+        u0 = W.separable_state(w, zeta)
+        dt, steps = W.time_step(w)
+        dt, steps = dt / 4, steps * 4
+        L = p.assemble()
+        u = u0.copy()
+        for _ in range(steps):
+            u = lsrk.step(lambda x: L @ x, u, dt)
+        T = dt * steps
+        shifted = W.Workload(**{**w.__dict__, "u0_factors": (
+            lambda y: np.sin(2 * np.pi * (y - w.a_const[0] * T)),
+            lambda y: np.sin(2 * np.pi * (y - w.a_const[1] * T)))})
+        diff = u - W.separable_state(shifted, zeta)
+        errs.append(math.sqrt(diff @ (p.mass_diagonal() * diff)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > k + 1 - 0.3, rates
