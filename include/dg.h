@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define DG_ABI_VERSION 1
+#define DG_ABI_VERSION 2
 
 typedef struct dg_ctx* dg_handle;
 typedef struct dg_batch_ctx* dg_batch;
@@ -80,6 +80,24 @@ typedef enum {
     DG_FIELD_PHASE_SPACE = 1
 } dg_field_kind;
 
+/* Nodal bases of the element (Sec. 2.3, 2.5, 5.1). */
+typedef enum {
+    /* Nodes and quadrature at the k+1 Gauss-Legendre points (collocation,
+     * diagonal mass matrix).  The default (a zero-initialised geometry). */
+    DG_BASIS_GL = 0,
+    /* Nodes and quadrature at the k+1 Gauss-Lobatto points (the collocation
+     * variant the paper mentions; diagonal mass, quadrature exact to degree
+     * 2k-1). */
+    DG_BASIS_GLL = 1,
+    /* Nodes at the Gauss-Lobatto points, quadrature at the Gauss-Legendre
+     * points (the paper's default element).  Its operator equals
+     * V^{-1} L_GL V with V_qi = phi_i(Gauss point q) in every direction, which
+     * is how the library evaluates it: vectors are changed to values at the
+     * Gauss points, the Gauss-Legendre operator runs, and the result is
+     * changed back (around each dg_apply, dg_rk_stage and dg_rk_step call). */
+    DG_BASIS_GLL_GAUSS = 2
+} dg_basis;
+
 /*
  * Geometry and velocity field (Sec. 3: tensor product of two meshes; the
  * mapping is block diagonal).  Configuration space is the lattice box
@@ -89,10 +107,14 @@ typedef enum {
  * cells per direction.  All boundaries are periodic.
  *
  * e_nodes (DG_FIELD_PHASE_SPACE only; NULL means E = 0): host array of
- *   n_xcells * (k+1)^dim_x * dim_v doubles, E_i at the x node (cell c_x,
- *   node q_x), index (c_x * (k+1)^dim_x + q_x) * dim_v + i, with c_x and q_x
- *   lexicographic, x_1 fastest; node coordinates as given by
- *   dg_node_coordinates().  The library copies it; the caller keeps ownership.
+ *   n_xcells * (k+1)^dim_x * dim_v doubles, E_i at the x quadrature point
+ *   (cell c_x, point q_x), index (c_x * (k+1)^dim_x + q_x) * dim_v + i, with
+ *   c_x and q_x lexicographic, x_1 fastest; point coordinates as given by
+ *   dg_node_coordinates(space 2).  For the collocated bases the quadrature
+ *   points are the nodes.  The library copies it; the caller keeps ownership.
+ *
+ * basis: a dg_basis value (0, the Gauss-Legendre collocation, if the struct
+ *   is zero-initialised).
  */
 typedef struct {
     double x_lo[3], x_hi[3];
@@ -101,6 +123,7 @@ typedef struct {
     int field_kind;
     double a_const[6];
     const double* e_nodes;
+    int basis;
 } dg_geometry;
 
 typedef struct {
@@ -116,6 +139,7 @@ typedef struct {
                                  a cell (each cell has one upwind neighbour
                                  per direction); the specialised 6D kernel
                                  runs only then                             */
+    int basis;                /* dg_basis of the handle                     */
 } dg_info_t;
 
 /* Launch configuration of the cell kernels (chosen by dg_autotune). */
@@ -143,6 +167,15 @@ const char* dg_last_error(void);
 dg_status dg_reference_nodes(int degree, double* nodes, double* weights);
 
 /*
+ * The 1D points of a dg_basis of degree ``degree`` on [-1, 1], ascending,
+ * into host arrays of degree+1 doubles (each may be NULL): the DoF nodes, and
+ * the quadrature points and weights of the cell integrals (where fields are
+ * sampled).  DG_BASIS_GLL and DG_BASIS_GLL_GAUSS need degree >= 1.
+ * INVALID_ARG for an unknown basis or degree outside [0, 5].
+ */
+dg_status dg_basis_nodes(int basis, int degree, double* nodes, double* qpoints, double* qweights);
+
+/*
  * Create a handle for the mesh T_x (x) T_v (Sec. 3, Eq. concept:tria:tensor)
  * of degree ``degree`` on the current CUDA device.  cells_x[dim_x] and
  * cells_v[dim_v] give cells per direction (>= 1).  Computes the 1D tables in
@@ -166,6 +199,8 @@ dg_status dg_info(dg_handle h, dg_info_t* info);
  * rows of dim_x lattice coordinates y (physical x = S y); space 1: v nodes,
  * n_vcells*(k+1)^dim_v rows of dim_v velocity coordinates.  Row order is
  * (cell, node), both lexicographic with the first direction fastest.
+ * space 2 and 3: the same for the x and v quadrature points (equal to the
+ * nodes except for DG_BASIS_GLL_GAUSS).
  */
 dg_status dg_node_coordinates(dg_handle h, int space, double* out);
 

@@ -8,10 +8,11 @@ time stepping.  The work runs in the CUDA library ``libdg.so`` behind the C
 ABI of ``include/dg.h``; this package is its thin Python binding plus the
 autograd wrapper of the adjoint.
 """
-from ._lib import PREC_FP32, PREC_FP64, PREC_MIXED, DGError  # noqa: F401
+from ._lib import (BASIS_GL, BASIS_GLL, BASIS_GLL_GAUSS, PREC_FP32, PREC_FP64,  # noqa: F401
+                   PREC_MIXED, DGError)
 
-__all__ = ["DG", "DGBatch", "DGError", "PREC_FP64", "PREC_FP32", "PREC_MIXED", "reference_nodes",
-           "build_library"]
+__all__ = ["DG", "DGBatch", "DGError", "PREC_FP64", "PREC_FP32", "PREC_MIXED", "BASIS_GL",
+           "BASIS_GLL", "BASIS_GLL_GAUSS", "reference_nodes", "basis_nodes", "build_library"]
 
 
 def build_library(verbose=False):
@@ -21,7 +22,7 @@ def build_library(verbose=False):
 
 def __getattr__(name):
     # torch-dependent parts are imported lazily
-    if name in ("DG", "DGBatch", "reference_nodes", "from_spec"):
+    if name in ("DG", "DGBatch", "reference_nodes", "basis_nodes", "from_spec"):
         from . import api
         return getattr(api, name)
     if name in ("RKForward", "final_state", "misfit_gradient", "CheckpointMismatch"):

@@ -16,6 +16,7 @@ DG_OK = 0
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID_ARG", 2: "DG_ERR_UNSUPPORTED", 3: "DG_ERR_CUDA",
                 4: "DG_ERR_OOM", 5: "DG_ERR_NONFINITE", 6: "DG_ERR_TIMEOUT"}
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
+BASIS_GL, BASIS_GLL, BASIS_GLL_GAUSS = 0, 1, 2
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
 
@@ -24,7 +25,8 @@ class Geometry(ctypes.Structure):
     _fields_ = [("x_lo", ctypes.c_double * 3), ("x_hi", ctypes.c_double * 3),
                 ("v_lo", ctypes.c_double * 3), ("v_hi", ctypes.c_double * 3),
                 ("shear_x", ctypes.c_double * 9), ("field_kind", ctypes.c_int),
-                ("a_const", ctypes.c_double * 6), ("e_nodes", c_double_p)]
+                ("a_const", ctypes.c_double * 6), ("e_nodes", c_double_p),
+                ("basis", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -33,7 +35,7 @@ class Info(ctypes.Structure):
                 ("dofs_per_cell", ctypes.c_int), ("dim_x", ctypes.c_int), ("dim_v", ctypes.c_int),
                 ("degree", ctypes.c_int), ("speed_sum", ctypes.c_double),
                 ("det_jacobian", ctypes.c_double), ("h", ctypes.c_double * 6),
-                ("uniform_sides", ctypes.c_int)]
+                ("uniform_sides", ctypes.c_int), ("basis", ctypes.c_int)]
 
 
 class Launch(ctypes.Structure):
@@ -78,6 +80,7 @@ def load():
         "dg_integrals": (i, [vp, vp, c_double_p, vp]),
         "dg_integrals_noalloc": (i, [vp, ll, i, i, d, c_double_p, vp]),
         "dg_check": (i, [vp, vp]),
+        "dg_basis_nodes": (i, [i, i, vp, vp, vp]),
         "dg_charge_density": (i, [vp, vp, i, vp, vp]),
         "dg_poisson_periodic_1d": (i, [vp, vp, vp, vp]),
         "dg_set_field_device": (i, [vp, vp, i, ctypes.c_double, vp]),

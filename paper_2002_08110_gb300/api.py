@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PREC_FP32, PREC_FP64, PREC_MIXED, DGError, check
+from ._lib import BASIS_GL, PREC_FP32, PREC_FP64, PREC_MIXED, DGError, check
 
 _WDTYPE = {PREC_FP64: torch.float64, PREC_FP32: torch.float32, PREC_MIXED: torch.float64}
 
@@ -21,6 +21,15 @@ def _stream():
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def basis_nodes(basis, degree):
+    """(DoF nodes, quadrature points, quadrature weights) of a basis (numpy)."""
+    lib = _lib.load()
+    arrs = [np.zeros(degree + 1) for _ in range(3)]
+    check(lib.dg_basis_nodes(int(basis), int(degree),
+                             *[a.ctypes.data_as(_lib.c_double_p) for a in arrs]))
+    return tuple(arrs)
 
 
 def reference_nodes(degree):
@@ -43,7 +52,7 @@ class DG:
     """
 
     def __init__(self, dim_x, dim_v, degree, cells_x, cells_v, x_lo, x_hi, v_lo, v_hi,
-                 field_kind=0, a_const=None, e_nodes=None, shear=None):
+                 field_kind=0, a_const=None, e_nodes=None, shear=None, basis=BASIS_GL):
         self.lib = _lib.load()
         self.dim_x, self.dim_v, self.degree = int(dim_x), int(dim_v), int(degree)
         g = _lib.Geometry()
@@ -57,6 +66,8 @@ class DG:
                 for m in range(self.dim_x):
                     g.shear_x[i * self.dim_x + m] = S[i, m]
         g.field_kind = int(field_kind)
+        g.basis = int(basis)
+        self.basis = int(basis)
         if a_const is not None:
             for j, a in enumerate(a_const):
                 g.a_const[j] = float(a)
@@ -91,8 +102,9 @@ class DG:
 
     # -- helpers -----------------------------------------------------------------
     def node_coordinates(self, space):
-        """x nodes (space 0, lattice coordinates) or v nodes (space 1)."""
-        if space == 0:
+        """x nodes (space 0, lattice coordinates), v nodes (space 1), or the x / v
+        quadrature points (spaces 2, 3; the nodes except for the GLL-Gauss basis)."""
+        if space % 2 == 0:
             rows, cols = int(self.info.n_xcells) * (self.degree + 1) ** self.dim_x, self.dim_x
         else:
             rows, cols = int(self.info.n_vcells) * (self.degree + 1) ** self.dim_v, self.dim_v

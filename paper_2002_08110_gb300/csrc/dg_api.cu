@@ -120,6 +120,7 @@ KParams base_params(const dg_ctx* h, int prec) {
   p.work = h->work_d;
   p.t64 = h->tables.t64;
   p.t32 = h->tables.t32;
+  p.tab = h->basis == DG_BASIS_GLL ? 1 : 0;
   return p;
 }
 
@@ -158,6 +159,50 @@ cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg&
   }
 }
 
+// DG_BASIS_GLL_GAUSS: four FP64 temporaries of n_dofs values (two vectors
+// at the Gauss points, the state there, and one for multi-pass basis
+// changes of cells too large for shared memory), allocated on first use.
+dg_status ensure_bc_tmp(dg_ctx* h) {
+  for (int i = 0; i < 4; ++i) {
+    if (h->bc_tmp[i]) continue;
+    cudaError_t e = cudaMalloc(&h->bc_tmp[i], static_cast<size_t>(h->n_dofs) * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "basis-change temporaries");
+  }
+  return DG_OK;
+}
+
+// y = M x on every cell, M = V (which 0), V^{-1} (1), V^T (2) or V^{-T} (3)
+// in every direction; x and y FP32 when the flags say so.
+dg_status change_basis(dg_ctx* h, int which, const void* x, int xf, void* y, int yf,
+                       cudaStream_t s) {
+  BasisMat M;
+  std::memset(&M, 0, sizeof(M));
+  for (int q = 0; q < h->n; ++q)
+    for (int i = 0; i < h->n; ++i) {
+      const int r = which >= 2 ? i : q, c = which >= 2 ? q : i;   // transposes read (i, q)
+      M.m[q * kMaxN + i] = (which % 2 == 0) ? h->tables.V[r][c] : h->tables.Vinv[r][c];
+    }
+  cudaError_t e = launch_basis_change(x, xf, y, yf, h->bc_tmp[3], h->ncells, h->d, h->n, M, s);
+  if (e == cudaErrorNotSupported)
+    return fail(DG_ERR_UNSUPPORTED, "FP32 basis change of cells this large");
+  if (e != cudaSuccess) return cuda_fail(e, "basis change");
+  return DG_OK;
+}
+
+dg_status apply_core(dg_handle h, const void* src, void* dst, int prec, cudaStream_t s,
+                     int adjoint) {
+  dg_status st;
+  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  KParams p = base_params(h, prec);
+  p.src = src;
+  p.dst = dst;
+  p.mode = 0;
+  p.adjoint = adjoint;
+  cudaError_t e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s);
+  if (e != cudaSuccess) return cuda_fail(e, "cell kernel launch");
+  return DG_OK;
+}
+
 dg_status do_apply(dg_handle h, const void* src, void* dst, int prec, void* stream, int adjoint) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
   const int combo = combo_of(prec);
@@ -167,14 +212,15 @@ dg_status do_apply(dg_handle h, const void* src, void* dst, int prec, void* stre
   if ((st = check_vec(dst, "dst")) != DG_OK) return st;
   const size_t bytes = static_cast<size_t>(h->n_dofs) * elem_bytes(prec);
   if (ranges_overlap(src, dst, bytes)) return fail(DG_ERR_INVALID_ARG, "src and dst overlap");
-  if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
-  KParams p = base_params(h, prec);
-  p.src = src;
-  p.dst = dst;
-  p.mode = 0;
-  p.adjoint = adjoint;
-  cudaError_t e = launch_cell(h, combo, p, h->cfg[prec], static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "cell kernel launch");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->basis != DG_BASIS_GLL_GAUSS) return apply_core(h, src, dst, prec, s, adjoint);
+  // L = V^{-1} L_GL V;  L^T = V^T L_GL^T V^{-T}
+  if ((st = ensure_bc_tmp(h)) != DG_OK) return st;
+  const int f = prec == DG_PREC_FP32;
+  if ((st = change_basis(h, adjoint ? 3 : 0, src, f, h->bc_tmp[0], f, s)) != DG_OK ||
+      (st = apply_core(h, h->bc_tmp[0], h->bc_tmp[1], prec, s, adjoint)) != DG_OK ||
+      (st = change_basis(h, adjoint ? 2 : 1, h->bc_tmp[1], f, dst, f, s)) != DG_OK)
+    return st;
   return DG_OK;
 }
 
@@ -252,6 +298,7 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->vp_rho);
   cudaFree(h->vp_e);
   cudaFree(h->host_stage);
+  for (int i = 0; i < 4; ++i) cudaFree(h->bc_tmp[i]);
   delete h;
 }
 
@@ -385,6 +432,17 @@ dg_status dg_reference_nodes(int degree, double* nodes, double* weights) {
   return DG_OK;
 }
 
+dg_status dg_basis_nodes(int basis, int degree, double* nodes, double* qpoints, double* qweights) {
+  if (basis < DG_BASIS_GL || basis > DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_INVALID_ARG, "unknown basis %d", basis);
+  if (degree < 0 || degree > 5) return fail(DG_ERR_INVALID_ARG, "degree must be in [0, 5]");
+  if (basis != DG_BASIS_GL && degree < 1)
+    return fail(DG_ERR_INVALID_ARG, "Gauss-Lobatto bases need degree >= 1");
+  if (!basis_points(basis, degree + 1, nodes, qpoints, qweights))
+    return fail(DG_ERR_INVALID_ARG, "no points for this degree");
+  return DG_OK;
+}
+
 dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const int* cells_v,
                     const dg_geometry* geometry, dg_handle* out) {
   if (out == nullptr) return fail(DG_ERR_INVALID_ARG, "out is NULL");
@@ -398,6 +456,8 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
   const dg_geometry& g = *geometry;
   if (g.field_kind != DG_FIELD_CONSTANT && g.field_kind != DG_FIELD_PHASE_SPACE)
     return fail(DG_ERR_INVALID_ARG, "unknown field_kind %d", g.field_kind);
+  if (g.basis < DG_BASIS_GL || g.basis > DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_INVALID_ARG, "unknown basis %d", g.basis);
   if (g.field_kind == DG_FIELD_PHASE_SPACE && dim_v < dim_x)
     return fail(DG_ERR_UNSUPPORTED, "phase-space field needs dim_v >= dim_x");
 
@@ -409,6 +469,7 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
   h->k = degree;
   h->n = degree + 1;
   h->field_kind = g.field_kind;
+  h->basis = g.basis;
   long long ncx = 1, ncv = 1;
   for (int j = 0; j < h->d; ++j) {
     const int c = j < dim_x ? cells_x[j] : cells_v[j - dim_x];
@@ -490,7 +551,7 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
       return fail(DG_ERR_INVALID_ARG, "a_const is not finite");
     }
   }
-  build_tables(h->n, &h->tables);
+  build_tables(h->n, h->basis, &h->tables);
   dg_status s = compute_speeds(h, g.e_nodes);
   if (s != DG_OK) {
     delete h;
@@ -514,7 +575,8 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
     free_ctx(h);
     return cuda_fail(e, "dg_create");
   }
-  if (h->d == 6 && h->n == 4 && (e = init_cell6d_tables(h->tables.t32)) != cudaSuccess) {
+  if (h->d == 6 && h->n == 4 &&
+      (e = init_cell6d_tables(h->tables.t32, h->basis == DG_BASIS_GLL ? 1 : 0)) != cudaSuccess) {
     free_ctx(h);
     return cuda_fail(e, "dg_create");
   }
@@ -543,17 +605,20 @@ dg_status dg_info(dg_handle h, dg_info_t* info) {
   info->det_jacobian = h->detJ;
   for (int j = 0; j < h->d; ++j) info->h[j] = h->h[j];
   info->uniform_sides = h->uniform_sides ? 1 : 0;
+  info->basis = h->basis;
   return DG_OK;
 }
 
 dg_status dg_node_coordinates(dg_handle h, int space, double* out) {
   if (h == nullptr || out == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
-  if (space != 0 && space != 1) return fail(DG_ERR_INVALID_ARG, "space must be 0 (x) or 1 (v)");
-  const int dims = space == 0 ? h->dx : h->dv;
-  const int off = space == 0 ? 0 : h->dx;
-  const long long nc = space == 0 ? h->ncx : h->ncv;
-  const int nq = space == 0 ? h->nqx : h->nqv;
-  const double* z = h->tables.zeta;
+  if (space < 0 || space > 3)
+    return fail(DG_ERR_INVALID_ARG, "space must be 0 (x nodes), 1 (v nodes), 2 or 3 (points)");
+  const bool xs = space % 2 == 0;
+  const int dims = xs ? h->dx : h->dv;
+  const int off = xs ? 0 : h->dx;
+  const long long nc = xs ? h->ncx : h->ncv;
+  const int nq = xs ? h->nqx : h->nqv;
+  const double* z = space < 2 ? h->tables.dofz : h->tables.zeta;
   for (long long c = 0; c < nc; ++c)
     for (int q = 0; q < nq; ++q) {
       long long cc = c;
@@ -634,6 +699,8 @@ dg_status dg_set_field_device(dg_handle h, const double* e, int components, doub
 
 dg_status dg_poisson_periodic_1d(dg_handle h, const double* rho, double* e, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->basis == DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_UNSUPPORTED, "the Poisson solve needs a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
   if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "the Poisson solve needs dim_x = 1");
   if (rho == nullptr || e == nullptr || reinterpret_cast<uintptr_t>(rho) % 8 != 0 ||
       reinterpret_cast<uintptr_t>(e) % 8 != 0)
@@ -656,6 +723,8 @@ dg_status dg_poisson_periodic_1d(dg_handle h, const double* rho, double* e, void
 dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
                         void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->basis == DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps needs a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
   if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need dim_x = 1");
   if (h->field_kind != DG_FIELD_PHASE_SPACE)
     return fail(DG_ERR_INVALID_ARG, "Vlasov-Poisson steps need a phase-space handle");
@@ -721,13 +790,28 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
       ranges_overlap(w_out, wb, u, ub))
     return fail(DG_ERR_INVALID_ARG, "w_in, w_out and u must not overlap");
   if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
-  return enqueue_stage(h, w_in, w_out, u, stage, dt, prec, adjoint ? 1 : 0,
-                       static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->basis != DG_BASIS_GLL_GAUSS)
+    return enqueue_stage(h, w_in, w_out, u, stage, dt, prec, adjoint ? 1 : 0, s);
+  // the stage at the Gauss points: w_in and u changed there, w_out and u back
+  if ((st = ensure_bc_tmp(h)) != DG_OK) return st;
+  const int f = prec == DG_PREC_FP32;
+  const int to = adjoint ? 3 : 0, back = adjoint ? 2 : 1;
+  if ((st = change_basis(h, to, w_in, f, h->bc_tmp[0], f, s)) != DG_OK ||
+      (st = change_basis(h, to, u, 0, h->bc_tmp[2], 0, s)) != DG_OK ||
+      (st = enqueue_stage(h, h->bc_tmp[0], h->bc_tmp[1], h->bc_tmp[2], stage, dt, prec,
+                          adjoint ? 1 : 0, s)) != DG_OK ||
+      (st = change_basis(h, back, h->bc_tmp[1], f, w_out, f, s)) != DG_OK ||
+      (st = change_basis(h, back, h->bc_tmp[2], 0, u, 0, s)) != DG_OK)
+    return st;
+  return DG_OK;
 }
 
 dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
                            double dt, int prec, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->basis == DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_UNSUPPORTED, "the host-buffer stage needs a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
   if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
   if (stage < 0 || stage > 4) return fail(DG_ERR_INVALID_ARG, "stage must be in [0, 4]");
   if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
@@ -766,6 +850,9 @@ dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u
   return DG_OK;
 }
 
+dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
+                       int adjoint, cudaStream_t s);
+
 dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
                      int adjoint, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
@@ -785,6 +872,19 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
   adjoint = adjoint ? 1 : 0;
   if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->basis != DG_BASIS_GLL_GAUSS) return rk_step_core(h, u, w0, w1, dt, nsteps, prec, adjoint, s);
+  // R(dt L) = V^{-1} R(dt L_GL) V: the steps run on the state at the Gauss points
+  if ((st = ensure_bc_tmp(h)) != DG_OK) return st;
+  if ((st = change_basis(h, adjoint ? 3 : 0, u, 0, h->bc_tmp[2], 0, s)) != DG_OK ||
+      (st = rk_step_core(h, h->bc_tmp[2], w0, w1, dt, nsteps, prec, adjoint, s)) != DG_OK ||
+      (st = change_basis(h, adjoint ? 2 : 1, h->bc_tmp[2], 0, u, 0, s)) != DG_OK)
+    return st;
+  return DG_OK;
+}
+
+dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
+                       int adjoint, cudaStream_t s) {
+  dg_status st;
   cudaError_t e = launch_convert(u, w0, prec == DG_PREC_FP32, h->n_dofs, s);
   if (e != cudaSuccess) return cuda_fail(e, "stage-vector initialisation");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -837,6 +937,13 @@ dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream) 
   dg_status st;
   if ((st = check_vec(u, "u")) != DG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (h->basis == DG_BASIS_GLL_GAUSS) {
+    // the quadrature acts on the interpolant's values at the Gauss points
+    if ((st = ensure_bc_tmp(h)) != DG_OK ||
+        (st = change_basis(h, 0, u, 0, h->bc_tmp[2], 0, s)) != DG_OK)
+      return st;
+    u = h->bc_tmp[2];
+  }
   KParams p = base_params(h, DG_PREC_FP64);
   cudaError_t e = launch_integrals(p, h->n, u, h->partial, h->partial_blocks, h->detJ, s);
   if (e != cudaSuccess) return cuda_fail(e, "integrals kernel");
@@ -859,6 +966,8 @@ dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream) 
 
 dg_status dg_charge_density(dg_handle h, const void* f, int prec, double* rho, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->basis == DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_UNSUPPORTED, "the charge density needs a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
   if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
     return fail(DG_ERR_INVALID_ARG, "f must be FP64 (DG_PREC_FP64) or FP32 (DG_PREC_FP32)");
   dg_status st;

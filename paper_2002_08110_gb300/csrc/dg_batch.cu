@@ -340,10 +340,12 @@ dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out) {
       free_batch(b);
       return report(DG_ERR_INVALID_ARG, "NULL handle in batch");
     }
-    if (h->field_kind != DG_FIELD_CONSTANT || h->d < 3 || h->d > 4 || h->ncells > (1LL << 30)) {
+    if (h->field_kind != DG_FIELD_CONSTANT || h->d < 3 || h->d > 4 || h->ncells > (1LL << 30) ||
+        h->basis != DG_BASIS_GL) {
       free_batch(b);
       return report(DG_ERR_UNSUPPORTED,
-                    "batched members must be constant-velocity problems with d = 3 or 4");
+                    "batched members must be constant-velocity problems with d = 3 or 4 "
+                    "in the Gauss-Legendre basis");
     }
     BInst I{};
     I.d = h->d;
@@ -369,7 +371,7 @@ dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out) {
   std::memset(t32, 0, sizeof(t32));
   for (int n = 2; n <= kMaxN; ++n) {
     HostTables ht;
-    build_tables(n, &ht);
+    build_tables(n, DG_BASIS_GL, &ht);
     t64[n] = ht.t64;
     t32[n] = ht.t32;
   }

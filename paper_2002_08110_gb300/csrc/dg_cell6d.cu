@@ -176,18 +176,18 @@ __device__ __forceinline__ void load_block(float (&x)[64], const float* v) {
 // The collocated 1D tables of n = 4 for both upwind sides (index 0: c > 0,
 // index 1: c < 0), in constant memory so that a block-uniform side selects
 // them with one broadcast load: G = Gp / Gn, Ln = Lm / -Lp, lw = lp / lm.
-__constant__ float c_G[2][16];
-__constant__ float c_Ln[2][4];
-__constant__ float c_lw[2][4];
+__constant__ float c_G[4][16];
+__constant__ float c_Ln[4][4];
+__constant__ float c_lw[4][4];
 
 // Traces, on the shared face, of the upwind neighbour's 16 lines along local
 // direction J, read from a landing buffer (row or column view).  With the
 // adjoint the neighbour values are scaled by M^{-1}: the element factor here,
 // the thread factor by the caller (tscale of lines_dir).
 template <int J, bool ROWS, bool ADJ>
-__device__ __forceinline__ void nb_traces(float (&tr)[16], const float* nbv, float c,
+__device__ __forceinline__ void nb_traces(float (&tr)[16], const float* nbv, float c, int tb,
                                           const Tab1D<float>& T) {
-  const int side = c > 0.f ? 0 : 1;
+  const int side = tb + (c > 0.f ? 0 : 1);
   float lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
@@ -213,8 +213,8 @@ __device__ __forceinline__ void nb_traces(float (&tr)[16], const float* nbv, flo
 // Traces of the thread's own 16 lines along J on the outflow face: for the
 // cell downstream they are exactly the inflow traces of its upwind neighbour.
 template <int J>
-__device__ __forceinline__ void own_traces(float (&tr)[16], const float (&u)[64], float c) {
-  const int side = c > 0.f ? 0 : 1;
+__device__ __forceinline__ void own_traces(float (&tr)[16], const float (&u)[64], float c, int tb) {
+  const int side = tb + (c > 0.f ? 0 : 1);
   float lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
@@ -234,8 +234,8 @@ __device__ __forceinline__ void own_traces(float (&tr)[16], const float (&u)[64]
 // c) come from constant memory into registers, so one body serves both signs.
 template <int J>
 __device__ __forceinline__ void lines_dir(float (&r)[64], const float (&u)[64],
-                                          const float (&tr)[16], float c, float tscale) {
-  const int side = c > 0.f ? 0 : 1;
+                                          const float (&tr)[16], float c, int tb, float tscale) {
+  const int side = tb + (c > 0.f ? 0 : 1);
   float Ln[4], G[16];
 #pragma unroll
   for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
@@ -258,10 +258,10 @@ __device__ __forceinline__ void lines_dir(float (&r)[64], const float (&u)[64],
 
 template <int J, bool ROWS, bool ADJ>
 __device__ __forceinline__ void direction(float (&r)[64], const float (&u)[64], const float* nbv,
-                                          float c, float wthread, const Tab1D<float>& T) {
+                                          float c, int tb, float wthread, const Tab1D<float>& T) {
   float tr[16];
-  nb_traces<J, ROWS, ADJ>(tr, nbv, c, T);
-  lines_dir<J>(r, u, tr, c, ADJ ? wthread : 1.f);
+  nb_traces<J, ROWS, ADJ>(tr, nbv, c, tb, T);
+  lines_dir<J>(r, u, tr, c, tb, ADJ ? wthread : 1.f);
 }
 
 struct Pipe {
@@ -340,6 +340,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
   __shared__ unsigned s_item;
   const int t = threadIdx.x;
   const Tab1D<float>& T = p.t32;
+  const int tb = 2 * p.tab;              // constant-table set of the basis
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
   const unsigned ncx = static_cast<unsigned>(p.ncx);
   const unsigned S3 = static_cast<unsigned>(p.cstride[5]);   // pencils along v3
@@ -438,17 +439,17 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
       for (int e = 0; e < 64; ++e) u[e] *= winv_t * wprod(T.winv, e);
     }
     ok &= mv.wait(P, p.err);
-    direction<0, true, ADJ>(r, u, view<true>(sm6 + P * kCellSmem, t), sp[0], winv_t, T);
+    direction<0, true, ADJ>(r, u, view<true>(sm6 + P * kCellSmem, t), sp[0], tb, winv_t, T);
     fence_async_smem();
     __syncthreads();
     mv.issue(P, cellp(nbr[2]), t);               // x3
     ok &= mv.wait(Q, p.err);
-    direction<1, true, ADJ>(r, u, view<true>(sm6 + Q * kCellSmem, t), sp[1], winv_t, T);
+    direction<1, true, ADJ>(r, u, view<true>(sm6 + Q * kCellSmem, t), sp[1], tb, winv_t, T);
     fence_async_smem();
     __syncthreads();
     mv.issue(Q, cellp(nbr[3]), t);               // v1
     ok &= mv.wait(P, p.err);
-    direction<2, true, ADJ>(r, u, view<true>(sm6 + P * kCellSmem, t), sp[2], winv_t, T);
+    direction<2, true, ADJ>(r, u, view<true>(sm6 + P * kCellSmem, t), sp[2], tb, winv_t, T);
     __syncthreads();                             // P is free: it takes the phase X result
     {
       float* rb = sm6 + P * kCellSmem + t * kPad;
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     if (has_next) mv.issue(A, cellp(next), t);   // the next cell
     mv.issue(P, cellp(nbr[4]), t);               // v2
     ok &= mv.wait(Q, p.err);
-    direction<0, false, ADJ>(r, u, view<false>(sm6 + Q * kCellSmem, t), sp[3], winv_t, T);
+    direction<0, false, ADJ>(r, u, view<false>(sm6 + Q * kCellSmem, t), sp[3], tb, winv_t, T);
     fence_async_smem();
     __syncthreads();
     if (need_v3)
@@ -479,14 +480,14 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     else if (has_next)
       mv.issue(Q, cellp(nbn[0]), t);             // x1 of the next cell
     ok &= mv.wait(P, p.err);
-    direction<1, false, ADJ>(r, u, view<false>(sm6 + P * kCellSmem, t), sp[4], winv_t, T);
+    direction<1, false, ADJ>(r, u, view<false>(sm6 + P * kCellSmem, t), sp[4], tb, winv_t, T);
     fence_async_smem();
     __syncthreads();
     if (has_next) mv.issue(P, cellp(need_v3 ? nbn[0] : nbn[1]), t);  // x1 or x2 of the next cell
     float tr[16];
     if (need_v3) {
       ok &= mv.wait(Q, p.err);
-      nb_traces<2, false, ADJ>(tr, view<false>(sm6 + Q * kCellSmem, t), sp[5], T);
+      nb_traces<2, false, ADJ>(tr, view<false>(sm6 + Q * kCellSmem, t), sp[5], tb, T);
 #pragma unroll
       for (int k = 0; k < 16; ++k) tr[k] *= ADJ ? winv_t : 1.f;
     } else {
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     {
       // this cell's outflow traces become the next cell's inflow traces
       float to[16];
-      own_traces<2>(to, u, sp[5]);
+      own_traces<2>(to, u, sp[5], tb);
 #pragma unroll
       for (int k = 0; k < 16; ++k) carried[k] = to[k];
     }
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     // ---- last direction fused with step 5: scatter / LSRK stage update
     const size_t g0 = static_cast<size_t>(cell) * 4096 + t;
     if (p.mode == 0) {
-      lines_dir<2>(r, u, tr, sp[5], 1.f);
+      lines_dir<2>(r, u, tr, sp[5], tb, 1.f);
       TW* dst = static_cast<TW*>(p.dst);
 #pragma unroll
       for (int m = 0; m < 64; ++m) {
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
       double uo[32];
 #pragma unroll
       for (int m = 0; m < 32; ++m) uo[m] = __ldcs(uu + g0 + 64 * m);
-      lines_dir<2>(r, u, tr, sp[5], 1.f);
+      lines_dir<2>(r, u, tr, sp[5], tb, 1.f);
       TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
       const float af = static_cast<float>(p.a_dt);
@@ -700,9 +701,9 @@ __device__ __forceinline__ constexpr int pk(int l, int p) {
 // buffer view (J = 0, 2: 8 lines; J = 1: 16 lines, partial sums over the two
 // halves added across the pair).
 template <int J, bool ROWS, bool ADJ>
-__device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, const int (&o)[4], float c, int h,
+__device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, const int (&o)[4], float c, int tb, int h,
                                             const Tab1D<float>& T) {
-  const int side = c > 0.f ? 0 : 1;
+  const int side = tb + (c > 0.f ? 0 : 1);
   float lw[4];
   if constexpr (J == 1) {
     lw[0] = c_lw[side][h];
@@ -738,8 +739,8 @@ __device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, c
 // h + 2 and receives the partner's two values of each line by shuffles.  The
 // rows depend on h, so their entries (scaled by c) are loaded into registers.
 __device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32],
-                                            const float (&tr)[16], float c, float tscale, int h) {
-  const int side = c > 0.f ? 0 : 1;
+                                            const float (&tr)[16], float c, int tb, float tscale, int h) {
+  const int side = tb + (c > 0.f ? 0 : 1);
   // columns ordered (own b = 0, own b = 1, partner b = 0, partner b = 1)
   float G[2][4], Ln[2];
 #pragma unroll
@@ -771,12 +772,12 @@ __device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32]
 
 template <int J>
 __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], const float (&tr)[16],
-                                        float c, float tscale, int h) {
+                                        float c, int tb, float tscale, int h) {
   if constexpr (J == 1) {
-    lines_split(r, u, tr, c, tscale, h);
+    lines_split(r, u, tr, c, tb, tscale, h);
   } else {
     // the 8 local lines along J = 0 or 2
-    const int side = c > 0.f ? 0 : 1;
+    const int side = tb + (c > 0.f ? 0 : 1);
     float Ln[4], G[16];
 #pragma unroll
     for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
@@ -797,8 +798,8 @@ __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], co
 }
 
 // own outflow traces along the last digit (8 local lines)
-__device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32], float c) {
-  const int side = c > 0.f ? 0 : 1;
+__device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32], float c, int tb) {
+  const int side = tb + (c > 0.f ? 0 : 1);
   float lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
@@ -813,11 +814,11 @@ __device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32
 
 template <int J, bool ROWS, bool ADJ>
 __device__ __forceinline__ void direction_p(float (&r)[32], const float (&u)[32], const float* nbv,
-                                            const int (&o)[4], float c, float wthread, int h,
+                                            const int (&o)[4], float c, int tb, float wthread, int h,
                                             const Tab1D<float>& T) {
   float tr[16];
-  nb_traces_p<J, ROWS, ADJ>(tr, nbv, o, c, h, T);
-  lines_p<J>(r, u, tr, c, ADJ ? wthread : 1.f, h);
+  nb_traces_p<J, ROWS, ADJ>(tr, nbv, o, c, tb, h, T);
+  lines_p<J>(r, u, tr, c, tb, ADJ ? wthread : 1.f, h);
 }
 
 // Tensor copy of one cell into a swizzled buffer: two boxes of 32 x 1 x 64
@@ -940,6 +941,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
   const int t = 16 * (T_ >> 5) + (lane & 7) + 8 * (lane >> 4);
   const bool issuer = h == 0;          // one thread per block row issues its copies
   const Tab1D<float>& T = p.t32;
+  const int tb = 2 * p.tab;              // constant-table set of the basis
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
   const unsigned S3 = static_cast<unsigned>(p.cstride[5]);   // pencils along v3
   const unsigned SV3 = S3 / static_cast<unsigned>(p.ncx);    // v-cell stride of v3
@@ -1052,17 +1054,17 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
       for (int k = 0; k < 32; ++k) u[k] *= winv_t * wprod_p(T.winv, k, h);
     }
     ok &= mv.wait(P, p.err);
-    direction_p<0, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[0], winv_t, h, T);
+    direction_p<0, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[0], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     issue(P, nbr[2]);                            // x3
     ok &= mv.wait(Q, p.err);
-    direction_p<1, true, ADJ>(r, u, sm6 + Q * kCellF, o, sp[1], winv_t, h, T);
+    direction_p<1, true, ADJ>(r, u, sm6 + Q * kCellF, o, sp[1], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     issue(Q, nbr[3]);                            // v1
     ok &= mv.wait(P, p.err);
-    direction_p<2, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[2], winv_t, h, T);
+    direction_p<2, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[2], tb, winv_t, h, T);
     __syncthreads();                             // P is free: it takes the phase X result
     {
       float* rb = sm6 + P * kCellF;
@@ -1088,7 +1090,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
     if (has_next) issue(A, next);                // the next cell
     issue(P, nbr[4]);                            // v2
     ok &= mv.wait(Q, p.err);
-    direction_p<0, false, ADJ>(r, u, sm6 + Q * kCellF, o, sp[3], winv_t, h, T);
+    direction_p<0, false, ADJ>(r, u, sm6 + Q * kCellF, o, sp[3], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     if (need_v3)
@@ -1096,14 +1098,14 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
     else if (has_next)
       issue(Q, nx0);                             // x1 of the next cell
     ok &= mv.wait(P, p.err);
-    direction_p<1, false, ADJ>(r, u, sm6 + P * kCellF, o, sp[4], winv_t, h, T);
+    direction_p<1, false, ADJ>(r, u, sm6 + P * kCellF, o, sp[4], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     if (has_next) issue(P, need_v3 ? nx0 : nx1);        // x1 or x2 of the next cell
     float tr[16];
     if (need_v3) {
       ok &= mv.wait(Q, p.err);
-      nb_traces_p<2, false, ADJ>(tr, sm6 + Q * kCellF, o, sp[5], h, T);
+      nb_traces_p<2, false, ADJ>(tr, sm6 + Q * kCellF, o, sp[5], tb, h, T);
 #pragma unroll
       for (int k = 0; k < 8; ++k) tr[k] *= ADJ ? winv_t : 1.f;
     } else {
@@ -1114,7 +1116,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
     }
     {
       float to[8];
-      own_traces_p(to, u, sp[5]);
+      own_traces_p(to, u, sp[5], tb);
       *reinterpret_cast<float4*>(carried) = make_float4(to[0], to[1], to[2], to[3]);
       *reinterpret_cast<float4*>(carried + 4) = make_float4(to[4], to[5], to[6], to[7]);
     }
@@ -1122,7 +1124,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
     // ---- last direction fused with step 5: scatter / LSRK stage update
     const size_t g0 = static_cast<size_t>(cell) * 4096 + t + 256 * h;
     if constexpr (MODE == 0) {
-      lines_p<2>(r, u, tr, sp[5], 1.f, h);
+      lines_p<2>(r, u, tr, sp[5], tb, 1.f, h);
       TW* dst = static_cast<TW*>(p.dst);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
@@ -1138,7 +1140,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
       double ua[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) ua[k] = __ldcs(uu + g0 + 64 * poff(k));
-      lines_p<2>(r, u, tr, sp[5], 1.f, h);
+      lines_p<2>(r, u, tr, sp[5], tb, 1.f, h);
       TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
       const float af = static_cast<float>(p.a_dt);
@@ -1266,7 +1268,7 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t init_cell6d_tables(const Tab1D<float>& t) {
+cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab) {
   float G[2][16], Ln[2][4], lw[2][4];
   for (int i = 0; i < 16; ++i) {
     G[0][i] = t.Gp[(i / 4) * 4 + i % 4];
@@ -1278,10 +1280,11 @@ cudaError_t init_cell6d_tables(const Tab1D<float>& t) {
     lw[0][i] = t.lp[i];
     lw[1][i] = t.lm[i];
   }
+  // table set ``tab`` (0: Gauss-Legendre, 1: Gauss-Lobatto collocation)
   cudaError_t e;
-  if ((e = cudaMemcpyToSymbol(c_G, G, sizeof(G))) != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_Ln, Ln, sizeof(Ln))) != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_lw, lw, sizeof(lw));
+  if ((e = cudaMemcpyToSymbol(c_G, G, sizeof(G), tab * sizeof(G))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_Ln, Ln, sizeof(Ln), tab * sizeof(Ln))) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_lw, lw, sizeof(lw), tab * sizeof(lw));
 }
 
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {

@@ -39,10 +39,15 @@ struct Tab1D {
   T winv[kMaxN];
 };
 
-// Host-side FP64 tables (dg_tables.cpp).
+// Host-side FP64 tables (dg_tables.cpp).  zeta/w: the quadrature points
+// and weights at which the operator is collocated; dofz: the DoF nodes
+// (equal to zeta except for DG_BASIS_GLL_GAUSS); V[q][i] = phi_i(zeta_q)
+// maps DoF values to values at zeta (identity for the collocated bases).
 struct HostTables {
-  int n;
+  int n, basis;
   double zeta[kMaxN], w[kMaxN];
+  double dofz[kMaxN];
+  double V[kMaxN][kMaxN], Vinv[kMaxN][kMaxN];
   double D[kMaxN][kMaxN];  // D[p][i] = phi_i'(zeta_p)
   double lp[kMaxN], lm[kMaxN];
   double Iq[kMaxN][kMaxN];  // Iq[q][i] = int_{-1}^{zeta_q} phi_i (1D Poisson solve)
@@ -50,7 +55,10 @@ struct HostTables {
   Tab1D<float> t32;
 };
 bool gauss_legendre(int n, double* x, double* w);
-void build_tables(int n, HostTables* t);
+bool gauss_lobatto(int n, double* x, double* w);
+// DoF nodes, quadrature points and weights of a basis (any may be NULL).
+bool basis_points(int basis, int n, double* dof_nodes, double* qpoints, double* qweights);
+void build_tables(int n, int basis, HostTables* t);
 
 // Kernel parameters (passed by value; lives in the constant bank).
 struct KParams {
@@ -73,6 +81,7 @@ struct KParams {
   int adjoint;              // 1: L^T = M L(-a) M^{-1}
   int last_stage;           // stage mode: w_out = u_new
   double a_dt, b_dt;        // stage mode coefficients (a_s dt, b_s dt)
+  int tab;                  // constant-table set of the 6D kernels (0 GL, 1 GLL)
   Tab1D<double> t64;
   Tab1D<float> t32;
 };
@@ -106,7 +115,7 @@ int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int
 // cudaErrorNotSupported if the configuration is not covered.
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
 // Uploads the n = 4 tables of the specialised kernel (they depend on n only).
-cudaError_t init_cell6d_tables(const Tab1D<float>& t);
+cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab);
 
 // Records the thread's last-error message and returns s (dg_api.cu).
 dg_status report(dg_status s, const char* msg);
@@ -129,6 +138,15 @@ cudaError_t launch_poisson_1d(const double* rho, double* e, long long ncx, int n
 cudaError_t launch_field_speeds(const double* e, int comps, double scale, long long ncx, int nq,
                                 int dv, const double* two_over_hv, double* cv64, float* cv32,
                                 int* flags, int* err, cudaStream_t s);
+// An n x n matrix (row-major, leading dimension kMaxN) passed by value.
+struct BasisMat {
+  double m[kMaxN * kMaxN];
+};
+// Tensor-product change of basis on every cell (dg_misc.cu).  tmp: an FP64
+// vector of n_dofs for cells too large for shared memory (FP64 in and out
+// only there; cudaErrorNotSupported otherwise).
+cudaError_t launch_basis_change(const void* x, int x_is_float, void* y, int y_is_float, double* tmp,
+                                long long ncells, int d, int n, const BasisMat& M, cudaStream_t s);
 cudaError_t launch_charge_density(const void* f, int f_is_float, long long ncx, long long ncv,
                                   int npc, int nqx, int nqv, int dv, int n,
                                   const Tab1D<double>& t, double detJv, double* rho,
@@ -149,6 +167,8 @@ struct dg_ctx {
   double S[9] = {0}, Sinv[9] = {0};
   double detJ = 0.0;
   int field_kind = 0;
+  int basis = 0;            // dg_basis
+  double* bc_tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // DG_BASIS_GLL_GAUSS temporaries
   double a_const[dg::kMaxDim] = {0};
   double speed_sum = 0.0;
   // every cell has a single upwind side per direction (no speed component

@@ -1,4 +1,6 @@
 // Small kernels: stage-vector initialisation and the quadrature integrals.
+#include <algorithm>
+
 #include "dg_convert.cuh"
 #include "dg_internal.h"
 
@@ -278,6 +280,107 @@ cudaError_t launch_field_speeds(const double* e, int comps, double scale, long l
   const long long blocks = (n + 255) / 256;
   k_field_speeds<<<static_cast<unsigned>(blocks), 256, 0, s>>>(e, comps, scale, ncx, nq, dv, sc,
                                                                cv64, cv32, flags, err);
+  return cudaGetLastError();
+}
+
+}  // namespace dg
+
+namespace dg {
+
+// Change of basis on every cell: y = (M (x) M (x) ... (x) M) x, the n x n
+// matrix M applied along each of the d directions (tensor product, Sec. 2.3).
+// With M = V (V_qi = phi_i(zeta_q)) it maps nodal values at the Gauss-Lobatto
+// points to values at the Gauss-Legendre points; M = V^{-1} maps back; the
+// transposes serve the adjoint.  Arithmetic in FP64.
+//
+// Shared-memory form: one block per cell at a time, the cell's values
+// ping-pong between two shared arrays, one direction per pass.
+template <typename TI, typename TO>
+__global__ void k_basis_cells(const TI* __restrict__ x, TO* __restrict__ y, long long ncells, int d,
+                              int n, int npc, BasisMat M) {
+  extern __shared__ double sb[];
+  for (long long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+    const size_t off = static_cast<size_t>(cell) * npc;
+    for (int i = threadIdx.x; i < npc; i += blockDim.x) sb[i] = static_cast<double>(x[off + i]);
+    __syncthreads();
+    double* a = sb;
+    double* b = sb + npc;
+    int stride = 1;
+    for (int j = 0; j < d; ++j) {
+      for (int i = threadIdx.x; i < npc; i += blockDim.x) {
+        const int pj = (i / stride) % n;
+        const int base = i - pj * stride;
+        double s = 0.0;
+        for (int p = 0; p < n; ++p) s += M.m[pj * kMaxN + p] * a[base + p * stride];
+        b[i] = s;
+      }
+      __syncthreads();
+      double* tmp = a;
+      a = b;
+      b = tmp;
+      stride *= n;
+    }
+    for (int i = threadIdx.x; i < npc; i += blockDim.x) y[off + i] = static_cast<TO>(a[i]);
+    __syncthreads();
+  }
+}
+
+// Global-memory form for cells too large for shared memory: one direction
+// per launch, one output value per thread.
+template <typename TI, typename TO>
+__global__ void k_basis_dir(const TI* __restrict__ x, TO* __restrict__ y, long long n_dofs, int npc,
+                            int stride, int n, BasisMat M) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_dofs;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int q = static_cast<int>(i % npc);
+    const int pj = (q / stride) % n;
+    const long long base = i - static_cast<long long>(pj) * stride;
+    double s = 0.0;
+    for (int p = 0; p < n; ++p) s += M.m[pj * kMaxN + p] * static_cast<double>(x[base + p * stride]);
+    y[i] = static_cast<TO>(s);
+  }
+}
+
+cudaError_t launch_basis_change(const void* x, int x_is_float, void* y, int y_is_float, double* tmp,
+                                long long ncells, int d, int n, const BasisMat& M, cudaStream_t s) {
+  int npc = 1;
+  for (int j = 0; j < d; ++j) npc *= n;
+  const size_t smem = 2 * static_cast<size_t>(npc) * sizeof(double);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (smem <= 200 * 1024) {
+    const long long blocks = std::min<long long>(ncells, 8LL * sms);
+    const int threads = npc >= 1024 ? 512 : 128;
+    cudaError_t e;
+#define DG_BC(TI, TO)                                                                            \
+  do {                                                                                           \
+    e = cudaFuncSetAttribute(k_basis_cells<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             static_cast<int>(smem));                                            \
+    if (e != cudaSuccess) return e;                                                              \
+    k_basis_cells<TI, TO><<<static_cast<unsigned>(blocks), threads, smem, s>>>(                  \
+        static_cast<const TI*>(x), static_cast<TO*>(y), ncells, d, n, npc, M);                   \
+  } while (0)
+    if (x_is_float && y_is_float) DG_BC(float, float);
+    else if (x_is_float) DG_BC(float, double);
+    else if (y_is_float) DG_BC(double, float);
+    else DG_BC(double, double);
+#undef DG_BC
+    return cudaGetLastError();
+  }
+  // d passes through FP64 temporaries: x -> tmp -> y -> tmp ... ending in y
+  if (tmp == nullptr || x_is_float || y_is_float) return cudaErrorNotSupported;
+  const long long n_dofs = ncells * npc;
+  const long long blocks = std::min<long long>((n_dofs + 255) / 256, 16LL * sms);
+  const double* in = static_cast<const double*>(x);
+  int stride = 1;
+  for (int j = 0; j < d; ++j) {
+    double* out = ((d - 1 - j) % 2 == 0) ? static_cast<double*>(y) : tmp;
+    k_basis_dir<double, double><<<static_cast<unsigned>(blocks), 256, 0, s>>>(in, out, n_dofs, npc,
+                                                                               stride, n, M);
+    in = out;
+    stride *= n;
+  }
   return cudaGetLastError();
 }
 

@@ -1,10 +1,12 @@
-// Host-side 1D tables of the collocated Gauss-Legendre element, in FP64.
+// Host-side 1D tables of the collocated elements, in FP64.
 //
 // Gauss-Legendre points (Sec. 2.5 of arXiv 2002.08110) by Newton's method on
 // the three-term recurrence of the Legendre polynomials, weights
-// w = 2 / ((1 - x^2) P_n'(x)^2); Lagrange derivatives by the barycentric
-// formula D[p][i] = (lambda_i / lambda_p) / (x_p - x_i) (p != i), with the
-// diagonal making each row sum to zero (derivative of a constant).
+// w = 2 / ((1 - x^2) P_n'(x)^2); Gauss-Lobatto points: the endpoints and the
+// roots of P_{n-1}' (Newton's method, second derivative from Legendre's
+// equation), weights 2 / (n (n-1) P_{n-1}(x)^2).  Lagrange derivatives by the
+// barycentric formula D[p][i] = (lambda_i / lambda_p) / (x_p - x_i) (p != i),
+// with the diagonal making each row sum to zero (derivative of a constant).
 #include <cmath>
 #include <cstring>
 
@@ -44,10 +46,91 @@ bool gauss_legendre(int n, double* x, double* w) {
   return true;
 }
 
-void build_tables(int n, HostTables* t) {
+bool gauss_lobatto(int n, double* x, double* w) {
+  if (n < 2 || n > kMaxN) return false;
+  const double pi = 3.14159265358979323846;
+  const int m = n - 1;
+  x[0] = -1.0;
+  x[m] = 1.0;
+  for (int i = 1; i < m; ++i) {
+    // interior nodes: roots of P_m', started from the Chebyshev-Lobatto points
+    double z = -std::cos(pi * i / m);
+    for (int it = 0; it < 100; ++it) {
+      double pn = 0.0, dp = 0.0;
+      legendre_eval(m, z, &pn, &dp);
+      const double d2 = (2.0 * z * dp - m * (m + 1.0) * pn) / (1.0 - z * z);
+      const double dz = dp / d2;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+  }
+  for (int i = 0; i < n; ++i) {
+    double pn = 1.0, dp = 0.0;
+    if (i == 0 || i == m) {
+      pn = (i == 0 && (m % 2 == 1)) ? -1.0 : 1.0;   // P_m(-1) = (-1)^m, P_m(1) = 1
+    } else {
+      legendre_eval(m, x[i], &pn, &dp);
+    }
+    w[i] = 2.0 / (n * (n - 1.0) * pn * pn);
+  }
+  return true;
+}
+
+bool basis_points(int basis, int n, double* dof_nodes, double* qpoints, double* qweights) {
+  double gx[kMaxN], gw[kMaxN], lx[kMaxN], lw[kMaxN];
+  if (!gauss_legendre(n, gx, gw)) return false;
+  if (basis != DG_BASIS_GL && !gauss_lobatto(n, lx, lw)) return false;
+  for (int i = 0; i < n; ++i) {
+    const bool lob_q = basis == DG_BASIS_GLL;        // quadrature at the Lobatto points
+    const bool lob_n = basis != DG_BASIS_GL;         // DoFs at the Lobatto points
+    if (dof_nodes) dof_nodes[i] = lob_n ? lx[i] : gx[i];
+    if (qpoints) qpoints[i] = lob_q ? lx[i] : gx[i];
+    if (qweights) qweights[i] = lob_q ? lw[i] : gw[i];
+  }
+  return true;
+}
+
+// Lagrange polynomial i through nodes z (n points) at x.
+static double lagrange(const double* z, int n, int i, double x) {
+  double v = 1.0;
+  for (int m = 0; m < n; ++m)
+    if (m != i) v *= (x - z[m]) / (z[i] - z[m]);
+  return v;
+}
+
+void build_tables(int n, int basis, HostTables* t) {
   std::memset(t, 0, sizeof(*t));
   t->n = n;
-  gauss_legendre(n, t->zeta, t->w);
+  t->basis = basis;
+  // the operator is collocated at the quadrature points (Gauss-Legendre for
+  // bases 0 and 2, Gauss-Lobatto for basis 1); basis 2 keeps its DoFs at the
+  // Lobatto nodes and changes basis around the Gauss-Legendre operator
+  basis_points(basis, n, t->dofz, t->zeta, t->w);
+  for (int q = 0; q < n; ++q)
+    for (int i = 0; i < n; ++i) t->V[q][i] = lagrange(t->dofz, n, i, t->zeta[q]);
+  {
+    // Vinv by Gauss-Jordan elimination with partial pivoting (n <= 6)
+    double a[kMaxN][2 * kMaxN];
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < 2 * n; ++c) a[r][c] = c < n ? t->V[r][c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < n; ++r)
+        if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+      if (piv != c)
+        for (int k = 0; k < 2 * n; ++k) std::swap(a[c][k], a[piv][k]);
+      const double inv = 1.0 / a[c][c];
+      for (int k = 0; k < 2 * n; ++k) a[c][k] *= inv;
+      for (int r = 0; r < n; ++r) {
+        if (r == c) continue;
+        const double f = a[r][c];
+        for (int k = 0; k < 2 * n; ++k) a[r][k] -= f * a[c][k];
+      }
+    }
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) t->Vinv[r][c] = a[r][n + c];
+  }
   const double* x = t->zeta;
   double lam[kMaxN];
   for (int i = 0; i < n; ++i) {

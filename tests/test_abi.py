@@ -23,7 +23,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_reference_nodes(lib):
-    assert lib.dg_version() == 1
+    assert lib.dg_version() == 2
     for k in range(6):
         x = np.zeros(k + 1)
         w = np.zeros(k + 1)
@@ -33,6 +33,32 @@ def test_version_and_reference_nodes(lib):
         assert np.allclose(x, xr, atol=1e-15) and np.allclose(w, wr, atol=1e-15)
     assert lib.dg_reference_nodes(6, x.ctypes.data_as(_lib.c_double_p), None) == 1
     assert lib.dg_reference_nodes(2, None, None) == 1
+
+
+def test_basis_nodes(lib):
+    """Gauss-Lobatto nodes (endpoints and the roots of P'_{n-1}) and weights
+    (exact for polynomials of degree 2n-3) of the library's host tables."""
+    P = np.polynomial.legendre.Legendre
+    for k in range(1, 6):
+        n = k + 1
+        a = [np.zeros(n) for _ in range(3)]
+        ptrs = [x.ctypes.data_as(_lib.c_double_p) for x in a]
+        assert lib.dg_basis_nodes(1, k, *ptrs) == 0
+        nodes, qp, qw = a
+        ref = np.concatenate([[-1.0], np.sort(P.basis(n - 1).deriv().roots().real), [1.0]])
+        assert np.allclose(nodes, ref, atol=1e-14) and np.allclose(qp, ref, atol=1e-14)
+        for m in range(2 * n - 2):        # exact up to degree 2n-3
+            exact = 0.0 if m % 2 else 2.0 / (m + 1)
+            assert abs(qw @ qp ** m - exact) <= 1e-14
+        assert lib.dg_basis_nodes(2, k, *ptrs) == 0        # GLL nodes, Gauss quadrature
+        xg, wg = np.polynomial.legendre.leggauss(n)
+        assert np.allclose(a[0], ref, atol=1e-14)
+        assert np.allclose(a[1], xg, atol=1e-15) and np.allclose(a[2], wg, atol=1e-15)
+    x = np.zeros(6)
+    px = x.ctypes.data_as(_lib.c_double_p)
+    assert lib.dg_basis_nodes(3, 2, px, None, None) == 1     # unknown basis
+    assert lib.dg_basis_nodes(1, 0, px, None, None) == 1     # Lobatto needs degree >= 1
+    assert lib.dg_basis_nodes(0, 6, px, None, None) == 1
 
 
 def _create(lib, dx, dv, k, cx, cv, kind=0):
