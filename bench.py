@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cells", type=int, default=8, help="cells per direction (default 8)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--basis", choices=["gl", "gll", "gll_gauss"], default="gl",
+                    help="element of the timed step: Gauss-Legendre collocation (default), "
+                         "Gauss-Lobatto collocation, or Lobatto nodes with Gauss quadrature")
     ap.add_argument("--kernel-variant", type=int, default=None,
                     help="6D cell kernel for the FP32-sweep paths (1: 64 threads per cell, "
                          "2: 128 threads per cell); default: the library's choice")
@@ -329,6 +332,44 @@ def measure_configs(torch, hbm_peak):
     del u0, u64, u32, k64
     torch.cuda.empty_cache()
 
+    # 6D in the Gauss-Lobatto bases: the collocation variant (FP32 stage; its
+    # v neighbours arrive as face layers) and the paper's Lobatto-node,
+    # Gauss-quadrature element (steps between two changes of basis)
+    from paper_2002_08110_gb300 import BASIS_GLL, BASIS_GLL_GAUSS, basis_nodes
+    w = W.config_6d()
+    dt, _ = W.time_step(w)
+    for name, basis in (("6d_gll_collocation", BASIS_GLL), ("6d_gll_gauss", BASIS_GLL_GAUSS)):
+        nodes, qpts, _ = basis_nodes(basis, w.k)
+        dg = DG(e_nodes=W.e_table(w, qpts), basis=basis, **W.dg_kwargs(w))
+        u = W.separable_state(w, nodes, xp=torch, device="cuda")
+        if basis == BASIS_GLL:
+            a, b = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda")
+            for i in range(3):
+                dg.rk_stage(a, b, u, i, dt, prec=PREC_FP32)
+                a, b = b, a
+            reps = 20
+            ms = _timed(torch, lambda: dg.rk_stage(a, b, u, 1, dt, prec=PREC_FP32), reps)
+            dg.check()
+            gbs = 24 * dg.n_dofs / (ms * 1e-3) / 1e9
+            out[name] = {"workload": w.name + "_gll_collocation", "dofs": dg.n_dofs,
+                         "ms_per_stage": ms, "GDoF/s_per_stage": dg.n_dofs / (ms * 1e-3) / 1e9,
+                         "frac_hbm": gbs / hbm_peak, "bytes_per_dof": 24,
+                         "uniform_sides": int(dg.info.uniform_sides)}
+            del a, b
+        else:
+            nst = 5
+            dg.rk_step(u, dt, nsteps=1, prec=PREC_FP32)
+            ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=nst, prec=PREC_FP32), 1)
+            dg.check()
+            out[name] = {"workload": w.name + "_gll_gauss", "dofs": dg.n_dofs, "steps_per_call": nst,
+                         "ms_per_step": ms / nst,
+                         "GDoF/s_per_stage": dg.n_dofs / (ms / nst / 5 * 1e-3) / 1e9,
+                         "note": "each call changes the FP64 state to the Gauss points and back "
+                                 "around its steps (two tensor-product passes)"}
+        dg.close()
+        del u
+        torch.cuda.empty_cache()
+
     # 2D: one period (T = 2, 240 steps), FP64
     w = W.config_2d()
     dg, zeta = make(w)
@@ -420,9 +461,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = W.config_6d(cells=args.cells)
-    zeta, _ = reference_nodes(w.k)
-    E = W.e_table(w, zeta)
-    dg = DG(e_nodes=E, **W.dg_kwargs(w))
+    from paper_2002_08110_gb300 import basis_nodes
+    basis = {"gl": 0, "gll": 1, "gll_gauss": 2}[args.basis]
+    zeta, qpts, _ = basis_nodes(basis, w.k)     # DoF nodes, quadrature points
+    E = W.e_table(w, qpts)
+    dg = DG(e_nodes=E, basis=basis, **W.dg_kwargs(w))
     if args.kernel_variant is not None:
         for prec in (PREC_FP32, PREC_MIXED):
             c = dg.get_launch(prec)
@@ -478,7 +521,7 @@ def main():
     bpd = BYTES_PER_DOF["stage_fp32w_fp64u" if kind == "stage" else kind]
     achieved = bpd * n / (avg_launch * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": recorded_traffic(kind),
+            "frac": achieved / hbm_peak, "traffic": recorded_traffic(kind if args.basis == "gl" else f"{kind}_{args.basis}"),
             "peak_kind": peak_kind, "bytes_per_dof": bpd,
             "kernel": "fused LSRK stage (cell kernel, stage mode)" if kind == "stage" else "cell kernel, operator application"}
 
@@ -563,7 +606,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": w.name, "dofs": n, "cells": w.ncells, "degree": w.k,
+            "config": {"workload": w.name if args.basis == "gl" else f"{w.name}_{args.basis}",
+                       "basis": args.basis, "dofs": n, "cells": w.ncells, "degree": w.k,
                        "step": "fused LSRK(5,4) stage: FP32 sweeps, FP32 stage vector, FP64 state",
                        "l2": "inputs larger than L2 (vectors 4.3-8.6 GB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

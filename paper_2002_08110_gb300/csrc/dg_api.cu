@@ -302,6 +302,12 @@ void free_ctx(dg_ctx* h) {
   delete h;
 }
 
+cudaError_t upload32(const std::vector<float>& src, float** dst) {
+  cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, src.size()) * sizeof(float));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(float), cudaMemcpyHostToDevice);
+}
+
 template <typename T>
 cudaError_t upload(const std::vector<double>& src, T** dst) {
   std::vector<T> tmp(src.size());
@@ -353,22 +359,41 @@ dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
         if (!std::isfinite(a)) return fail(DG_ERR_INVALID_ARG, "E is not finite");
         h->cv_host[(cx * h->nqx + q) * dv + i] = 2.0 / h->h[dx + i] * a;
       }
-  // uniform upwind side per cell and direction (zero speeds fit either side)
-  auto uniform = [](const std::vector<double>& tab, long long ncellsub, int nq, int dims) {
+  // Upwind side per cell and direction, and the FP32 tables of the FP32-sweep
+  // kernels.  A cell's side is the sign of its largest speed; speeds of at
+  // most 1e-12 of that (zeros of the field that fall on nodes, e.g. v = 0 on
+  // a Gauss-Lobatto face node, up to rounding) carry no flux at FP32
+  // precision and are stored as a zero with the cell's sign, so every node of
+  // the cell reads the same side; the cell is uniform if no larger speed has
+  // the other sign.  The FP64 tables keep the exact values.
+  auto sides = [](const std::vector<double>& tab, std::vector<float>& f32, long long ncellsub,
+                  int nq, int dims) {
+    f32.assign(tab.size(), 0.f);
+    bool ok = true;
     for (long long c = 0; c < ncellsub; ++c)
       for (int j = 0; j < dims; ++j) {
-        bool pos = false, neg = false;
+        double big = 0.0;
         for (int q = 0; q < nq; ++q) {
           const double v = tab[(c * nq + q) * dims + j];
-          pos |= v > 0.0;
-          neg |= v < 0.0;
+          if (std::fabs(v) > std::fabs(big)) big = v;
         }
-        if (pos && neg) return false;
+        const double thr = 1e-12 * std::fabs(big);
+        for (int q = 0; q < nq; ++q) {
+          const size_t r = (c * nq + q) * dims + j;
+          const double v = tab[r];
+          if (std::fabs(v) <= thr) {
+            f32[r] = big < 0.0 ? -0.0f : 0.0f;
+          } else {
+            f32[r] = static_cast<float>(v);
+            ok = ok && ((v > 0.0) == (big > 0.0));
+          }
+        }
       }
-    return true;
+    return ok;
   };
-  h->cx_uniform = uniform(h->cx_host, h->ncv, h->nqv, dx);
-  h->uniform_sides = h->cx_uniform && uniform(h->cv_host, h->ncx, h->nqx, dv);
+  h->cx_uniform = sides(h->cx_host, h->cx32_host, h->ncv, h->nqv, dx);
+  const bool cv_uniform = sides(h->cv_host, h->cv32_host, h->ncx, h->nqx, dv);   // always built
+  h->uniform_sides = h->cx_uniform && cv_uniform;
   double sum = 0.0;
   for (int j = 0; j < h->d; ++j) {
     double mx = 0.0;
@@ -560,9 +585,9 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess ||
       (e = upload(h->cx_host, &h->cx_d64)) != cudaSuccess ||
-      (e = upload(h->cx_host, &h->cx_d32)) != cudaSuccess ||
+      (e = upload32(h->cx32_host, &h->cx_d32)) != cudaSuccess ||
       (e = upload(h->cv_host, &h->cv_d64)) != cudaSuccess ||
-      (e = upload(h->cv_host, &h->cv_d32)) != cudaSuccess ||
+      (e = upload32(h->cv32_host, &h->cv_d32)) != cudaSuccess ||
       (e = cudaMalloc(&h->err_d, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(h->err_d, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&h->work_d, 16 * sizeof(unsigned))) != cudaSuccess ||
@@ -644,13 +669,13 @@ dg_status dg_set_field(dg_handle h, const double* e_nodes, void* stream) {
   if (s != DG_OK) return s;
   if (h->uniform_sides != was_uniform) drop_graphs(h);   // they hold the other kernel
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::vector<float> f(h->cv_host.begin(), h->cv_host.end());
   cudaError_t e;
   // synchronous with respect to the host buffers (pageable copies)
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess ||
       (e = cudaMemcpy(h->cv_d64, h->cv_host.data(), h->cv_host.size() * 8, cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
-      (e = cudaMemcpy(h->cv_d32, f.data(), f.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+      (e = cudaMemcpy(h->cv_d32, h->cv32_host.data(), h->cv32_host.size() * 4,
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "dg_set_field");
   // graphs captured with the same kernel stay valid (tables are read at run time)
   return DG_OK;

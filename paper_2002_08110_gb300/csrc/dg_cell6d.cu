@@ -187,7 +187,7 @@ __constant__ float c_lw[4][4];
 template <int J, bool ROWS, bool ADJ>
 __device__ __forceinline__ void nb_traces(float (&tr)[16], const float* nbv, float c, int tb,
                                           const Tab1D<float>& T) {
-  const int side = tb + (c > 0.f ? 0 : 1);
+  const int side = tb + (signbit(c) ? 1 : 0);
   float lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
@@ -214,7 +214,7 @@ __device__ __forceinline__ void nb_traces(float (&tr)[16], const float* nbv, flo
 // cell downstream they are exactly the inflow traces of its upwind neighbour.
 template <int J>
 __device__ __forceinline__ void own_traces(float (&tr)[16], const float (&u)[64], float c, int tb) {
-  const int side = tb + (c > 0.f ? 0 : 1);
+  const int side = tb + (signbit(c) ? 1 : 0);
   float lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
@@ -235,7 +235,7 @@ __device__ __forceinline__ void own_traces(float (&tr)[16], const float (&u)[64]
 template <int J>
 __device__ __forceinline__ void lines_dir(float (&r)[64], const float (&u)[64],
                                           const float (&tr)[16], float c, int tb, float tscale) {
-  const int side = tb + (c > 0.f ? 0 : 1);
+  const int side = tb + (signbit(c) ? 1 : 0);
   float Ln[4], G[16];
 #pragma unroll
   for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       if (ADJ) sp[j] = -sp[j];
-      nbr[j] = nb32(p, c, j, sp[j] > 0.f ? -1 : 1);
+      nbr[j] = nb32(p, c, j, signbit(sp[j]) ? 1 : -1);
     }
   };
   // v3 direction of a pencil (the same for all its cells and threads)
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
     const unsigned cx = b % ncx;
     float c5 = static_cast<const float*>(p.cv_tab)[(static_cast<size_t>(cx) * 64) * 3 + 2];
     if (ADJ) c5 = -c5;
-    return c5 >= 0.f;
+    return !signbit(c5);
   };
   auto pencil_cell = [&](unsigned b, int i, bool fwd) {
     return b + static_cast<unsigned>(fwd ? i : N3 - 1 - i) * S3;
@@ -703,7 +703,7 @@ __device__ __forceinline__ constexpr int pk(int l, int p) {
 template <int J, bool ROWS, bool ADJ>
 __device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, const int (&o)[4], float c, int tb, int h,
                                             const Tab1D<float>& T) {
-  const int side = tb + (c > 0.f ? 0 : 1);
+  const int side = tb + (signbit(c) ? 1 : 0);
   float lw[4];
   if constexpr (J == 1) {
     lw[0] = c_lw[side][h];
@@ -740,7 +740,7 @@ __device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, c
 // rows depend on h, so their entries (scaled by c) are loaded into registers.
 __device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32],
                                             const float (&tr)[16], float c, int tb, float tscale, int h) {
-  const int side = tb + (c > 0.f ? 0 : 1);
+  const int side = tb + (signbit(c) ? 1 : 0);
   // columns ordered (own b = 0, own b = 1, partner b = 0, partner b = 1)
   float G[2][4], Ln[2];
 #pragma unroll
@@ -777,7 +777,7 @@ __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], co
     lines_split(r, u, tr, c, tb, tscale, h);
   } else {
     // the 8 local lines along J = 0 or 2
-    const int side = tb + (c > 0.f ? 0 : 1);
+    const int side = tb + (signbit(c) ? 1 : 0);
     float Ln[4], G[16];
 #pragma unroll
     for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
@@ -799,7 +799,7 @@ __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], co
 
 // own outflow traces along the last digit (8 local lines)
 __device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32], float c, int tb) {
-  const int side = tb + (c > 0.f ? 0 : 1);
+  const int side = tb + (signbit(c) ? 1 : 0);
   float lw[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) lw[i] = c_lw[side][i];
@@ -836,6 +836,29 @@ __device__ __forceinline__ void tma_cell(float* dst, const CUtensorMap* tm, unsi
         : "memory");
 }
 
+// Face layers of a cell for the Gauss-Lobatto collocation, whose neighbour
+// traces are the neighbour's face nodes: the 16 rows (v nodes) with one v
+// digit fixed, as two compact 32 x 16 boxes (column halves) of the 5D view
+// (32, 2, 4 [q4], 4 [q5], 4 cells [q6]) of the stage vector.  dir 0, 1, 2 =
+// v1, v2, v3; f = the face node (0 or 3).  Compact row m runs over the other
+// two v digits (the lower one fastest).
+struct FaceMaps {
+  CUtensorMap m[3];
+};
+__device__ __forceinline__ void tma_face(float* dst, const FaceMaps* fm, int dir, unsigned cell, int f,
+                                         unsigned long long* bar, unsigned long long pol) {
+  const int c2 = dir == 0 ? f : 0, c3 = dir == 1 ? f : 0;
+  const int c4 = static_cast<int>(cell * 4u) + (dir == 2 ? f : 0);
+#pragma unroll
+  for (int h2 = 0; h2 < 2; ++h2)
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(smem_u32(dst + 512 * h2)),
+        "l"(reinterpret_cast<unsigned long long>(&fm->m[dir])), "r"(0), "r"(h2), "r"(c2), "r"(c3),
+        "r"(c4), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
 // Moves cells into the swizzled buffers.  FP32 input: one thread issues the
 // tensor copy.  FP64 input: each row's thread loads, converts and stores it.
 template <typename TIN>
@@ -863,6 +886,14 @@ struct Mover2 {
       }
     }
   }
+  // FP32 input only: the face layer of ``cell`` along v direction dir
+  __device__ __forceinline__ void issue_face(int b, unsigned cell, const FaceMaps* fm, int dir, int f,
+                                             int T_) {
+    if (T_ == 0) {
+      mbar_expect_tx(&pp->bar[b], 16 * 64 * 4);
+      tma_face(sm + b * kCellF, fm, dir, cell, f, &pp->bar[b], pol);
+    }
+  }
   __device__ __forceinline__ bool wait(int b, int* err) {
     if constexpr (sizeof(TIN) == 4) {
       const unsigned par = (phase >> b) & 1u;
@@ -879,6 +910,40 @@ struct Mover2 {
     }
   }
 };
+
+// Upwind traces from a compact face buffer (Gauss-Lobatto collocation: the
+// trace of a line is its face node, the neighbour's face layer holds them).
+// Thread (t, h) in phase V, local direction J of the v block:
+//   J = 0 (v1): lines (b, c) -> row m = (h + 2 b) + 4 c
+//   J = 1 (v2): lines (a, c) -> row m = a + 4 c      (16 lines, no shuffle)
+//   J = 2 (v3): lines (a, b) -> row m = a + 4 (h + 2 b)
+template <int J, bool ADJ>
+__device__ __forceinline__ void face_traces(float (&tr)[16], const float* buf, int t, int h, int f,
+                                            const Tab1D<float>& T) {
+  const int base = (t >> 5) * 512 + (t & 3);
+  const int tc = (t >> 2) & 7;
+  constexpr int nl = J == 1 ? 16 : 8;
+#pragma unroll
+  for (int l = 0; l < nl; ++l) {
+    int m, k;   // compact row, and the local element index (for the adjoint weights)
+    if constexpr (J == 0) {
+      m = (h + 2 * (l & 1)) + 4 * (l >> 1);
+      k = f + 4 * (l & 1) + 8 * (l >> 1);
+    } else if constexpr (J == 1) {
+      m = l;
+      k = (l & 3) + 8 * (l >> 2);
+    } else {
+      m = (l & 3) + 4 * (h + 2 * (l >> 2));
+      k = (l & 3) + 4 * (l >> 2) + 8 * f;
+    }
+    float x = buf[base + 32 * m + 4 * (tc ^ (m & 7))];
+    if (ADJ) {
+      if constexpr (J == 1) x *= T.winv[l & 3] * T.winv[f] * T.winv[l >> 2];
+      else x *= wprod_p(T.winv, k, h);
+    }
+    tr[l] = x;
+  }
+}
 
 // Block-uniform description of a work item (a v3 pencil), kept in shared
 // memory so that per-cell neighbour indices need no integer division.
@@ -913,7 +978,7 @@ __device__ __forceinline__ void pencil_info(const KParams& p, unsigned item, Pen
   pi.cvb = base / ncx;
   float c5 = static_cast<const float*>(p.cv_tab)[(static_cast<size_t>(pi.cx) * 64) * 3 + 2];
   if (ADJ) c5 = -c5;
-  pi.fwd = c5 >= 0.f ? 1u : 0u;
+  pi.fwd = signbit(c5) ? 0u : 1u;
 }
 
 // upwind neighbour along j of a cell at coordinate cj (periodic wrap)
@@ -921,14 +986,18 @@ __device__ __forceinline__ unsigned nb_c(const KParams& p, unsigned cell, unsign
                                          float c) {
   const unsigned st = static_cast<unsigned>(p.cstride[j]);
   const unsigned nj = static_cast<unsigned>(p.ncell[j]);
-  if (c > 0.f) return cj == 0 ? cell + (nj - 1) * st : cell - st;
+  if (!signbit(c)) return cj == 0 ? cell + (nj - 1) * st : cell - st;
   return cj == nj - 1 ? cell - (nj - 1) * st : cell + st;
 }
 
 // MODE 0: operator application (dst = K); MODE 1: fused LSRK stage.
-template <typename TIN, typename TW, bool ADJ, int MODE>
-__global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
-                                                      const __grid_constant__ CUtensorMap tmap) {
+// FACE: Gauss-Lobatto collocation with FP32 input; the v neighbours arrive
+// as face layers only (a quarter of a cell each).
+// TAB: constant-table set (0 Gauss-Legendre, 1 Gauss-Lobatto), a compile-time
+// offset so that it costs no register.
+template <typename TIN, typename TW, bool ADJ, int MODE, bool FACE, int TAB>
+__device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMap& tmap,
+                                              const FaceMaps* fmaps) {
   extern __shared__ __align__(128) float sm_raw[];
   // swizzled buffers need 1024-byte alignment (one KB of slack is allocated)
   float* const sm6 = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u) / 4;
@@ -941,7 +1010,7 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
   const int t = 16 * (T_ >> 5) + (lane & 7) + 8 * (lane >> 4);
   const bool issuer = h == 0;          // one thread per block row issues its copies
   const Tab1D<float>& T = p.t32;
-  const int tb = 2 * p.tab;              // constant-table set of the basis
+  constexpr int tb = 2 * TAB;            // constant-table set of the basis
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
   const unsigned S3 = static_cast<unsigned>(p.cstride[5]);   // pencils along v3
   const unsigned SV3 = S3 / static_cast<unsigned>(p.ncx);    // v-cell stride of v3
@@ -1062,7 +1131,10 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
     direction_p<1, true, ADJ>(r, u, sm6 + Q * kCellF, o, sp[1], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
-    issue(Q, nbr[3]);                            // v1
+    if constexpr (FACE)
+      mv.issue_face(Q, nbr[3], fmaps, 0, signbit(sp[3]) ? 0 : 3, T_);   // v1 face layer
+    else
+      issue(Q, nbr[3]);                          // v1
     ok &= mv.wait(P, p.err);
     direction_p<2, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[2], tb, winv_t, h, T);
     __syncthreads();                             // P is free: it takes the phase X result
@@ -1088,24 +1160,46 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
     fence_async_smem();
     __syncthreads();                             // A and P are free
     if (has_next) issue(A, next);                // the next cell
-    issue(P, nbr[4]);                            // v2
+    if constexpr (FACE)
+      mv.issue_face(P, nbr[4], fmaps, 1, signbit(sp[4]) ? 0 : 3, T_);   // v2 face layer
+    else
+      issue(P, nbr[4]);                          // v2
     ok &= mv.wait(Q, p.err);
-    direction_p<0, false, ADJ>(r, u, sm6 + Q * kCellF, o, sp[3], tb, winv_t, h, T);
+    if constexpr (FACE) {
+      float tr[16];
+      face_traces<0, ADJ>(tr, sm6 + Q * kCellF, t, h, signbit(sp[3]) ? 0 : 3, T);
+      lines_p<0>(r, u, tr, sp[3], tb, ADJ ? winv_t : 1.f, h);
+    } else {
+      direction_p<0, false, ADJ>(r, u, sm6 + Q * kCellF, o, sp[3], tb, winv_t, h, T);
+    }
     fence_async_smem();
     __syncthreads();
-    if (need_v3)
-      issue(Q, nbr[5]);                          // v3 (wrapped, not carried)
+    if (need_v3) {
+      if constexpr (FACE)
+        mv.issue_face(Q, nbr[5], fmaps, 2, signbit(sp[5]) ? 0 : 3, T_);  // v3 face layer
+      else
+        issue(Q, nbr[5]);                        // v3 (wrapped, not carried)
+    }
     else if (has_next)
       issue(Q, nx0);                             // x1 of the next cell
     ok &= mv.wait(P, p.err);
-    direction_p<1, false, ADJ>(r, u, sm6 + P * kCellF, o, sp[4], tb, winv_t, h, T);
+    if constexpr (FACE) {
+      float tr[16];
+      face_traces<1, ADJ>(tr, sm6 + P * kCellF, t, h, signbit(sp[4]) ? 0 : 3, T);
+      lines_p<1>(r, u, tr, sp[4], tb, ADJ ? winv_t : 1.f, h);
+    } else {
+      direction_p<1, false, ADJ>(r, u, sm6 + P * kCellF, o, sp[4], tb, winv_t, h, T);
+    }
     fence_async_smem();
     __syncthreads();
     if (has_next) issue(P, need_v3 ? nx0 : nx1);        // x1 or x2 of the next cell
     float tr[16];
     if (need_v3) {
       ok &= mv.wait(Q, p.err);
-      nb_traces_p<2, false, ADJ>(tr, sm6 + Q * kCellF, o, sp[5], tb, h, T);
+      if constexpr (FACE)
+        face_traces<2, ADJ>(tr, sm6 + Q * kCellF, t, h, signbit(sp[5]) ? 0 : 3, T);
+      else
+        nb_traces_p<2, false, ADJ>(tr, sm6 + Q * kCellF, o, sp[5], tb, h, T);
 #pragma unroll
       for (int k = 0; k < 8; ++k) tr[k] *= ADJ ? winv_t : 1.f;
     } else {
@@ -1206,6 +1300,20 @@ __global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
   if (bad) atomicOr(p.err, 1);
 }
 
+template <typename TIN, typename TW, bool ADJ, int MODE, int TAB>
+__global__ void __launch_bounds__(128, 4) k_cell6d4p(const KParams p,
+                                                      const __grid_constant__ CUtensorMap tmap) {
+  cell6d4p_body<TIN, TW, ADJ, MODE, false, TAB>(p, tmap, nullptr);
+}
+
+// Gauss-Lobatto collocation, FP32 input: the v neighbours as face layers.
+template <typename TIN, typename TW, bool ADJ, int MODE>
+__global__ void __launch_bounds__(128, 4) k_cell6d4p_face(const KParams p,
+                                                           const __grid_constant__ CUtensorMap tmap,
+                                                           const __grid_constant__ FaceMaps fmaps) {
+  cell6d4p_body<TIN, TW, ADJ, MODE, true, 1>(p, tmap, &fmaps);
+}
+
 // The driver's tensor-map encoder, looked up once through the runtime.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1237,16 +1345,57 @@ cudaError_t encode_cell_map(CUtensorMap* tm, const void* src, long long ncells) 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Face layers: 5D view (32 floats, 2 halves, 4 [q4], 4 [q5], 4 cells [q6])
+// of an FP32 stage vector, boxes of 16 rows with one v digit fixed.
+cudaError_t encode_face_maps(FaceMaps* fm, const void* src, long long ncells) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {32, 2, 4, 4, static_cast<cuuint64_t>(ncells) * 4};
+  const cuuint64_t strides[4] = {128, 256, 1024, 4096};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const cuuint32_t boxes[3][5] = {{32, 1, 1, 4, 4}, {32, 1, 4, 1, 4}, {32, 1, 4, 4, 1}};
+  for (int d = 0; d < 3; ++d) {
+    CUresult r = enc(&fm->m[d], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(src), dims,
+                     strides, boxes[d], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
 template <typename TIN, typename TW, bool ADJ>
 cudaError_t launch6p(KParams& p, cudaStream_t s) {
-  auto kern = p.mode == 0 ? k_cell6d4p<TIN, TW, ADJ, 0> : k_cell6d4p<TIN, TW, ADJ, 1>;
+  constexpr bool kF32 = sizeof(TIN) == 4;
+  const bool face = kF32 && p.tab == 1;
+  // kernels: Gauss-Legendre tables; Gauss-Lobatto with FP32 input (face
+  // layers); Gauss-Lobatto with FP64 input (full cells)
+  const void* kern;
+  if constexpr (kF32) {
+    if (face)
+      kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p_face<float, float, ADJ, 0>)
+                         : reinterpret_cast<const void*>(k_cell6d4p_face<float, float, ADJ, 1>);
+    else
+      kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 0, 0>)
+                         : reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 1, 0>);
+  } else {
+    if (p.tab == 1)
+      kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 0, 1>)
+                         : reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 1, 1>);
+    else
+      kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 0, 0>)
+                         : reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 1, 0>);
+  }
   // cell coordinates of the tensor copies are 32-bit signed rows
   if (p.ncells * 64 >= (1LL << 31)) return cudaErrorNotSupported;
   alignas(64) CUtensorMap tm;
+  alignas(64) FaceMaps fm;
   std::memset(&tm, 0, sizeof(tm));
+  std::memset(&fm, 0, sizeof(fm));
   cudaError_t e;
-  if constexpr (sizeof(TIN) == 4) {
+  if constexpr (kF32) {
     if ((e = encode_cell_map(&tm, p.src, p.ncells)) != cudaSuccess) return e;
+    if (face && (e = encode_face_maps(&fm, p.src, p.ncells)) != cudaSuccess) return e;
   }
   // 1 KB alignment slack, three cell buffers, the carried v3 traces (8 floats per thread)
   const size_t smem = 1024 + (static_cast<size_t>(kNumBuf) * kCellF + 128 * 8) * sizeof(float);
@@ -1262,7 +1411,21 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
   const long long grid = std::min<long long>(npencils, static_cast<long long>(sms) * per_sm);
   e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  kern<<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
+  if constexpr (kF32) {
+    if (face)
+      (p.mode == 0 ? k_cell6d4p_face<float, float, ADJ, 0> : k_cell6d4p_face<float, float, ADJ, 1>)
+          <<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm, fm);
+    else
+      (p.mode == 0 ? k_cell6d4p<TIN, TW, ADJ, 0, 0> : k_cell6d4p<TIN, TW, ADJ, 1, 0>)
+          <<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
+  } else {
+    if (p.tab == 1)
+      (p.mode == 0 ? k_cell6d4p<TIN, TW, ADJ, 0, 1> : k_cell6d4p<TIN, TW, ADJ, 1, 1>)
+          <<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
+    else
+      (p.mode == 0 ? k_cell6d4p<TIN, TW, ADJ, 0, 0> : k_cell6d4p<TIN, TW, ADJ, 1, 0>)
+          <<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
+  }
   return cudaGetLastError();
 }
 

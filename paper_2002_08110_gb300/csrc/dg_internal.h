@@ -178,6 +178,7 @@ struct dg_ctx {
   int device = 0;
   dg::HostTables tables;
   std::vector<double> cx_host, cv_host;   // contravariant speeds (FP64)
+  std::vector<float> cx32_host, cv32_host; // FP32 copies with side-consistent zeros
   double* cx_d64 = nullptr; float* cx_d32 = nullptr;
   double* cv_d64 = nullptr; float* cv_d32 = nullptr;
   int* err_d = nullptr;

@@ -256,18 +256,30 @@ __global__ void k_field_speeds(const double* __restrict__ e, int comps, double s
   if (i >= ncx * dv) return;
   const long long cx = i / dv;
   const int j = static_cast<int>(i - cx * dv);
-  bool pos = false, neg = false, bad = false;
+  // the cell's side is the sign of its largest speed; speeds of at most
+  // 1e-12 of it are stored in FP32 as a zero with that sign (as on the host)
+  double big = 0.0;
+  bool bad = false;
   for (int q = 0; q < nq; ++q) {
     const long long node = cx * nq + q;
-    const double a = j < comps ? scale * e[node * comps + j] : 0.0;
-    const double c = two_over_h.v[j] * a;
+    const double c = two_over_h.v[j] * (j < comps ? scale * e[node * comps + j] : 0.0);
     bad |= !isfinite(c);
-    pos |= c > 0.0;
-    neg |= c < 0.0;
-    cv64[node * dv + j] = c;
-    cv32[node * dv + j] = static_cast<float>(c);
+    if (fabs(c) > fabs(big)) big = c;
   }
-  if (pos && neg) atomicOr(flags, 1);
+  const double thr = 1e-12 * fabs(big);
+  bool mixed = false;
+  for (int q = 0; q < nq; ++q) {
+    const long long node = cx * nq + q;
+    const double c = two_over_h.v[j] * (j < comps ? scale * e[node * comps + j] : 0.0);
+    cv64[node * dv + j] = c;
+    if (fabs(c) <= thr) {
+      cv32[node * dv + j] = big < 0.0 ? -0.0f : 0.0f;
+    } else {
+      cv32[node * dv + j] = static_cast<float>(c);
+      mixed |= (c > 0.0) != (big > 0.0);
+    }
+  }
+  if (mixed) atomicOr(flags, 1);
   if (bad) atomicOr(err, 1);
 }
 

@@ -113,6 +113,28 @@ def test_gll_collocation_6d_kernels(prec):
     dg.close()
 
 
+def test_gll_collocation_6d_adjoint():
+    """The transposed operator of the 6D kernels in the Lobatto collocation
+    (face-layer loads for the v neighbours) agrees with the generic kernel."""
+    dg, p = _pair(1, 3, 3, 3, (2, 1, 2, 3, 2, 2), "const", seed=11)
+    assert dg.info.uniform_sides == 1
+    y = torch.tensor(np.random.default_rng(9).standard_normal(p.n_dofs), device="cuda",
+                     dtype=torch.float32)
+    outs = []
+    for variant in (0, 2):
+        dg.set_launch(1, threads=256, cells_per_block=1, variant=variant)
+        outs.append(dg.apply_adjoint(y, prec=1).double().cpu().numpy())
+    dg.check()
+    # term scale of L^T = M L(-a) M^{-1}: M |L(-a)| M^{-1} |y|
+    Md = p.mass_diagonal()
+    yy = np.abs(y.double().cpu().numpy())
+    scale = Md * p.with_field(p.field.negated()).apply_abs(yy / Md)
+    ref = Md * p.with_field(p.field.negated()).apply(y.double().cpu().numpy() / Md)
+    for o in outs:
+        assert np.linalg.norm(o - ref) <= TOL32 * np.linalg.norm(scale)
+    dg.close()
+
+
 def test_gll_collocation_rk_steps():
     dg, p = _pair(1, 2, 2, 2, (3, 2, 2, 3), "phase", seed=2)
     u0 = np.random.default_rng(1).standard_normal(p.n_dofs)
@@ -201,4 +223,30 @@ def test_gll_collocation_vlasov_poisson_pieces():
     e = dg.poisson_periodic_1d(torch.tensor(ref, device="cuda"))
     _, eref = ovp.poisson_periodic_1d(p, ref.reshape(6, 4))
     assert np.max(np.abs(e.cpu().numpy() - eref.reshape(-1))) <= 1e-13 * (np.max(np.abs(eref)) + 1)
+    dg.close()
+
+
+def test_gll_6d_workload_keeps_the_specialised_kernel():
+    """The 6D workload in the Lobatto collocation has field zeros on face
+    nodes (v = 0, and E = 0.05 sin 2 pi x at x = 1/2 up to rounding, a tiny
+    speed of either sign).  Such speeds carry no flux at FP32 precision; they
+    take the cell's side, the specialised kernel still runs, and the result
+    matches the oracle."""
+    import workloads as W
+    from paper_2002_08110_gb300 import DG, basis_nodes
+    w = W.shrink(W.config_6d(), cells_x=(2, 2, 2), cells_v=(2, 2, 2))
+    nodes, qpts, _ = basis_nodes(1, w.k)
+    dg = DG(e_nodes=W.e_table(w, qpts), basis=1, **W.dg_kwargs(w))
+    assert dg.info.uniform_sides == 1
+    p = Problem(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
+                PhaseSpaceField(w.dx, w.dv, W.e_function(w)), basis="gllc")
+    u = W.separable_state(w, nodes, xp=torch, device="cuda").float()
+    uin = u.double().cpu().numpy()
+    ref = p.apply(uin)
+    scale = np.linalg.norm(p.apply_abs(uin))
+    for variant in (0, 2):
+        dg.set_launch(1, threads=256, cells_per_block=1, variant=variant)
+        out = dg.apply(u, prec=1).double().cpu().numpy()
+        assert np.linalg.norm(out - ref) <= TOL32 * scale, variant
+    dg.check()
     dg.close()
