@@ -316,6 +316,17 @@ def measure_configs(torch, hbm_peak):
     u32 = u0.clone()
     ms32 = _timed(torch, lambda: dg.rk_step(u32, dt, nsteps=nacc, prec=PREC_FP32), 1)
     dg.check()
+    # delta-f form around the Maxwellian equilibrium: FP32 sweeps on u - u_eq
+    u_eq = W.separable_state(W.equilibrium_6d(w), zeta, xp=torch, device="cuda")
+    dg.set_reference(u_eq)
+    kdf = dg.apply_df(u0)
+    rel_apply_df = float(torch.linalg.vector_norm(kdf - k64) / torch.linalg.vector_norm(k64))
+    del kdf, u_eq
+    udf = u0.clone()
+    dg.rk_step_df(udf, dt, nsteps=1)
+    udf.copy_(u0)
+    msdf = _timed(torch, lambda: dg.rk_step_df(udf, dt, nsteps=nacc), 1)
+    dg.check()
     m0 = dg.integrals(u0)[0]
     out["6d_fp32_vs_fp64"] = {
         "workload": w.name, "steps": nacc,
@@ -325,11 +336,15 @@ def measure_configs(torch, hbm_peak):
         "mass_drift_fp64": (dg.integrals(u64)[0] - m0) / m0,
         "mass_drift_fp32_fp64state": (dg.integrals(u32)[0] - m0) / m0,
         "ms_per_step_fp64": ms64 / nacc, "ms_per_step_fp32_fp64state": ms32 / nacc,
+        "apply_rel_l2_diff_deltaf": rel_apply_df,
+        "state_rel_l2_diff_after_steps_deltaf": float(torch.linalg.vector_norm(udf - u64) /
+                                                      torch.linalg.vector_norm(u64)),
+        "ms_per_step_deltaf": msdf / nacc,
         "note": "K of the FP64 path matches the FP64 oracle to 1e-12 (tests); the plain relative "
                 "difference of K is large for smooth data (K << its terms); see tests for the "
                 "term-scale error"}
     dg.close()
-    del u0, u64, u32, k64
+    del u0, u64, u32, k64, udf
     torch.cuda.empty_cache()
 
     # 6D in the Gauss-Lobatto bases: the collocation variant (FP32 stage; its

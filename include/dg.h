@@ -272,6 +272,32 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
                      int prec, int adjoint, void* stream);
 
 /*
+ * delta-f form (FP32 sweeps with an FP64 reference).  With smooth data the
+ * result of the operator is much smaller than its terms, so FP32 sweeps lose
+ * relative accuracy; splitting u = u_ref + du and using linearity,
+ * L(u) = L(u_ref) + L(du), with L(u_ref) evaluated once in FP64, leaves FP32
+ * rounding only on the small part du.
+ *
+ * dg_set_reference: copies the FP64 device vector u_ref into the handle and
+ * evaluates K_ref = L(u_ref) in FP64 (kept in FP64 and FP32); the handle then
+ * holds 20 bytes per DoF until dg_destroy.  UNSUPPORTED for
+ * DG_BASIS_GLL_GAUSS.  Stream-ordered.
+ *
+ * dg_apply_df: dst = K_ref + L(f32(src - u_ref)) with FP32 sweeps; src and
+ * dst are FP64 device vectors.
+ *
+ * dg_rk_step_df: nsteps LSRK(5,4) steps on the FP64 state u (in place) in
+ * the form du = u - u_ref, K = K_ref + L(dw): FP32 stage vectors w0, w1 hold
+ * dw; u is turned into du before the steps and back after them (two FP64
+ * passes; the round trip rounds u at the level of its own ulp).  Graph-
+ * replayed like dg_rk_step.
+ */
+dg_status dg_set_reference(dg_handle h, const double* u_ref, void* stream);
+dg_status dg_apply_df(dg_handle h, const double* src, double* dst, void* stream);
+dg_status dg_rk_step_df(dg_handle h, double* u, float* w0, float* w1, double dt, int nsteps,
+                        void* stream);
+
+/*
  * Integrals of the FP64 vector u with the cell quadrature: out[0] = int u,
  * out[1] = int u^2, out[2] = max |u_i| over the nodes.  Synchronises
  * ``stream``; out is a host array of 3 doubles.

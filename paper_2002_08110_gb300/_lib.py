@@ -81,6 +81,9 @@ def load():
         "dg_integrals_noalloc": (i, [vp, ll, i, i, d, c_double_p, vp]),
         "dg_check": (i, [vp, vp]),
         "dg_basis_nodes": (i, [i, i, vp, vp, vp]),
+        "dg_set_reference": (i, [vp, vp, vp]),
+        "dg_apply_df": (i, [vp, vp, vp, vp]),
+        "dg_rk_step_df": (i, [vp, vp, vp, vp, ctypes.c_double, i, vp]),
         "dg_charge_density": (i, [vp, vp, i, vp, vp]),
         "dg_poisson_periodic_1d": (i, [vp, vp, vp, vp]),
         "dg_set_field_device": (i, [vp, vp, i, ctypes.c_double, vp]),

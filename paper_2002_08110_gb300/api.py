@@ -151,6 +151,30 @@ class DG:
                                    self._vec(u, PREC_FP64, "u"), int(stage), float(dt), prec,
                                    int(bool(adjoint)), _stream()))
 
+    # -- delta-f form -----------------------------------------------------------
+    def set_reference(self, u_ref):
+        """Keep u_ref and K_ref = L(u_ref) (FP64) for the delta-f calls."""
+        check(self.lib.dg_set_reference(self.handle, self._vec(u_ref, PREC_FP64, "u_ref"), _stream()))
+
+    def apply_df(self, src, dst=None):
+        """dst = L(u_ref) + L(src - u_ref) with FP32 sweeps (FP64 vectors)."""
+        if dst is None:
+            dst = torch.empty_like(src)
+        check(self.lib.dg_apply_df(self.handle, self._vec(src, PREC_FP64, "src"),
+                                   self._vec(dst, PREC_FP64, "dst"), _stream()))
+        return dst
+
+    def rk_step_df(self, u, dt, nsteps=1, w0=None, w1=None):
+        """LSRK(5,4) steps in the delta-f form (FP32 stage vectors)."""
+        if w0 is None:
+            w0 = self.empty(PREC_FP32, u.device)
+        if w1 is None:
+            w1 = self.empty(PREC_FP32, u.device)
+        check(self.lib.dg_rk_step_df(self.handle, self._vec(u, PREC_FP64, "u"),
+                                     self._vec(w0, PREC_FP32, "w0"), self._vec(w1, PREC_FP32, "w1"),
+                                     float(dt), int(nsteps), _stream()))
+        return u
+
     def rk_stage_host(self, w_in, w_out, u, stage, dt, prec=PREC_FP32):
         """One fused stage on host (CPU, preferably pinned) tensors; the library
         stages them through device memory it owns."""

@@ -121,6 +121,7 @@ KParams base_params(const dg_ctx* h, int prec) {
   p.t64 = h->tables.t64;
   p.t32 = h->tables.t32;
   p.tab = h->basis == DG_BASIS_GLL ? 1 : 0;
+  p.kref = h->kref_active;
   return p;
 }
 
@@ -299,6 +300,10 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->vp_e);
   cudaFree(h->host_stage);
   for (int i = 0; i < 4; ++i) cudaFree(h->bc_tmp[i]);
+  cudaFree(h->df_u);
+  cudaFree(h->df_k64);
+  cudaFree(h->df_k32);
+  cudaFree(h->df_tmp);
   delete h;
 }
 
@@ -928,6 +933,7 @@ dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, in
     key.prec = prec;
     key.adjoint = adjoint;
     key.parity = parity;
+    key.kref = h->kref_active;
     if (h->gexec[parity] && h->gkey[parity] == key) continue;
     if (h->gexec[parity]) {
       cudaGraphExecDestroy(h->gexec[parity]);
@@ -1135,3 +1141,81 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// delta-f form: K = L(u_ref) + L(u - u_ref)
+// ---------------------------------------------------------------------------
+dg_status dg_set_reference(dg_handle h, const double* u_ref, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->basis == DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_UNSUPPORTED, "the delta-f form needs a collocated basis");
+  dg_status st;
+  if ((st = check_vec(u_ref, "u_ref")) != DG_OK) return st;
+  const size_t n = static_cast<size_t>(h->n_dofs);
+  cudaError_t e;
+  if (h->df_u == nullptr &&
+      ((e = cudaMalloc(&h->df_u, n * sizeof(double))) != cudaSuccess ||
+       (e = cudaMalloc(&h->df_k64, n * sizeof(double))) != cudaSuccess ||
+       (e = cudaMalloc(&h->df_k32, n * sizeof(float))) != cudaSuccess ||
+       (e = cudaMalloc(&h->df_tmp, (n + 64) * sizeof(double))) != cudaSuccess))
+    return cuda_fail(e, "delta-f storage");
+  if (ranges_overlap(u_ref, n * 8, h->df_u, n * 8))
+    return fail(DG_ERR_INVALID_ARG, "u_ref overlaps the handle's storage");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(h->df_u, u_ref, n * sizeof(double), cudaMemcpyDeviceToDevice, s)) !=
+      cudaSuccess)
+    return cuda_fail(e, "reference copy");
+  if ((st = apply_core(h, h->df_u, h->df_k64, DG_PREC_FP64, s, 0)) != DG_OK) return st;
+  if ((e = launch_convert(h->df_k64, h->df_k32, 1, h->n_dofs, s)) != cudaSuccess)
+    return cuda_fail(e, "reference operator conversion");
+  h->df_ready = true;
+  return DG_OK;
+}
+
+dg_status dg_apply_df(dg_handle h, const double* src, double* dst, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->df_ready) return fail(DG_ERR_INVALID_ARG, "no reference state (dg_set_reference)");
+  dg_status st;
+  if ((st = check_vec(src, "src")) != DG_OK || (st = check_vec(dst, "dst")) != DG_OK) return st;
+  const size_t n = static_cast<size_t>(h->n_dofs);
+  if (ranges_overlap(src, dst, n * 8)) return fail(DG_ERR_INVALID_ARG, "src and dst overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* t1 = reinterpret_cast<float*>(h->df_tmp);
+  float* t2 = t1 + ((n + 63) / 64) * 64;          // two FP32 vectors in the FP64 scratch
+  cudaError_t e;
+  if ((e = launch_sub_to_f32(src, h->df_u, t1, h->n_dofs, s)) != cudaSuccess)
+    return cuda_fail(e, "delta-f input");
+  if ((st = apply_core(h, t1, t2, DG_PREC_FP32, s, 0)) != DG_OK) return st;
+  if ((e = launch_add_f32(h->df_k64, t2, dst, h->n_dofs, s)) != cudaSuccess)
+    return cuda_fail(e, "delta-f output");
+  return DG_OK;
+}
+
+dg_status dg_rk_step_df(dg_handle h, double* u, float* w0, float* w1, double dt, int nsteps,
+                        void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->df_ready) return fail(DG_ERR_INVALID_ARG, "no reference state (dg_set_reference)");
+  if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  dg_status st;
+  if ((st = check_vec(u, "u")) != DG_OK || (st = check_vec(w0, "w0")) != DG_OK ||
+      (st = check_vec(w1, "w1")) != DG_OK)
+    return st;
+  const size_t wb = static_cast<size_t>(h->n_dofs) * 4, ub = static_cast<size_t>(h->n_dofs) * 8;
+  if (ranges_overlap(w0, w1, wb) || ranges_overlap(w0, wb, u, ub) || ranges_overlap(w1, wb, u, ub))
+    return fail(DG_ERR_INVALID_ARG, "u, w0 and w1 must not overlap");
+  if (nsteps == 0) return DG_OK;
+  if ((st = ensure_scratch(h, DG_PREC_FP32)) != DG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // the steps advance du = u - u_ref with K = K_ref + L(dw)
+  if ((e = launch_axpy(u, -1.0, h->df_u, h->n_dofs, s)) != cudaSuccess)
+    return cuda_fail(e, "delta-f state");
+  h->kref_active = h->df_k32;
+  st = rk_step_core(h, u, w0, w1, dt, nsteps, DG_PREC_FP32, 0, s);
+  h->kref_active = nullptr;
+  if (st != DG_OK) return st;
+  if ((e = launch_axpy(u, 1.0, h->df_u, h->n_dofs, s)) != cudaSuccess)
+    return cuda_fail(e, "delta-f state");
+  return DG_OK;
+}

@@ -1108,7 +1108,8 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     }
     // the cell's FP64 state is needed only in the epilogue: ask L2 for it now
     // (one 512-byte row per issuing thread)
-    if (MODE == 1 && issuer) prefetch_l2_once(p.u + static_cast<size_t>(cell) * 4096 + t * 64, 512);
+    if (MODE >= 1 && issuer) prefetch_l2_once(p.u + static_cast<size_t>(cell) * 4096 + t * 64, 512);
+    if (MODE == 2 && issuer) prefetch_l2_once(p.kref + static_cast<size_t>(cell) * 4096 + t * 64, 256);
     float u[32], r[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) r[e] = 0.f;
@@ -1232,8 +1233,12 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
       // loads issued while the previous one is used
       double* uu = p.u;
       double ua[8];
+      float ka[8];   // MODE 2 (delta-f form): the reference operator K_ref
 #pragma unroll
-      for (int k = 0; k < 8; ++k) ua[k] = __ldcs(uu + g0 + 64 * poff(k));
+      for (int k = 0; k < 8; ++k) {
+        ua[k] = __ldcs(uu + g0 + 64 * poff(k));
+        ka[k] = MODE == 2 ? __ldcs(p.kref + g0 + 64 * poff(k)) : 0.f;
+      }
       lines_p<2>(r, u, tr, sp[5], tb, 1.f, h);
       TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
@@ -1242,15 +1247,20 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) {
         double ub[8];
+        float kb[8];
         if (ch < 3) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) ub[k] = __ldcs(uu + g0 + 64 * poff(8 * (ch + 1) + k));
+          for (int k = 0; k < 8; ++k) {
+            ub[k] = __ldcs(uu + g0 + 64 * poff(8 * (ch + 1) + k));
+            kb[k] = MODE == 2 ? __ldcs(p.kref + g0 + 64 * poff(8 * (ch + 1) + k)) : 0.f;
+          }
         }
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const int k = 8 * ch + kk;
           float K = r[k];
           if (ADJ) K *= w_t * wprod_p(T.w, k, h);
+          if (MODE == 2) K += ka[kk];
           nanacc = fmaf(K, 0.f, nanacc);   // stays 0 unless K is Inf or NaN
           const size_t g = g0 + 64 * poff(k);
           const double un = ua[kk] + f32_to_f64_finite(bf * K);
@@ -1263,7 +1273,10 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
         }
         if (ch < 3) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) ua[k] = ub[k];
+          for (int k = 0; k < 8; ++k) {
+            ua[k] = ub[k];
+            ka[k] = kb[k];
+          }
         }
       }
       bad |= nanacc != 0.f;
@@ -1368,16 +1381,22 @@ template <typename TIN, typename TW, bool ADJ>
 cudaError_t launch6p(KParams& p, cudaStream_t s) {
   constexpr bool kF32 = sizeof(TIN) == 4;
   const bool face = kF32 && p.tab == 1;
+  // delta-f stages: only the Gauss-Legendre FP32 kernel (else the generic one)
+  if (p.kref && (!kF32 || face || p.tab != 0 || ADJ || p.mode != 1)) return cudaErrorNotSupported;
+  const bool df = p.kref != nullptr;
   // kernels: Gauss-Legendre tables; Gauss-Lobatto with FP32 input (face
   // layers); Gauss-Lobatto with FP64 input (full cells)
-  const void* kern;
+  const void* kern = nullptr;
   if constexpr (kF32) {
-    if (face)
+    if (df) {
+      if constexpr (!ADJ) kern = reinterpret_cast<const void*>(k_cell6d4p<float, float, false, 2, 0>);
+    } else if (face) {
       kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p_face<float, float, ADJ, 0>)
                          : reinterpret_cast<const void*>(k_cell6d4p_face<float, float, ADJ, 1>);
-    else
+    } else {
       kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 0, 0>)
                          : reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 1, 0>);
+    }
   } else {
     if (p.tab == 1)
       kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 0, 1>)
@@ -1386,6 +1405,7 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
       kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 0, 0>)
                          : reinterpret_cast<const void*>(k_cell6d4p<TIN, TW, ADJ, 1, 0>);
   }
+  if (kern == nullptr) return cudaErrorNotSupported;
   // cell coordinates of the tensor copies are 32-bit signed rows
   if (p.ncells * 64 >= (1LL << 31)) return cudaErrorNotSupported;
   alignas(64) CUtensorMap tm;
@@ -1411,6 +1431,12 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
   const long long grid = std::min<long long>(npencils, static_cast<long long>(sms) * per_sm);
   e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
+  if constexpr (kF32 && !ADJ) {
+    if (df) {
+      k_cell6d4p<float, float, false, 2, 0><<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (kF32) {
     if (face)
       (p.mode == 0 ? k_cell6d4p_face<float, float, ADJ, 0> : k_cell6d4p_face<float, float, ADJ, 1>)
@@ -1452,6 +1478,7 @@ cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab) {
 
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
   if (p.dx != 3 || p.dv != 3 || p.ncells >= (1LL << 31)) return cudaErrorNotSupported;
+  if (p.kref && cfg.variant != 2) return cudaErrorNotSupported;   // delta-f: pair kernel or generic
   if (cfg.variant == 2) {
     if (combo == kFFF)
       return p.adjoint ? launch6p<float, float, true>(p, s) : launch6p<float, float, false>(p, s);

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
       if (p.mode == 0) {
         static_cast<TW*>(p.dst)[g] = cvt<TW>(K);
       } else {
+        if (p.kref) K += static_cast<TC>(p.kref[g]);    // delta-f form
         const double uo = p.u[g];
         if constexpr (sizeof(TC) == 8) {
           const double un = uo + p.b_dt * K;

@@ -82,6 +82,7 @@ struct KParams {
   int last_stage;           // stage mode: w_out = u_new
   double a_dt, b_dt;        // stage mode coefficients (a_s dt, b_s dt)
   int tab;                  // constant-table set of the 6D kernels (0 GL, 1 GLL)
+  const float* kref;        // stage mode, delta-f form: K = kref + L(w) (nullptr: plain)
   Tab1D<double> t64;
   Tab1D<float> t32;
 };
@@ -147,6 +148,11 @@ struct BasisMat {
 // only there; cudaErrorNotSupported otherwise).
 cudaError_t launch_basis_change(const void* x, int x_is_float, void* y, int y_is_float, double* tmp,
                                 long long ncells, int d, int n, const BasisMat& M, cudaStream_t s);
+// y = f32(a - b) (delta-f input), and z = k + f64(y) (delta-f output), and
+// x += s * r in FP64 (dg_misc.cu).
+cudaError_t launch_sub_to_f32(const double* a, const double* b, float* y, long long n, cudaStream_t s);
+cudaError_t launch_add_f32(const double* k, const float* y, double* z, long long n, cudaStream_t s);
+cudaError_t launch_axpy(double* x, double sc, const double* r, long long n, cudaStream_t s);
 cudaError_t launch_charge_density(const void* f, int f_is_float, long long ncx, long long ncv,
                                   int npc, int nqx, int nqv, int dv, int n,
                                   const Tab1D<double>& t, double detJv, double* rho,
@@ -184,6 +190,14 @@ struct dg_ctx {
   int* err_d = nullptr;
   unsigned* work_d = nullptr;   // work-queue counter
   int* field_flags_d = nullptr; // device-fed field: bit 0 mixed upwind side in a cell, bit 1 non-finite
+  // delta-f form: reference state, its operator in FP64 and FP32, and the
+  // K_ref the next enqueued stages add (set only inside dg_rk_step_df)
+  double* df_u = nullptr;
+  double* df_k64 = nullptr;
+  float* df_k32 = nullptr;
+  const float* kref_active = nullptr;
+  double* df_tmp = nullptr;     // two FP32 vectors for dg_apply_df
+  bool df_ready = false;
   double* vp_rho = nullptr;     // Vlasov-Poisson scratch: rho and E at the x nodes
   double* vp_e = nullptr;
   // device staging of the host-buffer stage call: u (FP64) and two stage vectors
@@ -196,9 +210,10 @@ struct dg_ctx {
   struct GraphKey {
     const void* u = nullptr; const void* w0 = nullptr; const void* w1 = nullptr;
     double dt = 0.0; int prec = -1; int adjoint = -1; int parity = -1;
+    const void* kref = nullptr;
     bool operator==(const GraphKey& o) const {
       return u == o.u && w0 == o.w0 && w1 == o.w1 && dt == o.dt && prec == o.prec &&
-             adjoint == o.adjoint && parity == o.parity;
+             adjoint == o.adjoint && parity == o.parity && kref == o.kref;
     }
   };
   GraphKey gkey[2];

@@ -397,3 +397,46 @@ cudaError_t launch_basis_change(const void* x, int x_is_float, void* y, int y_is
 }
 
 }  // namespace dg
+
+namespace dg {
+
+// Element-wise helpers of the delta-f form (grid-stride loops).
+__global__ void k_sub_to_f32(const double* __restrict__ a, const double* __restrict__ b,
+                             float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] = f64_to_f32(a[i] - b[i]);
+}
+__global__ void k_add_f32(const double* __restrict__ k, const float* __restrict__ y,
+                          double* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    z[i] = k[i] + f32_to_f64(y[i]);
+}
+__global__ void k_axpy(double* __restrict__ x, double sc, const double* __restrict__ r, long long n) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    x[i] += sc * r[i];
+}
+
+static unsigned ew_blocks(long long n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return static_cast<unsigned>(std::max<long long>(1, std::min<long long>((n + 255) / 256, 8LL * sms)));
+}
+
+cudaError_t launch_sub_to_f32(const double* a, const double* b, float* y, long long n, cudaStream_t s) {
+  k_sub_to_f32<<<ew_blocks(n), 256, 0, s>>>(a, b, y, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_f32(const double* k, const float* y, double* z, long long n, cudaStream_t s) {
+  k_add_f32<<<ew_blocks(n), 256, 0, s>>>(k, y, z, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy(double* x, double sc, const double* r, long long n, cudaStream_t s) {
+  k_axpy<<<ew_blocks(n), 256, 0, s>>>(x, sc, r, n);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

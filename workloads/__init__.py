@@ -245,6 +245,13 @@ def config_6d(cells=8, k=3):
         steps=50, cfl=0.2, amax=(6.0, 6.0, 6.0, 0.05, 0.05, 0.05))
 
 
+def equilibrium_6d(w: Workload):
+    """The 6D workload's spatially uniform Maxwellian (its state without the
+    1% density perturbation): the reference state of the delta-f form."""
+    one = lambda y: np.ones_like(y)
+    return Workload(**{**w.__dict__, "u0_factors": (one,) + tuple(w.u0_factors[1:])})
+
+
 def _E5(y1, y2):
     return [0.1 * np.sin(TWO_PI * y1), 0.1 * np.cos(TWO_PI * y2), 0.1 * np.sin(TWO_PI * (y1 + y2))]
 
