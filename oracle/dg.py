@@ -106,11 +106,17 @@ class Problem:
     cells_x/v : cells per direction
     x_lo/x_hi : lattice box of configuration space; v_lo/v_hi velocity box
     shear     : dx-by-dx matrix S of the affine map x = S y (None: identity)
+    deform    : per-direction amplitudes delta of a curved x-mesh (None: affine):
+                x_i = y_i + delta_i L_m / (2 pi) sin(2 pi (y_m - lo_m) / L_m),
+                m = (i + 1) mod dx, L the box size -- a periodic, non-affine
+                deformation of the lattice, so that every quadrature point has
+                its own Jacobian (Sec. 5.1 deforms the Cartesian mesh
+                slightly for this reason).  Not combined with a shear.
     field     : callable a(y_x, v) -> (..., d) physical velocity
     """
 
     def __init__(self, dx, dv, k, cells_x, cells_v, x_lo, x_hi, v_lo, v_hi,
-                 field, shear=None, basis="gl"):
+                 field, shear=None, basis="gl", deform=None):
         self.dx, self.dv, self.d = dx, dv, dx + dv
         self.k, self.n = k, k + 1
         self.cells = np.array(list(cells_x) + list(cells_v), dtype=np.int64)
@@ -130,6 +136,9 @@ class Problem:
         self.J = J
         self.detJ = float(np.linalg.det(J))
         self.Jinv = np.linalg.inv(J)
+        self.deform = None if deform is None else np.asarray(deform, dtype=np.float64)
+        if self.deform is not None:
+            assert shear is None and basis in ("gl", "gllc")   # diagonal mass only
         self.ncells = int(np.prod(self.cells))
         self.dofs_per_cell = self.n ** self.d
         self.n_dofs = self.ncells * self.dofs_per_cell
@@ -174,11 +183,51 @@ class Problem:
     def node_coordinates(self, cell):
         return self.coordinates(cell, [self.T.nodes] * self.d)
 
+    def physical_x(self, yx):
+        """x = Phi(y) of the curved mesh (the identity map S y otherwise)."""
+        if self.deform is None:
+            return yx @ self.S.T
+        L = self.hi[:self.dx] - self.lo[:self.dx]
+        x = np.array(yx, dtype=np.float64, copy=True)
+        for i in range(self.dx):
+            m = (i + 1) % self.dx
+            x[..., i] += self.deform[i] * L[m] / (2 * np.pi) * np.sin(
+                2 * np.pi * (yx[..., m] - self.lo[m]) / L[m])
+        return x
+
+    def jacobian(self, cell, points):
+        """(J, |J|) at the given reference points: J has shape (..., d, d).
+        For the curved mesh J_x = (dPhi/dy) diag(h_x / 2) at every point."""
+        yx, v = self.coordinates(cell, points)
+        shape = yx.shape[:-1]
+        if self.deform is None:
+            J = np.broadcast_to(self.J, shape + (self.d, self.d))
+            return J, np.full(shape, self.detJ)
+        dx = self.dx
+        L = self.hi[:dx] - self.lo[:dx]
+        DPhi = np.broadcast_to(np.eye(dx), shape + (dx, dx)).copy()
+        for i in range(dx):
+            m = (i + 1) % dx
+            DPhi[..., i, m] += self.deform[i] * np.cos(2 * np.pi * (yx[..., m] - self.lo[m]) / L[m])
+        J = np.zeros(shape + (self.d, self.d))
+        J[..., :dx, :dx] = DPhi * (self.h[:dx] / 2)
+        J[..., dx:, dx:] = np.diag(self.h[dx:] / 2)
+        return J, np.linalg.det(J)
+
     def contravariant_speed(self, cell, points):
         """c = J^{-1} a at the given reference points, shape (..., d)."""
         yx, v = self.coordinates(cell, points)
         a = self.field(yx, v)
-        return a @ self.Jinv.T
+        if self.deform is None:
+            return a @ self.Jinv.T
+        J, _ = self.jacobian(cell, points)
+        return np.linalg.solve(J, a[..., None])[..., 0]
+
+    def _detJ(self, cell, points):
+        """|J| at the points (a scalar for the affine mesh)."""
+        if self.deform is None:
+            return self.detJ
+        return self.jacobian(cell, points)[1]
 
     def interpolate(self, f, cell_list=None):
         """Nodal interpolation of f(y_x, v) (the initial state)."""
@@ -217,9 +266,10 @@ class Problem:
             Uq = _axis_apply(T.B, Uq, m)
         C = self.contravariant_speed(cell, [T.zeta] * d)
         W = _outer_weights([T.w] * d)
+        dJ = self._detJ(cell, [T.zeta] * d)
         b = np.zeros_like(Ue)
         for j in range(d):
-            F = W * self.detJ * C[..., j] * Uq
+            F = W * dJ * C[..., j] * Uq
             G = F
             for m in range(d):
                 G = _axis_apply((T.Bd if m == j else T.B).T, G, m)
@@ -236,7 +286,7 @@ class Problem:
                 ustar = np.where(s * cj > 0, own, nb)
                 wf = [T.w] * d
                 wf[j] = np.array([1.0])
-                flux = _outer_weights(wf) * self.detJ * cj * ustar
+                flux = _outer_weights(wf) * self._detJ(cell, pts) * cj * ustar
                 G = flux
                 for m in range(d):
                     if m != j:
@@ -254,9 +304,10 @@ class Problem:
             Uq = _axis_apply(aB, Uq, m)
         C = np.abs(self.contravariant_speed(cell, [T.zeta] * d))
         W = _outer_weights([T.w] * d)
+        dJ = self._detJ(cell, [T.zeta] * d)
         b = np.zeros_like(Ue)
         for j in range(d):
-            G = W * self.detJ * C[..., j] * Uq
+            G = W * dJ * C[..., j] * Uq
             for m in range(d):
                 G = _axis_apply((aBd if m == j else aB).T, G, m)
             b += G
@@ -272,7 +323,7 @@ class Problem:
                 ustar = np.where(s * cj > 0, own, nb)
                 wf = [T.w] * d
                 wf[j] = np.array([1.0])
-                G = _outer_weights(wf) * self.detJ * np.abs(cj) * ustar
+                G = _outer_weights(wf) * self._detJ(cell, pts) * np.abs(cj) * ustar
                 for m in range(d):
                     if m != j:
                         G = _axis_apply(aB.T, G, m)
@@ -292,7 +343,7 @@ class Problem:
         assert self.basis in ("gl", "gllc")   # collocation: diagonal mass
         u = np.asarray(u, dtype=np.float64)
         sel = range(self.ncells) if cells is None else cells
-        out = [self.apply_mass_inverse(self._cell_residual_abs(u, e)).reshape(-1, order="F")
+        out = [self.apply_mass_inverse(self._cell_residual_abs(u, e), e).reshape(-1, order="F")
                for e in sel]
         return np.concatenate(out) if cells is None else np.stack(out)
 
@@ -300,14 +351,22 @@ class Problem:
         T = self.T
         return T.B.T @ np.diag(T.w) @ T.B
 
-    def apply_mass_inverse(self, b):
+    def apply_mass_inverse(self, b, cell=None):
+        """M^{-1} b on one cell (``cell`` is needed on the curved mesh, where
+        the collocation mass is diag(W |J(q)|))."""
+        if self.deform is not None:
+            W = _outer_weights([self.T.w] * self.d)
+            return b / (W * self._detJ(cell, [self.T.zeta] * self.d))
         M1 = self.mass_1d()
         y = b / self.detJ
         for m in range(self.d):
             y = _axis_apply(np.linalg.inv(M1), y, m)
         return y
 
-    def apply_mass(self, y):
+    def apply_mass(self, y, cell=None):
+        if self.deform is not None:
+            W = _outer_weights([self.T.w] * self.d)
+            return y * W * self._detJ(cell, [self.T.zeta] * self.d)
         M1 = self.mass_1d()
         b = y * self.detJ
         for m in range(self.d):
@@ -320,7 +379,7 @@ class Problem:
         u = np.asarray(u, dtype=np.float64)
         assert u.shape == (self.n_dofs,)
         sel = range(self.ncells) if cells is None else cells
-        out = [self.apply_mass_inverse(self.cell_residual(u, e)).reshape(-1, order="F")
+        out = [self.apply_mass_inverse(self.cell_residual(u, e), e).reshape(-1, order="F")
                for e in sel]
         return np.concatenate(out) if cells is None else np.stack(out)
 
@@ -356,11 +415,12 @@ class Problem:
         W = _outer_weights([T.w] * d).reshape(-1, order="F")
         C = self.contravariant_speed(cell, [T.zeta] * d)
         Cf = C.reshape(-1, d, order="F")
+        dJ = np.broadcast_to(self._detJ(cell, [T.zeta] * d), [n] * d).reshape(-1, order="F")
         A_own = np.zeros((n ** d, n ** d))
         blocks = {}
         for j in range(d):
             KBd = _kron_list([T.Bd if m == j else T.B for m in range(d)])
-            A_own += KBd.T @ np.diag(W * self.detJ * Cf[:, j]) @ KB
+            A_own += KBd.T @ np.diag(W * dJ * Cf[:, j]) @ KB
         for j in range(d):
             for s in (1, -1):
                 ls, lo = (T.lp, T.lm) if s > 0 else (T.lm, T.lp)
@@ -373,12 +433,14 @@ class Problem:
                 wf[j] = np.array([1.0])
                 Wf = _outer_weights(wf).reshape(-1, order="F")
                 out = (s * cj > 0).astype(np.float64)
-                A_own += -s * Ts.T @ np.diag(Wf * self.detJ * cj * out) @ Ts
+                dJf = self._detJ(cell, pts)
+                dJf = np.asarray(dJf).reshape(-1, order="F") if np.ndim(dJf) else dJf
+                A_own += -s * Ts.T @ np.diag(Wf * dJf * cj * out) @ Ts
                 nbc = self.neighbour(cell, j, s)
-                blk = -s * Ts.T @ np.diag(Wf * self.detJ * cj * (1.0 - out)) @ Tn
+                blk = -s * Ts.T @ np.diag(Wf * dJf * cj * (1.0 - out)) @ Tn
                 blocks[nbc] = blocks.get(nbc, 0.0) + blk
         blocks[cell] = blocks.get(cell, 0.0) + A_own
-        M = KB.T @ np.diag(W * self.detJ) @ KB
+        M = KB.T @ np.diag(W * dJ) @ KB
         Minv = np.linalg.inv(M)
         return {c: Minv @ B for c, B in blocks.items()}
 
@@ -410,7 +472,11 @@ class Problem:
         """Diagonal of M for the collocation basis (|J| times the weights)."""
         assert self.basis in ("gl", "gllc")   # collocation: diagonal mass
         W = _outer_weights([self.T.w] * self.d).reshape(-1, order="F")
-        return np.tile(W * self.detJ, self.ncells)
+        if self.deform is None:
+            return np.tile(W * self.detJ, self.ncells)
+        pts = [self.T.zeta] * self.d
+        return np.concatenate([W * np.asarray(self._detJ(e, pts)).reshape(-1, order="F")
+                               for e in range(self.ncells)])
 
     # -- Vlasov-Poisson coupling (Sec. 6) -------------------------------------
     def charge_density(self, u, x_cells=None):
@@ -445,8 +511,9 @@ class Problem:
             Uq = self.cell_tensor(u, e)
             for m in range(self.d):
                 Uq = _axis_apply(T.B, Uq, m)
-            mass += self.detJ * float(np.sum(W * Uq))
-            l2 += self.detJ * float(np.sum(W * Uq * Uq))
+            dJ = self._detJ(e, [T.zeta] * self.d)
+            mass += float(np.sum(W * dJ * Uq))
+            l2 += float(np.sum(W * dJ * Uq * Uq))
         return mass, l2, float(np.max(np.abs(u)))
 
 

@@ -605,3 +605,83 @@ def test_gllc_convergence_order(k):
         errs.append(math.sqrt(diff @ (p.mass_diagonal() * diff)))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert rates[-1] > k + 1 - 0.3, rates
+
+
+# ---------------------------------------------------------------------------
+# curved (non-affine) x-mesh: a Jacobian per quadrature point (Sec. 5.1)
+# ---------------------------------------------------------------------------
+def test_curved_zero_deformation_is_the_affine_operator():
+    f = ConstantField([0.7, -0.4, 0.3, 0.5])
+    pa = Problem(2, 2, 2, [2, 3], [2, 2], [0, 0], [1, 1], [-1, -1], [1, 1], f)
+    pc = Problem(2, 2, 2, [2, 3], [2, 2], [0, 0], [1, 1], [-1, -1], [1, 1], f, deform=[0.0, 0.0])
+    u = np.random.default_rng(0).standard_normal(pa.n_dofs)
+    np.testing.assert_allclose(pc.apply(u), pa.apply(u), rtol=0, atol=1e-13 * np.abs(pa.apply(u)).max())
+
+
+@pytest.mark.parametrize("dx,dv", [(1, 1), (2, 1), (1, 2)])
+def test_curved_conserves_mass(dx, dv):
+    """The face geometry is evaluated at the same physical point from both
+    sides, so the upwind flux is single-valued and mass is conserved exactly."""
+    rng = np.random.default_rng(dx + 2 * dv)
+    a = rng.uniform(-1, 1, dx + dv)
+    p = Problem(dx, dv, 2, [3] * dx, [2] * dv, [0] * dx, [1] * dx, [-1] * dv, [1] * dv,
+                ConstantField(a), deform=rng.uniform(-0.3, 0.3, dx))
+    u = rng.standard_normal(p.n_dofs)
+    Md = p.mass_diagonal()
+    Lu = p.apply(u)
+    assert abs(Md @ Lu) <= 1e-13 * (np.abs(Md) @ np.abs(Lu))
+
+
+def test_curved_translation_order():
+    """A product of sines in PHYSICAL coordinates translated by a constant
+    velocity on a strongly deformed 1x1v mesh (delta = 0.3): the L2 error at
+    T = 1/4 against the exact translate falls at order k+1."""
+    a = np.array([1.0, 0.5])
+    k = 2
+
+    def f(x, v):
+        return np.sin(2 * np.pi * x) * np.sin(2 * np.pi * v)
+
+    errs = []
+    for N in (4, 8, 16):
+        p = Problem(1, 1, k, [N], [N], [0.0], [1.0], [0.0], [1.0], ConstantField(a), deform=[0.3])
+        X = lambda yx: p.physical_x(yx)[..., 0]
+        u = p.interpolate(lambda yx, v: f(X(yx), v[..., 0]))
+        T = 0.25
+        steps = int(math.ceil(T / (0.2 * 1.0 / (a[0] * N * 1.5 + a[1] * N))))
+        dt = T / steps
+        L = p.assemble()
+        for _ in range(steps):
+            u = lsrk.step(lambda x: L @ x, u, dt)
+        ex = p.interpolate(lambda yx, v: f(X(yx) - a[0] * T, v[..., 0] - a[1] * T))
+        diff = u - ex
+        errs.append(math.sqrt(diff @ (p.mass_diagonal() * diff)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > k + 1 - 0.3, rates
+
+
+def test_curved_consistency_two_x_directions():
+    """L u against -a . grad u (physical gradient) for a smooth u on a 2x1v
+    mesh whose x directions are coupled by the deformation (off-diagonal,
+    point-dependent J_x): the error falls at order >= k - 1/2."""
+    a = np.array([0.7, -0.4, 0.3])
+    tp = 2 * np.pi
+    k = 2
+
+    def parts(x1, x2, v):
+        s1, c1, s2, c2, sv, cv = (np.sin(tp * x1), np.cos(tp * x1), np.sin(tp * x2),
+                                  np.cos(tp * x2), np.sin(tp * v), np.cos(tp * v))
+        return s1 * c2 * sv, -tp * (a[0] * c1 * c2 * sv - a[1] * s1 * s2 * sv + a[2] * s1 * c2 * cv)
+
+    errs = []
+    for N in (3, 6, 12):
+        p = Problem(2, 1, k, [N, N], [N], [0, 0], [1, 1], [0], [1], ConstantField(a),
+                    deform=[0.25, -0.2])
+
+        def ev(i):
+            return lambda yx, v: parts(*np.moveaxis(p.physical_x(yx), -1, 0), v[..., 0])[i]
+
+        diff = p.apply(p.interpolate(ev(0))) - p.interpolate(ev(1))
+        errs.append(math.sqrt(diff @ (p.mass_diagonal() * diff)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > k - 0.5, rates
