@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define DG_ABI_VERSION 2
+#define DG_ABI_VERSION 3
 
 typedef struct dg_ctx* dg_handle;
 typedef struct dg_batch_ctx* dg_batch;
@@ -115,6 +115,17 @@ typedef enum {
  *
  * basis: a dg_basis value (0, the Gauss-Legendre collocation, if the struct
  *   is zero-initialised).
+ *
+ * deform: amplitudes delta_i of a curved (non-affine) configuration mesh; all
+ *   zero (the default) keeps the affine map.  The map is
+ *     x_i = y_i + delta_i L_m / (2 pi) sin(2 pi (y_m - x_lo_m) / L_m),
+ *   m = (i + 1) mod dim_x, L = x_hi - x_lo: periodic, with a Jacobian of its
+ *   own at every quadrature point (Sec. 5.1 deforms the Cartesian mesh for
+ *   this reason).  |delta_i| < 0.5; not combined with shear_x; collocated
+ *   bases (DG_BASIS_GL, DG_BASIS_GLL) only.  Fields and initial data stay
+ *   functions of the lattice coordinates y.  The curved mesh runs in the
+ *   generic kernel; its transposed operator (dg_apply_adjoint, adjoint
+ *   steps) and the 1D Poisson solve are UNSUPPORTED.
  */
 typedef struct {
     double x_lo[3], x_hi[3];
@@ -124,6 +135,7 @@ typedef struct {
     double a_const[6];
     const double* e_nodes;
     int basis;
+    double deform[3];
 } dg_geometry;
 
 typedef struct {
@@ -200,7 +212,8 @@ dg_status dg_info(dg_handle h, dg_info_t* info);
  * n_vcells*(k+1)^dim_v rows of dim_v velocity coordinates.  Row order is
  * (cell, node), both lexicographic with the first direction fastest.
  * space 2 and 3: the same for the x and v quadrature points (equal to the
- * nodes except for DG_BASIS_GLL_GAUSS).
+ * nodes except for DG_BASIS_GLL_GAUSS).  space 4: physical coordinates x of
+ * the x nodes (x = S y, or the curved map of dg_geometry.deform).
  */
 dg_status dg_node_coordinates(dg_handle h, int space, double* out);
 

@@ -26,7 +26,7 @@ class Geometry(ctypes.Structure):
                 ("v_lo", ctypes.c_double * 3), ("v_hi", ctypes.c_double * 3),
                 ("shear_x", ctypes.c_double * 9), ("field_kind", ctypes.c_int),
                 ("a_const", ctypes.c_double * 6), ("e_nodes", c_double_p),
-                ("basis", ctypes.c_int)]
+                ("basis", ctypes.c_int), ("deform", ctypes.c_double * 3)]
 
 
 class Info(ctypes.Structure):

@@ -52,7 +52,8 @@ class DG:
     """
 
     def __init__(self, dim_x, dim_v, degree, cells_x, cells_v, x_lo, x_hi, v_lo, v_hi,
-                 field_kind=0, a_const=None, e_nodes=None, shear=None, basis=BASIS_GL):
+                 field_kind=0, a_const=None, e_nodes=None, shear=None, basis=BASIS_GL,
+                 deform=None):
         self.lib = _lib.load()
         self.dim_x, self.dim_v, self.degree = int(dim_x), int(dim_v), int(degree)
         g = _lib.Geometry()
@@ -67,6 +68,9 @@ class DG:
                     g.shear_x[i * self.dim_x + m] = S[i, m]
         g.field_kind = int(field_kind)
         g.basis = int(basis)
+        if deform is not None:
+            for j, dl in enumerate(deform):
+                g.deform[j] = float(dl)
         self.basis = int(basis)
         if a_const is not None:
             for j, a in enumerate(a_const):
@@ -102,8 +106,9 @@ class DG:
 
     # -- helpers -----------------------------------------------------------------
     def node_coordinates(self, space):
-        """x nodes (space 0, lattice coordinates), v nodes (space 1), or the x / v
-        quadrature points (spaces 2, 3; the nodes except for the GLL-Gauss basis)."""
+        """x nodes (space 0, lattice coordinates), v nodes (space 1), the x / v
+        quadrature points (spaces 2, 3; the nodes except for the GLL-Gauss
+        basis), or the physical coordinates of the x nodes (space 4)."""
         if space % 2 == 0:
             rows, cols = int(self.info.n_xcells) * (self.degree + 1) ** self.dim_x, self.dim_x
         else:

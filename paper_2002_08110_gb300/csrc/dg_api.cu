@@ -122,6 +122,12 @@ KParams base_params(const dg_ctx* h, int prec) {
   p.t32 = h->tables.t32;
   p.tab = h->basis == DG_BASIS_GLL ? 1 : 0;
   p.kref = h->kref_active;
+  if (h->curved) {
+    const bool f64 = prec == DG_PREC_FP64;   // compute type of the sweeps
+    p.geo_c = f64 ? static_cast<const void*>(h->geo_c64) : static_cast<const void*>(h->geo_c32);
+    p.geo_f = f64 ? static_cast<const void*>(h->geo_f64) : static_cast<const void*>(h->geo_f32);
+    p.ax_tab = f64 ? static_cast<const void*>(h->ax64) : static_cast<const void*>(h->ax32);
+  }
   return p;
 }
 
@@ -146,7 +152,7 @@ dg_status ensure_scratch(dg_ctx* h, int prec) {
 
 cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
                         cudaStream_t s) {
-  if (cfg.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides) {
+  if (cfg.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides && !h->curved) {
     cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
     if (e != cudaErrorNotSupported) return e;
   }
@@ -206,6 +212,8 @@ dg_status apply_core(dg_handle h, const void* src, void* dst, int prec, cudaStre
 
 dg_status do_apply(dg_handle h, const void* src, void* dst, int prec, void* stream, int adjoint) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (adjoint && h->curved)
+    return fail(DG_ERR_UNSUPPORTED, "the transposed operator is not available on a curved mesh");
   const int combo = combo_of(prec);
   if (combo < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
   dg_status st;
@@ -300,6 +308,13 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->vp_e);
   cudaFree(h->host_stage);
   for (int i = 0; i < 4; ++i) cudaFree(h->bc_tmp[i]);
+  cudaFree(h->geo_c64);
+  cudaFree(h->geo_c32);
+  cudaFree(h->geo_f64);
+  cudaFree(h->geo_f32);
+  cudaFree(h->ax64);
+  cudaFree(h->ax32);
+  cudaFree(h->jx_d);
   cudaFree(h->df_u);
   cudaFree(h->df_k64);
   cudaFree(h->df_k32);
@@ -324,10 +339,112 @@ cudaError_t upload(const std::vector<double>& src, T** dst) {
 
 // Contravariant speeds c = J^{-1} a at the x and v nodes (Sec. 3: only the
 // low-dimensional parts are stored and combined on the fly, Sec. 6).
+// Curved x-mesh (dg_geometry.deform): x = Phi(y), Phi_i(y) = y_i +
+// delta_i L_m / (2 pi) sin(2 pi (y_m - lo_m) / L_m), m = (i+1) mod dx.  At
+// every x quadrature point and every x face point: J_x = (dPhi/dy) diag(h/2),
+// its determinant and |J_x| J_x^{-1} (the contravariant flux rows; Nanson's
+// formula for the faces).
+void jacobian_x(const dg_ctx* h, const double* y, double* det, double* R) {
+  const int dx = h->dx;
+  double J[3][3];
+  for (int i = 0; i < dx; ++i)
+    for (int m = 0; m < dx; ++m) J[i][m] = (i == m ? 1.0 : 0.0);
+  for (int i = 0; i < dx; ++i) {
+    const int m = (i + 1) % dx;
+    const double L = h->h[m] * h->ncell[m];
+    J[i][m] += h->deform[i] * std::cos(2.0 * 3.14159265358979323846 * (y[m] - h->lo[m]) / L);
+  }
+  for (int i = 0; i < dx; ++i)
+    for (int m = 0; m < dx; ++m) J[i][m] *= h->h[m] / 2.0;
+  // adjugate / determinant for dx <= 3
+  double A[3][3] = {{0}};
+  double dt;
+  if (dx == 1) {
+    dt = J[0][0];
+    A[0][0] = 1.0;
+  } else if (dx == 2) {
+    dt = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    A[0][0] = J[1][1];
+    A[0][1] = -J[0][1];
+    A[1][0] = -J[1][0];
+    A[1][1] = J[0][0];
+  } else {
+    for (int i = 0; i < 3; ++i)
+      for (int m = 0; m < 3; ++m) {
+        const int i1 = (m + 1) % 3, i2 = (m + 2) % 3, m1 = (i + 1) % 3, m2 = (i + 2) % 3;
+        A[i][m] = J[i1][m1] * J[i2][m2] - J[i1][m2] * J[i2][m1];   // adj = cofactor^T
+      }
+    dt = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+  }
+  *det = dt;
+  // |J| J^{-1} = sign(det) adj(J)
+  const double sg = dt < 0.0 ? -1.0 : 1.0;
+  for (int i = 0; i < dx; ++i)
+    for (int m = 0; m < dx; ++m) R[i * dx + m] = sg * A[i][m];
+  *det = std::fabs(dt);
+}
+
+dg_status compute_geometry(dg_ctx* h) {
+  const int dx = h->dx, n = h->n, nqx = h->nqx;
+  const double* z = h->tables.zeta;
+  int nf = 1;
+  for (int m = 1; m < dx; ++m) nf *= n;
+  const int sc = 1 + dx * dx;
+  h->geo_c_host.assign(static_cast<size_t>(h->ncx) * nqx * sc, 0.0);
+  h->geo_f_host.assign(static_cast<size_t>(h->ncx) * dx * 2 * nf * dx, 0.0);
+  for (long long cx = 0; cx < h->ncx; ++cx) {
+    int cc[3] = {0, 0, 0};
+    long long c = cx;
+    for (int m = 0; m < dx; ++m) {
+      cc[m] = static_cast<int>(c % h->ncell[m]);
+      c /= h->ncell[m];
+    }
+    // cell points
+    for (int q = 0; q < nqx; ++q) {
+      double y[3];
+      int qq = q;
+      for (int m = 0; m < dx; ++m) {
+        y[m] = h->lo[m] + h->h[m] * (cc[m] + (z[qq % n] + 1.0) / 2.0);
+        qq /= n;
+      }
+      double det, R[9];
+      jacobian_x(h, y, &det, R);
+      if (!(det > 0.0)) return fail(DG_ERR_INVALID_ARG, "deformation folds the mesh");
+      double* o = &h->geo_c_host[(static_cast<size_t>(cx) * nqx + q) * sc];
+      o[0] = det;
+      for (int i = 0; i < dx * dx; ++i) o[1 + i] = R[i];
+    }
+    // face points: direction j, side (0: xi_j = -1, 1: +1), the other digits
+    for (int j = 0; j < dx; ++j)
+      for (int sd = 0; sd < 2; ++sd)
+        for (int f = 0; f < nf; ++f) {
+          double y[3];
+          int ff = f;
+          for (int m = 0; m < dx; ++m) {
+            double xi;
+            if (m == j) {
+              xi = sd ? 1.0 : -1.0;
+            } else {
+              xi = z[ff % n];
+              ff /= n;
+            }
+            y[m] = h->lo[m] + h->h[m] * (cc[m] + (xi + 1.0) / 2.0);
+          }
+          double det, R[9];
+          jacobian_x(h, y, &det, R);
+          if (!(det > 0.0)) return fail(DG_ERR_INVALID_ARG, "deformation folds the mesh");
+          double* o = &h->geo_f_host[((((static_cast<size_t>(cx) * dx + j) * 2 + sd) * nf) + f) * dx];
+          for (int m = 0; m < dx; ++m) o[m] = R[j * dx + m];
+        }
+  }
+  return DG_OK;
+}
+
 dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
   const int n = h->n, dx = h->dx, dv = h->dv;
   h->cx_host.assign(static_cast<size_t>(h->ncv) * h->nqv * dx, 0.0);
   h->cv_host.assign(static_cast<size_t>(h->ncx) * h->nqx * dv, 0.0);
+  h->ax_host.assign(static_cast<size_t>(h->ncv) * h->nqv * dx, 0.0);
   const double* z = h->tables.zeta;
   for (long long cv = 0; cv < h->ncv; ++cv)
     for (int q = 0; q < h->nqv; ++q) {
@@ -351,6 +468,7 @@ dg_status compute_speeds(dg_ctx* h, const double* e_nodes) {
         double s = 0.0;
         for (int m = 0; m < dx; ++m) s += h->Sinv[i * dx + m] * a[m];
         h->cx_host[(cv * h->nqv + q) * dx + i] = 2.0 / h->h[i] * s;
+        h->ax_host[(cv * h->nqv + q) * dx + i] = a[i];   // physical, for the curved mesh
       }
     }
   for (long long cx = 0; cx < h->ncx; ++cx)
@@ -587,6 +705,30 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
     delete h;
     return s;
   }
+  for (int i = 0; i < 3; ++i) {
+    const double dl = i < dim_x ? g.deform[i] : 0.0;
+    if (!std::isfinite(dl) || std::fabs(dl) >= 0.5) {
+      delete h;
+      return fail(DG_ERR_INVALID_ARG, "deform amplitudes must be finite and below 0.5 in size");
+    }
+    h->deform[i] = dl;
+    h->curved = h->curved || dl != 0.0;
+  }
+  if (h->curved) {
+    if (!zero) {
+      delete h;
+      return fail(DG_ERR_UNSUPPORTED, "a curved mesh cannot also be sheared");
+    }
+    if (h->basis == DG_BASIS_GLL_GAUSS) {
+      delete h;
+      return fail(DG_ERR_UNSUPPORTED, "the curved mesh needs a collocated basis");
+    }
+    if ((s = compute_geometry(h)) != DG_OK) {
+      delete h;
+      return s;
+    }
+    h->uniform_sides = false;   // the specialised kernels assume an affine mesh
+  }
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess ||
       (e = upload(h->cx_host, &h->cx_d64)) != cudaSuccess ||
@@ -599,6 +741,20 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
       (e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     free_ctx(h);
     return cuda_fail(e, "dg_create");
+  }
+  if (h->curved) {
+    std::vector<double> jx(static_cast<size_t>(h->ncx) * h->nqx);
+    for (size_t i = 0; i < jx.size(); ++i) jx[i] = h->geo_c_host[i * (1 + dim_x * dim_x)];
+    if ((e = upload(h->geo_c_host, &h->geo_c64)) != cudaSuccess ||
+        (e = upload(h->geo_c_host, &h->geo_c32)) != cudaSuccess ||
+        (e = upload(h->geo_f_host, &h->geo_f64)) != cudaSuccess ||
+        (e = upload(h->geo_f_host, &h->geo_f32)) != cudaSuccess ||
+        (e = upload(h->ax_host, &h->ax64)) != cudaSuccess ||
+        (e = upload(h->ax_host, &h->ax32)) != cudaSuccess ||
+        (e = upload(jx, &h->jx_d)) != cudaSuccess) {
+      free_ctx(h);
+      return cuda_fail(e, "dg_create");
+    }
   }
   h->partial_blocks = std::min<long long>(4 * sm_count(), std::max<long long>(1, h->n_dofs / 256));
   if ((e = cudaMalloc(&h->partial, sizeof(double) * 3 * h->partial_blocks)) != cudaSuccess) {
@@ -641,8 +797,33 @@ dg_status dg_info(dg_handle h, dg_info_t* info) {
 
 dg_status dg_node_coordinates(dg_handle h, int space, double* out) {
   if (h == nullptr || out == nullptr) return fail(DG_ERR_INVALID_ARG, "NULL argument");
-  if (space < 0 || space > 3)
-    return fail(DG_ERR_INVALID_ARG, "space must be 0 (x nodes), 1 (v nodes), 2 or 3 (points)");
+  if (space < 0 || space > 4)
+    return fail(DG_ERR_INVALID_ARG,
+                "space must be 0 (x nodes), 1 (v nodes), 2 or 3 (points), 4 (physical x nodes)");
+  if (space == 4) {
+    dg_status st = dg_node_coordinates(h, 0, out);
+    if (st != DG_OK) return st;
+    const int dx = h->dx;
+    const long long rows = h->ncx * h->nqx;
+    for (long long r = 0; r < rows; ++r) {
+      double y[3], x[3];
+      for (int m = 0; m < dx; ++m) y[m] = out[r * dx + m];
+      for (int i = 0; i < dx; ++i) {
+        double v = 0.0;
+        if (h->curved) {
+          const int m = (i + 1) % dx;
+          const double L = h->h[m] * h->ncell[m];
+          v = y[i] + h->deform[i] * L / (2.0 * 3.14159265358979323846) *
+                         std::sin(2.0 * 3.14159265358979323846 * (y[m] - h->lo[m]) / L);
+        } else {
+          for (int m = 0; m < dx; ++m) v += h->S[i * dx + m] * y[m];
+        }
+        x[i] = v;
+      }
+      for (int m = 0; m < dx; ++m) out[r * dx + m] = x[m];
+    }
+    return DG_OK;
+  }
   const bool xs = space % 2 == 0;
   const int dims = xs ? h->dx : h->dv;
   const int off = xs ? 0 : h->dx;
@@ -732,6 +913,7 @@ dg_status dg_poisson_periodic_1d(dg_handle h, const double* rho, double* e, void
   if (h->basis == DG_BASIS_GLL_GAUSS)
     return fail(DG_ERR_UNSUPPORTED, "the Poisson solve needs a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
   if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "the Poisson solve needs dim_x = 1");
+  if (h->curved) return fail(DG_ERR_UNSUPPORTED, "the Poisson solve needs an affine mesh");
   if (rho == nullptr || e == nullptr || reinterpret_cast<uintptr_t>(rho) % 8 != 0 ||
       reinterpret_cast<uintptr_t>(e) % 8 != 0)
     return fail(DG_ERR_INVALID_ARG, "rho and e must be non-NULL and 8-byte aligned");
@@ -754,13 +936,14 @@ dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, i
                         void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
   if (h->basis == DG_BASIS_GLL_GAUSS)
-    return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps needs a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
+    return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
   if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need dim_x = 1");
   if (h->field_kind != DG_FIELD_PHASE_SPACE)
     return fail(DG_ERR_INVALID_ARG, "Vlasov-Poisson steps need a phase-space handle");
   if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
   if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  if (h->curved) return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need an affine mesh");
   dg_status st;
   if ((st = check_vec(u, "u")) != DG_OK || (st = check_vec(w0, "w0")) != DG_OK ||
       (st = check_vec(w1, "w1")) != DG_OK)
@@ -810,6 +993,8 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
   if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
   if (stage < 0 || stage > 4) return fail(DG_ERR_INVALID_ARG, "stage must be in [0, 4]");
   if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  if (adjoint && h->curved)
+    return fail(DG_ERR_UNSUPPORTED, "adjoint stages are not available on a curved mesh");
   dg_status st;
   if ((st = check_vec(w_in, "w_in")) != DG_OK || (st = check_vec(w_out, "w_out")) != DG_OK ||
       (st = check_vec(u, "u")) != DG_OK)
@@ -889,6 +1074,8 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
   if (combo_of(prec) < 0) return fail(DG_ERR_INVALID_ARG, "unknown precision %d", prec);
   if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
   if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  if (adjoint && h->curved)
+    return fail(DG_ERR_UNSUPPORTED, "adjoint steps are not available on a curved mesh");
   dg_status st;
   if ((st = check_vec(u, "u")) != DG_OK || (st = check_vec(w0, "w0")) != DG_OK ||
       (st = check_vec(w1, "w1")) != DG_OK)
@@ -976,7 +1163,11 @@ dg_status dg_integrals(dg_handle h, const double* u, double* out, void* stream) 
     u = h->bc_tmp[2];
   }
   KParams p = base_params(h, DG_PREC_FP64);
-  cudaError_t e = launch_integrals(p, h->n, u, h->partial, h->partial_blocks, h->detJ, s);
+  double detJv = 1.0;
+  for (int j = h->dx; j < h->d; ++j) detJv *= h->h[j] / 2.0;
+  cudaError_t e = launch_integrals(p, h->n, u, h->partial, h->partial_blocks,
+                                   h->curved ? detJv : h->detJ, h->curved ? h->jx_d : nullptr,
+                                   h->nqx, s);
   if (e != cudaSuccess) return cuda_fail(e, "integrals kernel");
   std::vector<double> host(3 * h->partial_blocks);
   if ((e = cudaMemcpyAsync(host.data(), h->partial, host.size() * 8, cudaMemcpyDeviceToHost, s)) !=

@@ -341,7 +341,7 @@ dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out) {
       return report(DG_ERR_INVALID_ARG, "NULL handle in batch");
     }
     if (h->field_kind != DG_FIELD_CONSTANT || h->d < 3 || h->d > 4 || h->ncells > (1LL << 30) ||
-        h->basis != DG_BASIS_GL) {
+        h->basis != DG_BASIS_GL || h->curved) {
       free_batch(b);
       return report(DG_ERR_UNSUPPORTED,
                     "batched members must be constant-velocity problems with d = 3 or 4 "

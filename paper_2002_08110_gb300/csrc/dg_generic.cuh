@@ -116,6 +116,74 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
         const int l = it - c * NL;
         const int base = (l % sj) + (l / sj) * sj * N;
         const long long cell = cell0 + c;
+        if (p.geo_c != nullptr && j < p.dx) {
+          // Curved x-mesh: the flux speed g = |J_x| c_j varies along the line.
+          // With collocation the line's weak form divided by the diagonal
+          // mass reads du_q = (1/|J_x,q|) [sum_p Dt[q][p] g_p u_p
+          //                                - Lp[q] F(+1) + Lm[q] F(-1)],
+          // F(+-1) = g(+-1) u*(+-1) with the upwind state at each face.
+          const long long cx = cell % p.ncx, cv = cell / p.ncx;
+          const int qx0 = base % nqx, qv = base / nqx;
+          const int dxn = p.dx, sc = 1 + dxn * dxn;
+          const TC* A = static_cast<const TC*>(p.ax_tab) + (cv * nqv + qv) * dxn;
+          const TC* Gc = static_cast<const TC*>(p.geo_c) + cx * nqx * sc;
+          TC uu[N], g[N], ij[N];
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            uu[q] = SMEM ? su[c * NP + base + q * sj] : cvt<TC>(src[cell * NP + base + q * sj]);
+            const TC* gq = Gc + (qx0 + q * sj) * sc;
+            TC cq = TC(0);
+            for (int m = 0; m < dxn; ++m) cq += gq[1 + j * dxn + m] * A[m];
+            g[q] = cq;
+            ij[q] = TC(1) / gq[0];
+          }
+          int f = 0, mul = 1, rr = qx0, nf = 1;
+          for (int m = 0; m < dxn; ++m) {
+            const int dg = rr % N;
+            rr /= N;
+            if (m != j) {
+              f += dg * mul;
+              mul *= N;
+              nf *= N;
+            }
+          }
+          const TC* Fm = static_cast<const TC*>(p.geo_f) + ((((cx * dxn + j) * 2 + 0) * nf) + f) * dxn;
+          const TC* Fp = static_cast<const TC*>(p.geo_f) + ((((cx * dxn + j) * 2 + 1) * nf) + f) * dxn;
+          TC gm = TC(0), gp = TC(0);
+          for (int m = 0; m < dxn; ++m) {
+            gm += Fm[m] * A[m];
+            gp += Fp[m] * A[m];
+          }
+          TC tp = TC(0), tm = TC(0);
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            tp += T.lp[q] * uu[q];
+            tm += T.lm[q] * uu[q];
+          }
+          TC up = tp, um = tm;
+          if (!(gp > TC(0))) {           // inflow at +1: the neighbour above's -1 trace
+            const TIN* ns = src + neighbour_cell(p, cell, j, 1) * NP + base;
+            up = TC(0);
+#pragma unroll
+            for (int q = 0; q < N; ++q) up += T.lm[q] * cvt<TC>(ns[q * sj]);
+          }
+          if (gm > TC(0)) {              // inflow at -1: the neighbour below's +1 trace
+            const TIN* ns = src + neighbour_cell(p, cell, j, -1) * NP + base;
+            um = TC(0);
+#pragma unroll
+            for (int q = 0; q < N; ++q) um += T.lp[q] * cvt<TC>(ns[q * sj]);
+          }
+          const TC Fplus = gp * up, Fminus = gm * um;
+          TC* r = sr + c * NP + base;
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            TC acc = T.Lm[q] * Fminus - T.Lp[q] * Fplus;
+#pragma unroll
+            for (int s2 = 0; s2 < N; ++s2) acc += T.Dt[q * N + s2] * (g[s2] * uu[s2]);
+            r[q * sj] += ij[q] * acc;
+          }
+          continue;
+        }
         TC cj = line_speed<TC>(p, j, cell, base, nqx, nqv);
         if (p.adjoint) cj = -cj;
         if (cj == TC(0)) continue;

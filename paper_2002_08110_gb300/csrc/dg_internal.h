@@ -29,6 +29,7 @@ constexpr int kMaxN = 6;
 // against the diagonal mass matrix.)
 template <typename T>
 struct Tab1D {
+  T Dt[kMaxN * kMaxN];      // Dt[q][p] = D[p][q] w_p / w_q (the curved-mesh line operator)
   T Gp[kMaxN * kMaxN];
   T Gn[kMaxN * kMaxN];
   T Lp[kMaxN];
@@ -83,6 +84,14 @@ struct KParams {
   double a_dt, b_dt;        // stage mode coefficients (a_s dt, b_s dt)
   int tab;                  // constant-table set of the 6D kernels (0 GL, 1 GLL)
   const float* kref;        // stage mode, delta-f form: K = kref + L(w) (nullptr: plain)
+  // curved x-mesh (nullptr: affine), in the compute type: per x cell and x
+  // point [ncx][n^dx][1 + dx*dx] = (|J_x|, |J_x| J_x^{-1} row-major); per x
+  // cell, direction j, side (0: -1, 1: +1) and face point (the other x
+  // digits) [ncx][dx][2][n^(dx-1)][dx] = |J_x| (J_x^{-1})_{j,:}; and the
+  // physical a_x at the v points [ncv][n^dv][dx]
+  const void* geo_c;
+  const void* geo_f;
+  const void* ax_tab;
   Tab1D<double> t64;
   Tab1D<float> t32;
 };
@@ -126,7 +135,7 @@ void lsrk_coefficients(double* a4, double* b5);
 // Small kernels (dg_misc.cu).
 cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n, cudaStream_t s);
 cudaError_t launch_integrals(const KParams& p, int n, const double* u, double* partial,
-                             int blocks, double detJ, cudaStream_t s);
+                             int blocks, double detJ, const double* jx, int nqx, cudaStream_t s);
 // Zero-mean periodic antiderivative of rho - mean(rho) on a 1D mesh (the
 // Poisson solve of Sec. 6 for dim_x = 1), and contravariant v speeds from a
 // device field (dg_misc.cu).
@@ -174,6 +183,13 @@ struct dg_ctx {
   double detJ = 0.0;
   int field_kind = 0;
   int basis = 0;            // dg_basis
+  bool curved = false;      // deformed x-mesh (dg_geometry.deform)
+  double deform[3] = {0, 0, 0};
+  std::vector<double> geo_c_host, geo_f_host, ax_host;
+  double* geo_c64 = nullptr; float* geo_c32 = nullptr;
+  double* geo_f64 = nullptr; float* geo_f32 = nullptr;
+  double* ax64 = nullptr; float* ax32 = nullptr;
+  double* jx_d = nullptr;   // |J_x| per x point (FP64) for the integrals
   double* bc_tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // DG_BASIS_GLL_GAUSS temporaries
   double a_const[dg::kMaxDim] = {0};
   double speed_sum = 0.0;

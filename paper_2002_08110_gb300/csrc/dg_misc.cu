@@ -30,13 +30,15 @@ cudaError_t launch_convert(const double* u, void* w, int w_is_float, long long n
 // Per-block partial sums of |J| W_q u_q, |J| W_q u_q^2 and max |u_q| (cell
 // quadrature at the collocation nodes, Sec. 2.5).  FP64.
 __global__ void k_integrals(const double* __restrict__ u, long long n_dofs, int npc, int d, int n,
-                            Tab1D<double> t, double detJ, double* __restrict__ partial) {
+                            Tab1D<double> t, double detJ, const double* __restrict__ jx, int nqx,
+                            long long ncx, double* __restrict__ partial) {
   __shared__ double s_m[256], s_l[256], s_x[256];
   double m = 0.0, l = 0.0, x = 0.0;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n_dofs;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     int q = static_cast<int>(i % npc);
-    double w = detJ;
+    // curved x-mesh: detJ holds |J_v| and jx the |J_x| of each x point
+    double w = jx ? detJ * jx[((i / npc) % ncx) * nqx + q % nqx] : detJ;
     for (int k = 0; k < d; ++k) {
       w *= t.w[q % n];
       q /= n;
@@ -66,12 +68,12 @@ __global__ void k_integrals(const double* __restrict__ u, long long n_dofs, int 
 }
 
 cudaError_t launch_integrals(const KParams& p, int n, const double* u, double* partial,
-                             int blocks, double detJ, cudaStream_t s) {
+                             int blocks, double detJ, const double* jx, int nqx, cudaStream_t s) {
   const int d = p.dx + p.dv;
   int npc = 1;
   for (int k = 0; k < d; ++k) npc *= n;
   const long long n_dofs = p.ncells * npc;
-  k_integrals<<<blocks, 256, 0, s>>>(u, n_dofs, npc, d, n, p.t64, detJ, partial);
+  k_integrals<<<blocks, 256, 0, s>>>(u, n_dofs, npc, d, n, p.t64, detJ, jx, nqx, p.ncx, partial);
   return cudaGetLastError();
 }
 

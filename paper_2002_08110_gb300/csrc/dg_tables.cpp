@@ -186,11 +186,13 @@ void build_tables(int n, int basis, HostTables* t) {
   for (int q = 0; q < n; ++q)
     for (int p = 0; p < n; ++p) {
       const double dt = t->D[p][q] * t->w[p] / t->w[q];
+      d.Dt[q * n + p] = dt;
       d.Gp[q * n + p] = dt - d.Lp[q] * t->lp[p];
       d.Gn[q * n + p] = dt + d.Lm[q] * t->lm[p];
     }
   Tab1D<float>& f = t->t32;
   for (int i = 0; i < kMaxN * kMaxN; ++i) {
+    f.Dt[i] = static_cast<float>(d.Dt[i]);
     f.Gp[i] = static_cast<float>(d.Gp[i]);
     f.Gn[i] = static_cast<float>(d.Gn[i]);
   }
