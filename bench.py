@@ -385,6 +385,23 @@ def measure_configs(torch, hbm_peak):
         del u
         torch.cuda.empty_cache()
 
+    # 6D on a curved x-mesh (a Jacobian per quadrature point, deformation
+    # 0.1 in every x direction): FP32 stage in the generic kernel
+    zeta, _ = reference_nodes(w.k)
+    dg = DG(e_nodes=W.e_table(w, zeta), deform=(0.1, 0.1, 0.1), **W.dg_kwargs(w))
+    u = W.separable_state(w, zeta, xp=torch, device="cuda")
+    a, b = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda")
+    dg.rk_stage(a, b, u, 0, dt, prec=PREC_FP32)
+    ms = _timed(torch, lambda: dg.rk_stage(a, b, u, 1, dt, prec=PREC_FP32), 5)
+    dg.check()
+    out["6d_curved"] = {"workload": w.name + "_curved0.1", "dofs": dg.n_dofs, "ms_per_stage": ms,
+                        "GDoF/s_per_stage": dg.n_dofs / (ms * 1e-3) / 1e9,
+                        "frac_hbm": 24 * dg.n_dofs / (ms * 1e-3) / 1e9 / hbm_peak,
+                        "kernel": "generic (the specialised 6D kernels are affine-only)"}
+    dg.close()
+    del u, a, b
+    torch.cuda.empty_cache()
+
     # 2D: one period (T = 2, 240 steps), FP64
     w = W.config_2d()
     dg, zeta = make(w)
