@@ -723,6 +723,10 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
       delete h;
       return fail(DG_ERR_UNSUPPORTED, "the curved mesh needs a collocated basis");
     }
+    if (static_cast<size_t>(h->npc) * 16 > 200 * 1024) {
+      delete h;
+      return fail(DG_ERR_UNSUPPORTED, "curved meshes support cells of at most 12800 DoFs");
+    }
     if ((s = compute_geometry(h)) != DG_OK) {
       delete h;
       return s;

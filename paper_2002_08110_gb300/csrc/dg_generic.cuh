@@ -76,7 +76,9 @@ __device__ __forceinline__ long long neighbour_cell(const KParams& p, long long 
   return cell + static_cast<long long>(c2 - cj) * st;
 }
 
-template <int D, int N, typename TC, typename TIN, typename TW, bool SMEM>
+// CURVED: the curved x-mesh path for the x directions (a separate
+// instantiation, so the affine kernel carries none of its registers or code).
+template <int D, int N, typename TC, typename TIN, typename TW, bool SMEM, bool CURVED>
 __global__ void __launch_bounds__(512) k_generic(const KParams p) {
   constexpr int NP = Pow<N, D>::v;
   constexpr int NL = NP / N;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
         const int l = it - c * NL;
         const int base = (l % sj) + (l / sj) * sj * N;
         const long long cell = cell0 + c;
-        if (p.geo_c != nullptr && j < p.dx) {
+        if (CURVED && j < p.dx) {
           // Curved x-mesh: the flux speed g = |J_x| c_j varies along the line.
           // With collocation the line's weak form divided by the diagonal
           // mass reads du_q = (1/|J_x,q|) [sum_p Dt[q][p] g_p u_p
@@ -281,7 +283,8 @@ cudaError_t launch_generic(KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
       smem = static_cast<size_t>(cpb) * NP * sizeof(TC) * 2;
     }
     p.cells_per_block = cpb;
-    auto kern = k_generic<D, N, TC, TIN, TW, true>;
+    auto kern = p.geo_c != nullptr ? k_generic<D, N, TC, TIN, TW, true, true>
+                                   : k_generic<D, N, TC, TIN, TW, true, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -289,10 +292,12 @@ cudaError_t launch_generic(KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     kern<<<static_cast<unsigned>(grid), cfg.threads, smem, s>>>(p);
   } else {
-    if (p.scratch == nullptr) return cudaErrorInvalidValue;
+    // curved meshes are limited to cells that fit in shared memory (checked
+    // when the handle is created)
+    if (p.scratch == nullptr || p.geo_c != nullptr) return cudaErrorInvalidValue;
     p.cells_per_block = 1;
     const int blocks = generic_grid_blocks(D, N, p.ncells, 1, cfg.threads);
-    k_generic<D, N, TC, TIN, TW, false><<<blocks, cfg.threads, 0, s>>>(p);
+    k_generic<D, N, TC, TIN, TW, false, false><<<blocks, cfg.threads, 0, s>>>(p);
   }
   return cudaGetLastError();
 }
