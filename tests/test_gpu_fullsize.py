@@ -163,3 +163,53 @@ def test_5d_adjoint_fullsize_sampled():
     got = out[e * npc:(e + 1) * npc].double().cpu().numpy()
     assert np.linalg.norm(got - ref) <= 4e-5 * np.linalg.norm(scale)
     dg.close()
+
+
+def test_6d_gll_collocation_stage_sampled():
+    """The Lobatto-collocation stage at 8^6 (face-layer kernel) on sampled
+    cells against the oracle's gllc operator."""
+    from paper_2002_08110_gb300 import DG, PREC_FP32, basis_nodes
+    from oracle.dg import PhaseSpaceField, Problem
+    w = W.config_6d()
+    nodes, qpts, _ = basis_nodes(1, w.k)
+    dg = DG(e_nodes=W.e_table(w, qpts), basis=1, **W.dg_kwargs(w))
+    assert dg.info.uniform_sides == 1
+    p = Problem(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
+                PhaseSpaceField(w.dx, w.dv, W.e_function(w)), basis="gllc")
+    u = W.separable_state(w, nodes, xp=torch, device="cuda")
+    npc = p.dofs_per_cell
+    dt, _ = W.time_step(w)
+    w_in = u.float()
+    w_out = torch.empty_like(w_in)
+    uu = u.clone()
+    stage = 2
+    dg.rk_stage(w_in, w_out, uu, stage, dt, prec=PREC_FP32)
+    dg.check()
+    cells = _sample_cells(p, 3, seed=4)
+    K, S = _oracle_cells(p, DeviceVector(w_in), cells)
+    for e, Ke, Se in zip(cells, K, S):
+        sl = slice(e * npc, (e + 1) * npc)
+        u_old = u[sl].cpu().numpy()
+        u_ref = u_old + lsrk.B[stage] * dt * Ke
+        err_u = np.abs(uu[sl].cpu().numpy() - u_ref)
+        assert np.linalg.norm(err_u) <= 1e-5 * dt * np.linalg.norm(Se) + 1e-15 * np.linalg.norm(u_old)
+    dg.close()
+
+
+def test_6d_deltaf_apply_sampled(six):
+    """The delta-f operator at 8^6 around the Maxwellian: plain relative error
+    against the oracle on sampled cells below 1e-5 of the sampled K."""
+    w, dg, p, u = six
+    from paper_2002_08110_gb300 import reference_nodes
+    zeta, _ = reference_nodes(w.k)
+    u_eq = W.separable_state(W.equilibrium_6d(w), zeta, xp=torch, device="cuda")
+    dg.set_reference(u_eq)
+    k = dg.apply_df(u)
+    dg.check()
+    npc = p.dofs_per_cell
+    cells = _sample_cells(p, 3, seed=5)
+    K, _ = _oracle_cells(p, DeviceVector(u), cells)
+    got = np.concatenate([k[e * npc:(e + 1) * npc].cpu().numpy() for e in cells])
+    ref = np.concatenate(K)
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+    del k, u_eq
