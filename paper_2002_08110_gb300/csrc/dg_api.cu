@@ -544,8 +544,10 @@ void lsrk_coefficients(double* a4, double* b5) {
 }
 
 size_t generic_smem_bytes(int d, int n, int combo, int cells_per_block) {
+  // per cell: input and residual in the compute type, and the cell's
+  // bookkeeping (x cell, v cell, two neighbours per direction)
   const size_t tb = combo == kDDD ? 8 : 4;
-  const size_t b = static_cast<size_t>(ipow(n, d)) * tb * 2 * cells_per_block;
+  const size_t b = (static_cast<size_t>(ipow(n, d)) * tb * 2 + (2 + 2 * d) * 8) * cells_per_block;
   return b <= 200 * 1024 ? b : 0;
 }
 

@@ -187,3 +187,24 @@ def test_launch_configurations_agree():
     out = dg.apply(u).cpu().numpy()
     assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))
     dg.close()
+
+
+@pytest.mark.parametrize("cells", [(2, 2, 2, 2, 2, 2), (1, 3, 1, 2, 1, 1)])
+def test_zero_velocity_gives_exact_zero(cells):
+    """a = 0 (the degenerate field): the operator is exactly zero in every
+    precision and kernel, and a stage leaves the state unchanged."""
+    from paper_2002_08110_gb300 import DG
+    dg = DG(3, 3, 3, cells[:3], cells[3:], [0] * 3, [1] * 3, [-1] * 3, [1] * 3, field_kind=0,
+            a_const=[0.0] * 6)
+    u = torch.tensor(np.random.default_rng(2).standard_normal(dg.n_dofs), device="cuda")
+    for prec, x in ((0, u), (1, u.float()), (2, u)):
+        for variant in (0, 1, 2):
+            if prec == 0 and variant:
+                continue
+            dg.set_launch(prec, threads=256, cells_per_block=1, variant=variant)
+            assert torch.count_nonzero(dg.apply(x, prec=prec)) == 0, (prec, variant)
+    w_in, w_out, uu = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda"), u.clone()
+    dg.rk_stage(w_in, w_out, uu, 1, 0.1, prec=1)
+    dg.check()
+    assert torch.equal(uu, u)
+    dg.close()
