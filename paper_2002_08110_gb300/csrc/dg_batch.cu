@@ -55,6 +55,7 @@ struct BParams {
   int* err;
   int mode;        // 0: convert u -> w0, 1: stage
   int stage, parity;
+  int nbt_off;     // byte offset of the per-cell neighbour table in shared memory
   double a, b;     // a_s (or b_4 at the last stage), b_s
   int last_stage;
 };
@@ -84,7 +85,7 @@ __device__ __forceinline__ int nb_cell(const BInst& I, int cell, int j, int s) {
 // stage vectors of type TW (TC == TW here).
 template <int D, int N, typename TC, typename TW>
 __device__ void process_tile(const BInst& I, const BParams& bp, int c0, int nc, TC* su, TC* sr,
-                             int& bad) {
+                             int* nbt, int& bad) {
   constexpr int NP = Pow<N, D>::v;
   constexpr int NL = NP / N;
   const Tab1D<TC>& T = btab<TC>(N);
@@ -95,6 +96,13 @@ __device__ void process_tile(const BInst& I, const BParams& bp, int c0, int nc, 
     su[i] = src[base0 + i];
     sr[i] = TC(0);
   }
+  // upwind neighbours of the tile's cells (below, above), once per cell
+  for (int c = threadIdx.x; c < nc; c += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      nbt[c * 2 * kBatchMaxDim + 2 * j] = nb_cell(I, c0 + c, j, -1);
+      nbt[c * 2 * kBatchMaxDim + 2 * j + 1] = nb_cell(I, c0 + c, j, 1);
+    }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -107,11 +115,10 @@ __device__ void process_tile(const BInst& I, const BParams& bp, int c0, int nc, 
         const int c = it / NL;
         const int l = it - c * NL;
         const int base = (l % sj) + (l / sj) * sj * N;
-        const int cell = c0 + c;
         TC uu[N];
 #pragma unroll
         for (int q = 0; q < N; ++q) uu[q] = su[c * NP + base + q * sj];
-        const int nb = nb_cell(I, cell, j, pos ? -1 : 1);
+        const int nb = nbt[c * 2 * kBatchMaxDim + 2 * j + (pos ? 0 : 1)];
         const TW* ns = src + static_cast<size_t>(nb) * NP + base;
         TC t = TC(0);
 #pragma unroll
@@ -182,17 +189,18 @@ __global__ void __launch_bounds__(512) k_batch(const BParams bp) {
     TC* su = reinterpret_cast<TC*>(bsm);
     const int cap = tl.ncells * I.npc;
     TC* sr = su + cap;
+    int* nbt = reinterpret_cast<int*>(bsm + bp.nbt_off);
     switch (I.d * 8 + I.n) {
-      case 3 * 8 + 2: process_tile<3, 2, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 3 * 8 + 3: process_tile<3, 3, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 3 * 8 + 4: process_tile<3, 4, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 3 * 8 + 5: process_tile<3, 5, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 3 * 8 + 6: process_tile<3, 6, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 4 * 8 + 2: process_tile<4, 2, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 4 * 8 + 3: process_tile<4, 3, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 4 * 8 + 4: process_tile<4, 4, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 4 * 8 + 5: process_tile<4, 5, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
-      case 4 * 8 + 6: process_tile<4, 6, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, bad); break;
+      case 3 * 8 + 2: process_tile<3, 2, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 3 * 8 + 3: process_tile<3, 3, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 3 * 8 + 4: process_tile<3, 4, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 3 * 8 + 5: process_tile<3, 5, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 3 * 8 + 6: process_tile<3, 6, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 4 * 8 + 2: process_tile<4, 2, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 4 * 8 + 3: process_tile<4, 3, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 4 * 8 + 4: process_tile<4, 4, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 4 * 8 + 5: process_tile<4, 5, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
+      case 4 * 8 + 6: process_tile<4, 6, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
       default: break;
     }
   }
@@ -214,6 +222,7 @@ struct dg_batch_ctx {
   int threads = 256;
   std::vector<Tile> tiles;
   size_t smem64 = 0, smem32 = 0;  // bytes of dynamic shared memory
+  int nbt_off64 = 0, nbt_off32 = 0;  // offset of the neighbour table in it
   BInst* inst_d = nullptr;
   Tile* tiles_d = nullptr;
   int* counters_d = nullptr;      // one per stage (+ the conversion pass)
@@ -256,7 +265,7 @@ void drop_graphs(dg_batch b) {
 // Tiles of `tile_dofs` DoFs (whole cells, at least one), member by member.
 dg_status build_tiles(dg_batch b) {
   b->tiles.clear();
-  size_t max_cells_dofs = 0;
+  size_t max_cells_dofs = 0, max_cells = 0;
   for (int m = 0; m < b->count; ++m) {
     const int npc = static_cast<int>(b->npc[m]);
     const int per = std::max(1, b->tile_dofs / npc);
@@ -266,9 +275,14 @@ dg_status build_tiles(dg_batch b) {
       b->tiles.push_back(t);
     }
     max_cells_dofs = std::max(max_cells_dofs, static_cast<size_t>(per) * npc);
+    max_cells = std::max(max_cells, static_cast<size_t>(per));
   }
-  b->smem64 = max_cells_dofs * 2 * sizeof(double);
-  b->smem32 = max_cells_dofs * 2 * sizeof(float);
+  // the tile's values and residuals, then its cells' neighbour table
+  b->nbt_off64 = static_cast<int>(max_cells_dofs * 2 * sizeof(double));
+  b->nbt_off32 = static_cast<int>(max_cells_dofs * 2 * sizeof(float));
+  const size_t nbt_bytes = max_cells * 2 * kBatchMaxDim * sizeof(int);
+  b->smem64 = b->nbt_off64 + nbt_bytes;
+  b->smem32 = b->nbt_off32 + nbt_bytes;
   if (b->smem64 > 200 * 1024) b->smem64 = 0;  // FP64 not possible at this tile size
   if (b->smem32 > 200 * 1024) return report(DG_ERR_INVALID_ARG, "tile too large for shared memory");
   cudaFree(b->tiles_d);
@@ -316,6 +330,7 @@ dg_status enqueue_step(dg_batch b, int prec, int parity, cudaStream_t s) {
     bp.a = st < 4 ? A[st] : B[4];
     bp.b = B[st];
     bp.last_stage = st == 4;
+    bp.nbt_off = prec == DG_PREC_FP64 ? b->nbt_off64 : b->nbt_off32;
     e = prec == DG_PREC_FP64 ? launch_batch<double, double>(b, bp, b->smem64, s)
                              : launch_batch<float, float>(b, bp, b->smem32, s);
     if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
