@@ -91,7 +91,7 @@ dg_status check_vec(const void* ptr, const char* name) {
 // Captured LSRK graphs hold kernel choices and scratch pointers: dropped
 // whenever either changes.
 void drop_graphs(dg_ctx* h) {
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < dg_ctx::kGraphSlots; ++i)
     if (h->gexec[i]) {
       cudaGraphExecDestroy(h->gexec[i]);
       h->gexec[i] = nullptr;
@@ -292,7 +292,7 @@ dg_status validate_cfg(const dg_ctx* h, int prec, const LaunchCfg& c) {
 
 void free_ctx(dg_ctx* h) {
   if (!h) return;
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < dg_ctx::kGraphSlots; ++i)
     if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   cudaFree(h->cx_d64);
@@ -1117,6 +1117,7 @@ dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, in
       if ((st = enqueue_step(h, u, w0, w1, dt, prec, adjoint, i % 2, s)) != DG_OK) return st;
     return DG_OK;
   }
+  int slot_of[2] = {-1, -1};
   for (int parity = 0; parity < 2 && parity < nsteps; ++parity) {
     dg_ctx::GraphKey key;
     key.u = u;
@@ -1127,10 +1128,22 @@ dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, in
     key.adjoint = adjoint;
     key.parity = parity;
     key.kref = h->kref_active;
-    if (h->gexec[parity] && h->gkey[parity] == key) continue;
-    if (h->gexec[parity]) {
-      cudaGraphExecDestroy(h->gexec[parity]);
-      h->gexec[parity] = nullptr;
+    int slot = -1;
+    for (int i = 0; i < dg_ctx::kGraphSlots; ++i)
+      if (h->gexec[i] && h->gkey[i] == key) slot = i;
+    if (slot >= 0) {
+      h->gused[slot] = ++h->gclock;
+      slot_of[parity] = slot;
+      continue;
+    }
+    // a free slot, else the least recently used one other than this call's
+    for (int i = 0; i < dg_ctx::kGraphSlots && slot < 0; ++i)
+      if (!h->gexec[i]) slot = i;
+    if (slot < 0) {
+      for (int i = 0; i < dg_ctx::kGraphSlots; ++i)
+        if (i != slot_of[0] && (slot < 0 || h->gused[i] < h->gused[slot])) slot = i;
+      cudaGraphExecDestroy(h->gexec[slot]);
+      h->gexec[slot] = nullptr;
     }
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal)) !=
@@ -1143,16 +1156,19 @@ dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, in
       return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-    e = cudaGraphInstantiate(&h->gexec[parity], graph, 0);
+    e = cudaGraphInstantiate(&h->gexec[slot], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-      h->gexec[parity] = nullptr;
+      h->gexec[slot] = nullptr;
       return cuda_fail(e, "graph instantiation");
     }
-    h->gkey[parity] = key;
+    h->gkey[slot] = key;
+    h->gused[slot] = ++h->gclock;
+    slot_of[parity] = slot;
   }
   for (int i = 0; i < nsteps; ++i)
-    if ((e = cudaGraphLaunch(h->gexec[i % 2], s)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    if ((e = cudaGraphLaunch(h->gexec[slot_of[i % 2]], s)) != cudaSuccess)
+      return cuda_fail(e, "graph launch");
   return DG_OK;
 }
 

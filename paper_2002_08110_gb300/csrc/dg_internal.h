@@ -232,6 +232,12 @@ struct dg_ctx {
              adjoint == o.adjoint && parity == o.parity && kref == o.kref;
     }
   };
-  GraphKey gkey[2];
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // a small least-recently-used cache: the checkpointed backward of the
+  // autograd wrapper alternates between the recomputation and the adjoint
+  // steps, which are different graphs
+  static constexpr int kGraphSlots = 8;
+  GraphKey gkey[kGraphSlots];
+  cudaGraphExec_t gexec[kGraphSlots] = {};
+  unsigned long long gused[kGraphSlots] = {};
+  unsigned long long gclock = 0;
 };
