@@ -408,6 +408,16 @@ dg_status dg_integrals_noalloc(const double* u, long long n_cells, int dim, int 
  */
 dg_status dg_check(dg_handle h, void* stream);
 
+/*
+ * Self-test of the failure path of the bounded waits: launches one block
+ * that waits on an mbarrier whose expected bytes never arrive (no copy is
+ * issued), gives up after about 1 ms of SM clock and latches the timeout,
+ * so the next dg_check returns DG_ERR_TIMEOUT and clears it.  Nothing is
+ * left in flight; the context stays usable.  (The cell kernels wait up to
+ * about 2 s before giving up the same way.)
+ */
+dg_status dg_selftest_wait(dg_handle h, void* stream);
+
 /* Current launch configuration for ``prec`` (host struct). */
 dg_status dg_get_launch(dg_handle h, int prec, dg_launch* cfg);
 

@@ -80,6 +80,7 @@ def load():
         "dg_integrals": (i, [vp, vp, c_double_p, vp]),
         "dg_integrals_noalloc": (i, [vp, ll, i, i, d, c_double_p, vp]),
         "dg_check": (i, [vp, vp]),
+        "dg_selftest_wait": (i, [vp, vp]),
         "dg_basis_nodes": (i, [i, i, vp, vp, vp]),
         "dg_set_reference": (i, [vp, vp, vp]),
         "dg_apply_df": (i, [vp, vp, vp, vp]),

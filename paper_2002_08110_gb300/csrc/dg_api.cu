@@ -1432,3 +1432,10 @@ dg_status dg_rk_step_df(dg_handle h, double* u, float* w0, float* w1, double dt,
     return cuda_fail(e, "delta-f state");
   return DG_OK;
 }
+
+dg_status dg_selftest_wait(dg_handle h, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  cudaError_t e = launch_wait_probe(h->err_d, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  return DG_OK;
+}

@@ -1457,6 +1457,29 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
 
 }  // namespace
 
+// Self-test of the bounded waits: one block arrives on an mbarrier that
+// expects 16 bytes no copy will ever deliver, waits with the same bounded
+// loop as the cell kernels (a short limit here), gives up and latches the
+// timeout bit.  Nothing is in flight when it returns.
+__global__ void k_wait_probe(int* err, long long limit) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  bool done = false;
+  while (!done && clock64() - t0 < limit) done = mbar_try_wait(&bar, 0);
+  if (!done && threadIdx.x == 0) atomicOr(err, 2);
+}
+
+cudaError_t launch_wait_probe(int* err, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(err, 2000000LL);   // about 1 ms of SM clock
+  return cudaGetLastError();
+}
+
 cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab) {
   float G[2][16], Ln[2][4], lw[2][4];
   for (int i = 0; i < 16; ++i) {

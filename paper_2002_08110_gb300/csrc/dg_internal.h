@@ -126,6 +126,8 @@ int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
 // Uploads the n = 4 tables of the specialised kernel (they depend on n only).
 cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab);
+// A block whose bounded mbarrier wait runs out by construction (dg_cell6d.cu).
+cudaError_t launch_wait_probe(int* err, cudaStream_t s);
 
 // Records the thread's last-error message and returns s (dg_api.cu).
 dg_status report(dg_status s, const char* msg);

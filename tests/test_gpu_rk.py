@@ -198,3 +198,22 @@ def test_host_buffer_stage_equals_device_stage(prec):
         assert torch.equal(hw_out, dw_out.cpu())
     dg.check()
     dg.close()
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """A kernel wait that cannot complete (an mbarrier expecting bytes that no
+    copy delivers) gives up after its limit and latches DG_ERR_TIMEOUT; the
+    latch clears and the context keeps working."""
+    import ctypes
+    from paper_2002_08110_gb300 import DGError
+    dg, p = random_problem(2, 2, 2, (2, 3, 2, 2), "phase", seed=3)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert dg.lib.dg_selftest_wait(dg.handle, stream) == 0
+    with pytest.raises(DGError) as err:
+        dg.check()
+    assert err.value.status == 6            # DG_ERR_TIMEOUT
+    dg.check()                              # cleared
+    u = torch.tensor(np.random.default_rng(0).standard_normal(p.n_dofs), device="cuda")
+    ref = p.apply(u.cpu().numpy())
+    assert np.linalg.norm(dg.apply(u).cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+    dg.close()
