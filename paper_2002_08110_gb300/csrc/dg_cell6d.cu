@@ -97,14 +97,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
       : "memory");
 }
-// Brings `bytes` (a multiple of 16, 16-byte aligned) into L2 ahead of use,
-// marked evict-first: the FP64 state is read once per stage.
-__device__ __forceinline__ void prefetch_l2_once(const void* src, unsigned bytes) {
-  unsigned long long pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(src),
-               "r"(bytes), "l"(pol)
-               : "memory");
+// Brings `bytes` (a multiple of 16, 16-byte aligned) into L2 ahead of use.
+// No eviction hint: at full size an evict-first line is often gone again
+// before the epilogue reads it (measured: more DRAM reads, slower stage).
+__device__ __forceinline__ void prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Orders this thread's earlier generic-proxy accesses of shared memory before
@@ -1106,10 +1103,6 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
       nx0 = nb_c(p, next, pn.coord[0], 0, c0);
       nx1 = nb_c(p, next, pn.coord[1], 1, c1);
     }
-    // the cell's FP64 state is needed only in the epilogue: ask L2 for it now
-    // (one 512-byte row per issuing thread)
-    if (MODE >= 1 && issuer) prefetch_l2_once(p.u + static_cast<size_t>(cell) * 4096 + t * 64, 512);
-    if (MODE == 2 && issuer) prefetch_l2_once(p.kref + static_cast<size_t>(cell) * 4096 + t * 64, 256);
     float u[32], r[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) r[e] = 0.f;
@@ -1175,6 +1168,11 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     }
     fence_async_smem();
     __syncthreads();
+    // the cell's FP64 state is needed only in the epilogue: ask L2 for it two
+    // directions ahead (one 512-byte row per issuing thread).  Asked for at
+    // the start of the cell, a fifth of it was evicted again before use.
+    if (MODE >= 1 && issuer) prefetch_l2(p.u + static_cast<size_t>(cell) * 4096 + t * 64, 512);
+    if (MODE == 2 && issuer) prefetch_l2(p.kref + static_cast<size_t>(cell) * 4096 + t * 64, 256);
     if (need_v3) {
       if constexpr (FACE)
         mv.issue_face(Q, nbr[5], fmaps, 2, signbit(sp[5]) ? 0 : 3, T_);  // v3 face layer
