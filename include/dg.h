@@ -267,6 +267,12 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
  * copies u and w_out back, all ordered on ``stream``.  The host buffers must
  * stay valid until the stream reaches the end of the call.  This is the
  * end-to-end form of one stage for callers whose state lives on the host.
+ * Where the 128-thread 6D kernel runs (dg_launch variant 2, FP32 sweeps, at
+ * least 2 cells along v3), the stage is pipelined over up to 8 slabs of v3
+ * cells: copies in, kernels and copies out of different slabs overlap on two
+ * handle-owned copy streams joined to ``stream`` by events; the results are
+ * bit-identical to dg_rk_stage.  Otherwise the copies and the stage run one
+ * after the other on ``stream``.
  */
 dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
                            double dt, int prec, void* stream);

@@ -156,6 +156,7 @@ cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg&
     cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
     if (e != cudaErrorNotSupported) return e;
   }
+  if (p.v3_n > 0) return cudaErrorInvalidValue;     // the generic kernels walk whole cells only
   switch (h->d) {
     case 2: return launch_cell_d2(h->n, combo, p, cfg, s);
     case 3: return launch_cell_d3(h->n, combo, p, cfg, s);
@@ -307,6 +308,10 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->vp_rho);
   cudaFree(h->vp_e);
   cudaFree(h->host_stage);
+  if (h->xfer_in) cudaStreamDestroy(h->xfer_in);
+  if (h->xfer_out) cudaStreamDestroy(h->xfer_out);
+  for (cudaEvent_t ev : h->xev)
+    if (ev) cudaEventDestroy(ev);
   for (int i = 0; i < 4; ++i) cudaFree(h->bc_tmp[i]);
   cudaFree(h->geo_c64);
   cudaFree(h->geo_c32);
@@ -1028,6 +1033,93 @@ dg_status dg_rk_stage(dg_handle h, const void* w_in, void* w_out, double* u, int
   return DG_OK;
 }
 
+// Can the host-buffer stage run slab by slab?  Only the 128-thread 6D kernel
+// walks part of a pencil (KParams::v3_lo/v3_n), and it needs 2+ v3 cells.
+bool stage_pipelines(const dg_ctx* h, int prec) {
+  return h->d == 6 && h->dx == 3 && h->n == 4 && h->uniform_sides && !h->curved &&
+         prec != DG_PREC_FP64 && h->cfg[prec].variant == 2 && h->ncell[5] >= 2 &&
+         h->kref_active == nullptr && h->ncells * 64 < (1LL << 31);
+}
+
+// The host-buffer stage as a pipeline over slabs of v3 cells (contiguous in
+// memory): slab c's copies in, its stage kernel and its copies out run on
+// three streams, so that the two copy directions and the kernels overlap.
+// Kernel c reads the stage vector of slab c and of both v3-neighbour slabs
+// (either may be upwind, the sign of the v3 speed varies with x), so the
+// stage vector's slabs are sent in the order last, 0, 1, 2, ...
+dg_status stage_host_pipelined(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
+                               double dt, int prec, double* du, void* dw_in, void* dw_out,
+                               cudaStream_t s) {
+  constexpr int kC = dg_ctx::kMaxChunks;
+  cudaError_t e;
+  if (!h->xfer_in && (e = cudaStreamCreateWithFlags(&h->xfer_in, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream");
+  if (!h->xfer_out && (e = cudaStreamCreateWithFlags(&h->xfer_out, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream");
+  for (cudaEvent_t& ev : h->xev)
+    if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "copy event");
+  const int n3 = h->ncell[5];
+  const int nch = std::min(n3, kC);
+  int lo[kC + 1];
+  for (int c = 0; c <= nch; ++c) lo[c] = static_cast<int>(static_cast<long long>(c) * n3 / nch);
+  const size_t slab_dofs = static_cast<size_t>(h->cstride[5]) * h->npc;   // DoFs per v3 cell
+  const size_t we = elem_bytes(prec);
+  cudaEvent_t ev_start = h->xev[2 * kC], ev_done = h->xev[2 * kC + 1];
+  cudaEvent_t* ev_in = h->xev;
+  cudaEvent_t* ev_k = h->xev + kC;
+  auto copy = [&](void* dst, const void* src, size_t elem, int c, cudaMemcpyKind kind,
+                  cudaStream_t st) {
+    const size_t off = static_cast<size_t>(lo[c]) * slab_dofs * elem;
+    const size_t len = static_cast<size_t>(lo[c + 1] - lo[c]) * slab_dofs * elem;
+    return cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len,
+                           kind, st);
+  };
+  if ((e = cudaEventRecord(ev_start, s)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(h->xfer_in, ev_start, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(h->xfer_out, ev_start, 0)) != cudaSuccess)
+    return cuda_fail(e, "pipeline start");
+  bool sent[kC] = {false};
+  for (int c = 0; c < nch; ++c) {
+    for (int nb : {(c + nch - 1) % nch, c, (c + 1) % nch}) {
+      if (sent[nb]) continue;
+      if ((e = copy(dw_in, w_in, we, nb, cudaMemcpyHostToDevice, h->xfer_in)) != cudaSuccess)
+        return cuda_fail(e, "host-to-device copy");
+      sent[nb] = true;
+    }
+    if ((e = copy(du, u, 8, c, cudaMemcpyHostToDevice, h->xfer_in)) != cudaSuccess ||
+        (e = cudaEventRecord(ev_in[c], h->xfer_in)) != cudaSuccess)
+      return cuda_fail(e, "host-to-device copy");
+  }
+  KParams p = base_params(h, prec);
+  p.src = dw_in;
+  p.dst = dw_out;
+  p.u = du;
+  p.mode = 1;
+  p.last_stage = stage == 4;
+  p.a_dt = stage < 4 ? kRkA[stage] * dt : kRkB[4] * dt;
+  p.b_dt = kRkB[stage] * dt;
+  for (int c = 0; c < nch; ++c) {
+    p.v3_lo = lo[c];
+    p.v3_n = lo[c + 1] - lo[c];
+    if ((e = cudaStreamWaitEvent(s, ev_in[c], 0)) != cudaSuccess)
+      return cuda_fail(e, "pipeline wait");
+    if ((e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s)) != cudaSuccess)
+      return cuda_fail(e, "stage kernel launch");
+    if ((e = cudaEventRecord(ev_k[c], s)) != cudaSuccess) return cuda_fail(e, "pipeline event");
+  }
+  for (int c = 0; c < nch; ++c) {
+    if ((e = cudaStreamWaitEvent(h->xfer_out, ev_k[c], 0)) != cudaSuccess ||
+        (e = copy(u, du, 8, c, cudaMemcpyDeviceToHost, h->xfer_out)) != cudaSuccess ||
+        (e = copy(w_out, dw_out, we, c, cudaMemcpyDeviceToHost, h->xfer_out)) != cudaSuccess)
+      return cuda_fail(e, "device-to-host copy");
+  }
+  if ((e = cudaEventRecord(ev_done, h->xfer_out)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(s, ev_done, 0)) != cudaSuccess)
+    return cuda_fail(e, "pipeline end");
+  return DG_OK;
+}
+
 dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u, int stage,
                            double dt, int prec, void* stream) {
   if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
@@ -1061,6 +1153,8 @@ dg_status dg_rk_stage_host(dg_handle h, const void* w_in, void* w_out, double* u
   void* dw_in = base + round_up(ub);
   void* dw_out = base + round_up(ub) + round_up(wb);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (stage_pipelines(h, prec))
+    return stage_host_pipelined(h, w_in, w_out, u, stage, dt, prec, du, dw_in, dw_out, s);
   if ((e = cudaMemcpyAsync(dw_in, w_in, wb, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(du, u, ub, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e, "host-to-device copy");

@@ -1011,7 +1011,8 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
   const unsigned S3 = static_cast<unsigned>(p.cstride[5]);   // pencils along v3
   const unsigned SV3 = S3 / static_cast<unsigned>(p.ncx);    // v-cell stride of v3
-  const int N3 = p.ncell[5];
+  const int N3 = p.v3_n > 0 ? p.v3_n : p.ncell[5];            // cells walked per pencil
+  const unsigned V3L = p.v3_n > 0 ? static_cast<unsigned>(p.v3_lo) : 0u;
   const unsigned npencils = S3;
   const float winv_t = ADJ ? wprod(T.winv, t) : 1.f;
   const float w_t = ADJ ? wprod(T.w, t) : 1.f;
@@ -1033,7 +1034,7 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
   int slot = 0;
   auto issue = [&](int b, unsigned c) { mv.issue(b, c, src, T_, t, h); };
   auto v3c = [&](const PencilInfo& pi, int i) {
-    return pi.fwd ? static_cast<unsigned>(i) : static_cast<unsigned>(N3 - 1 - i);
+    return V3L + (pi.fwd ? static_cast<unsigned>(i) : static_cast<unsigned>(N3 - 1 - i));
   };
   // speeds of the thread's nodes and the upwind neighbours of cell i of a pencil
   auto setup = [&](const PencilInfo& pi, int i, unsigned& cell, float (&sp)[6],
@@ -1499,6 +1500,8 @@ cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab) {
 
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
   if (p.dx != 3 || p.dv != 3 || p.ncells >= (1LL << 31)) return cudaErrorNotSupported;
+  if (p.v3_n > 0 && (cfg.variant != 2 || p.v3_lo < 0 || p.v3_lo + p.v3_n > p.ncell[5]))
+    return cudaErrorInvalidValue;                                   // v3 ranges: pair kernel only
   if (p.kref && cfg.variant != 2) return cudaErrorNotSupported;   // delta-f: pair kernel or generic
   if (cfg.variant == 2) {
     if (combo == kFFF)

@@ -84,6 +84,10 @@ struct KParams {
   double a_dt, b_dt;        // stage mode coefficients (a_s dt, b_s dt)
   int tab;                  // constant-table set of the 6D kernels (0 GL, 1 GLL)
   const float* kref;        // stage mode, delta-f form: K = kref + L(w) (nullptr: plain)
+  // 128-thread 6D kernel only: walk the v3 cells [v3_lo, v3_lo + v3_n) of
+  // every pencil (v3_n = 0: all of them); the upwind v3 neighbour of the
+  // first cell is read from the stage vector
+  int v3_lo, v3_n;
   // curved x-mesh (nullptr: affine), in the compute type: per x cell and x
   // point [ncx][n^dx][1 + dx*dx] = (|J_x|, |J_x| J_x^{-1} row-major); per x
   // cell, direction j, side (0: -1, 1: +1) and face point (the other x
@@ -220,6 +224,10 @@ struct dg_ctx {
   double* vp_e = nullptr;
   // device staging of the host-buffer stage call: u (FP64) and two stage vectors
   void* host_stage = nullptr; size_t host_stage_bytes = 0;
+  // pipelined host-buffer stage: copy streams and events (created on first use)
+  static constexpr int kMaxChunks = 8;
+  cudaStream_t xfer_in = nullptr, xfer_out = nullptr;
+  cudaEvent_t xev[2 * kMaxChunks + 2] = {};
   void* scratch = nullptr; size_t scratch_bytes = 0;
   double* partial = nullptr; int partial_blocks = 0;
   cudaStream_t capture_stream = nullptr;

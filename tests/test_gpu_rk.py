@@ -217,3 +217,33 @@ def test_bounded_wait_gives_up_and_reports_timeout():
     ref = p.apply(u.cpu().numpy())
     assert np.linalg.norm(dg.apply(u).cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
     dg.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n3", [2, 6, 10])
+def test_host_buffer_stage_pipelined_6d(prec, n3):
+    """The 6D host-buffer stage runs as a pipeline over slabs of v3 cells
+    (one slab per v3 cell up to 8, uneven slabs beyond); every slab's kernel
+    walks part of each pencil and reads the v3 neighbour of its first cell.
+    The bits equal the one-launch device stage's, for both pencil directions
+    (the v3 speed changes sign across x3 cells)."""
+    dg, p = dg_for(W.shrink(W.config_6d(), cells_x=(2, 2, 2), cells_v=(2, 2, n3)))
+    assert dg.info.uniform_sides == 1
+    rng = np.random.default_rng(n3)
+    wdt = torch.float32 if prec == 1 else torch.float64
+    u0 = torch.tensor(rng.standard_normal(dg.n_dofs))
+    w_in = torch.tensor(rng.standard_normal(dg.n_dofs)).to(wdt)
+    for stage in (0, 4):
+        du, dw_in = u0.cuda(), w_in.cuda()
+        dw_out = torch.empty_like(dw_in)
+        dg.rk_stage(dw_in, dw_out, du, stage, 0.01, prec=prec)
+        hu = u0.clone().pin_memory()
+        hw_in = w_in.clone().pin_memory()
+        hw_out = torch.empty_like(hw_in).pin_memory()
+        dg.rk_stage_host(hw_in, hw_out, hu, stage, 0.01, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(hu, du.cpu())
+        assert torch.equal(hw_out, dw_out.cpu())
+        assert not torch.equal(hu, u0)
+    dg.check()
+    dg.close()
