@@ -161,7 +161,10 @@ typedef struct {
     int order[6];             /* order in which the d directions are swept  */
     int variant;              /* 0 = generic; 6D, k = 3, FP32 sweeps: 1 = specialised,
                                  64 threads per cell; 2 = specialised, 128 threads per
-                                 cell (default)                              */
+                                 cell (default).  4D with dim_x = dim_v = 2, FP32
+                                 sweeps: 2 = specialised, n^2 threads per cell, cell
+                                 in registers (default; the adjoint, the delta-f
+                                 stage and curved meshes use the generic kernel) */
 } dg_launch;
 
 /* Library version (DG_ABI_VERSION). */

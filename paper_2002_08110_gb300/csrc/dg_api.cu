@@ -156,6 +156,10 @@ cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg&
     cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
     if (e != cudaErrorNotSupported) return e;
   }
+  if (cfg.variant == 2 && h->d == 4 && h->dx == 2 && !h->curved) {
+    cudaError_t e = launch_cell_4d(h->n, combo, p, cfg, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (p.v3_n > 0) return cudaErrorInvalidValue;     // the generic kernels walk whole cells only
   switch (h->d) {
     case 2: return launch_cell_d2(h->n, combo, p, cfg, s);
@@ -272,6 +276,7 @@ void default_cfg(dg_ctx* h) {
     c.cells_per_block = cpb;
     if (h->npc >= 1024) c.threads = 512;
     if (h->d == 6 && h->n == 4 && prec != DG_PREC_FP64) c.variant = 2;
+    if (h->d == 4 && h->dx == 2 && prec != DG_PREC_FP64) c.variant = 2;
   }
 }
 
@@ -1383,7 +1388,9 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
         (generic_smem_bytes(h->d, h->n, combo, c) != 0 || c == 1))
       cpbs.push_back(c);
   for (int variant = 0; variant < 3; ++variant) {
-    if (variant >= 1 && !(h->d == 6 && h->n == 4 && prec != DG_PREC_FP64)) continue;
+    const bool spec6 = h->d == 6 && h->n == 4 && prec != DG_PREC_FP64;
+    const bool spec4 = h->d == 4 && h->dx == 2 && prec != DG_PREC_FP64 && !h->curved;
+    if (variant >= 1 && !spec6 && !(variant == 2 && spec4)) continue;
     for (int rev = 0; rev < 2; ++rev)
       for (int t : threads_c)
         for (int c : cpbs) {
@@ -1394,7 +1401,7 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
           for (int j = 0; j < kMaxDim; ++j) cfg.order[j] = j;
           if (rev)
             for (int j = 0; j < h->d; ++j) cfg.order[j] = h->d - 1 - j;
-          // the specialised kernel fixes 64 threads per cell and its sweep order
+          // the specialised kernels fix their block shape and sweep order
           if (variant >= 1 && (c > 2 || rev || t != 128)) continue;
           cands.push_back(cfg);
         }

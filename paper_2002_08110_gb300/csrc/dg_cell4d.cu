@@ -1,0 +1,292 @@
+// Specialised 4D cell kernel (dim_x = 2, dim_v = 2) with FP32 sweeps, n = 2..6.
+//
+// It computes the same operator as the generic kernel (Algorithm 2: per
+// direction the collocated 1D operator with the upwind flux and the inverse
+// mass folded in, Gp / Gn and the lifts Lm / Lp of the tables; Sec. 3.2 /
+// Eq. 7 for the flux) but keeps every value a thread works on in registers.
+// In phase space a cell's n^4 values form an (n^2) x (n^2) matrix: a column
+// is the n^2 x values at one v node (contiguous in memory, DoF index
+// q = x1 + n x2 + n^2 (v1 + n v2)), a row the n^2 v values at one x node.
+// The x speeds depend on the v node only and the v speeds on the x node only
+// (Sec. 5.1), so
+//   phase X: thread k holds column k: both x directions are line operations
+//            on its registers with one speed each; the upwind neighbour's
+//            column (a per-thread choice, so speeds may change sign inside a
+//            cell) is read from global memory, contiguous;
+//   phase V: after an exchange through shared memory, thread k holds row k
+//            and the phase X residual of it; both v directions likewise,
+//            then the scatter or the fused LSRK stage update.
+// A block takes CPB consecutive cells, n^2 threads each.  Shared memory
+// holds the cells (padded columns: conflict-free in both phases) and the
+// phase X residuals.
+#include "dg_convert.cuh"
+#include "dg_internal.h"
+
+namespace dg {
+namespace {
+
+template <int N>
+struct Cell4 {
+  static constexpr int S = N * N;                 // values of a column or a row
+  static constexpr int NP = S * S;                // values of a cell
+  static constexpr int PAD = S + 1;               // column stride in shared memory
+  static constexpr int THREADS = N == 6 ? 256 : 128;
+  static constexpr int CPB = THREADS / S;         // cells per block
+  static constexpr int BUF = CPB * S * PAD;       // floats per shared buffer
+};
+
+// The lines of one direction over a thread's S = n^2 values v[d1 + n d2]:
+// ST = 1 runs along d1 (lines indexed by d2), ST = n along d2.  nb holds the
+// upwind neighbour's values at the same positions; c is the contravariant
+// speed (nonzero).  Positive speed: r += c (Gp u + Lm t), t the neighbour
+// below's trace at +1; negative: r += c (Gn u - Lp t), t the neighbour
+// above's trace at -1.
+template <int N, int ST>
+__device__ __forceinline__ void dir4(float (&r)[N * N], const float (&u)[N * N],
+                                     const float (&nb)[N * N], float c, const Tab1D<float>& T) {
+  const bool pos = c > 0.f;
+  float G[N * N], L[N], l[N];
+#pragma unroll
+  for (int k = 0; k < N * N; ++k) G[k] = pos ? T.Gp[k] : T.Gn[k];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    L[q] = pos ? T.Lm[q] : -T.Lp[q];
+    l[q] = pos ? T.lp[q] : T.lm[q];
+  }
+  constexpr int OT = ST == 1 ? N : 1;     // stride between the lines
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const int b = a * OT;
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < N; ++q) t = fmaf(l[q], nb[b + q * ST], t);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      float acc = L[q] * t;
+#pragma unroll
+      for (int s = 0; s < N; ++s) acc = fmaf(G[q * N + s], u[b + s * ST], acc);
+      r[b + q * ST] = fmaf(c, acc, r[b + q * ST]);
+    }
+  }
+}
+
+// A neighbour's column k (S contiguous values) into registers.
+template <int N, typename TIN>
+__device__ __forceinline__ void load_col(float (&v)[N * N], const TIN* __restrict__ src,
+                                         unsigned cell, int k) {
+  constexpr int S = N * N;
+  const TIN* col = src + static_cast<size_t>(cell) * (S * S) + static_cast<size_t>(S) * k;
+  if constexpr (sizeof(TIN) == 4 && S % 4 == 0) {
+    // 16-byte aligned: the vector is, and S * k * 4 and S * S * 4 are multiples of 16
+#pragma unroll
+    for (int i = 0; i < S / 4; ++i) {
+      const float4 x = __ldg(reinterpret_cast<const float4*>(col) + i);
+      v[4 * i] = x.x;
+      v[4 * i + 1] = x.y;
+      v[4 * i + 2] = x.z;
+      v[4 * i + 3] = x.w;
+    }
+  } else if constexpr (sizeof(TIN) == 8 && S % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(col) + i);
+      v[2 * i] = f64_to_f32(x.x);
+      v[2 * i + 1] = f64_to_f32(x.y);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < S; ++i) v[i] = cvt<float>(__ldg(col + i));
+  }
+}
+
+// A neighbour's row k (S values at stride S; consecutive threads read
+// consecutive addresses).
+template <int N, typename TIN>
+__device__ __forceinline__ void load_row(float (&v)[N * N], const TIN* __restrict__ src,
+                                         unsigned cell, int k) {
+  constexpr int S = N * N;
+  const TIN* row = src + static_cast<size_t>(cell) * (S * S) + k;
+#pragma unroll
+  for (int m = 0; m < S; ++m) v[m] = cvt<float>(__ldg(row + S * m));
+}
+
+// MODE 0: operator application (dst = K); MODE 1: fused LSRK stage.
+// Every global read is issued as early as its address is known, so that a
+// thread has several in flight: the upwind neighbours' columns before the
+// barrier that completes the gather, their rows before the exchange, the
+// FP64 state in chunks of 8 ahead of its use.
+template <int N, typename TIN, typename TW, int MODE>
+__global__ void __launch_bounds__(Cell4<N>::THREADS) k_cell4d(const KParams p) {
+  using C = Cell4<N>;
+  constexpr int S = C::S, NP = C::NP, PAD = C::PAD, CPB = C::CPB;
+  constexpr int NCH = (S + 7) / 8;       // chunks of the FP64 state of a row
+  extern __shared__ __align__(16) float sm4[];
+  float* const su = sm4;
+  float* const sr = sm4 + C::BUF;
+  const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
+  const Tab1D<float>& T = p.t32;
+  const unsigned ncells = static_cast<unsigned>(p.ncells);
+  const unsigned cell0 = blockIdx.x * static_cast<unsigned>(CPB);
+  const int nc = static_cast<int>(min(static_cast<unsigned>(CPB), ncells - cell0));
+  const int c = threadIdx.x / S;
+  const int k = threadIdx.x - c * S;     // the thread's column (phase X) and row (phase V)
+  const bool active = c < nc;
+  const unsigned cell = cell0 + static_cast<unsigned>(c);
+  unsigned co[4];                        // cell coordinates, x1 fastest
+  {
+    unsigned rem = cell;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned nj = static_cast<unsigned>(p.ncell[j]);
+      co[j] = rem % nj;
+      rem /= nj;
+    }
+  }
+  // upwind neighbour along j (periodic): below for a positive speed
+  auto upwind = [&](int j, bool pos) -> unsigned {
+    const unsigned st = static_cast<unsigned>(p.cstride[j]);
+    const unsigned nj = static_cast<unsigned>(p.ncell[j]);
+    if (pos) return co[j] == 0 ? cell + (nj - 1) * st : cell - st;
+    return co[j] == nj - 1 ? cell - (nj - 1) * st : cell + st;
+  };
+  // speeds: x directions at the v node k of the cell, v directions at its x node k
+  float c0 = 0.f, c1 = 0.f, e0 = 0.f, e1 = 0.f;
+  if (active) {
+    const unsigned cx = co[0] + static_cast<unsigned>(p.ncell[0]) * co[1];
+    const unsigned cv = co[2] + static_cast<unsigned>(p.ncell[2]) * co[3];
+    const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * S + k) * 2;
+    const float* ctv = static_cast<const float*>(p.cv_tab) + (static_cast<size_t>(cx) * S + k) * 2;
+    c0 = ctx[0];
+    c1 = ctx[1];
+    e0 = ctv[0];
+    e1 = ctv[1];
+  }
+
+  // gather the block's cells, each column padded to S + 1 floats
+#pragma unroll 4
+  for (int i = threadIdx.x; i < nc * NP; i += C::THREADS) {
+    const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
+    su[(cc * S + t) * PAD + q] = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
+  }
+  float u[S], r[S], nbA[S], nbB[S];
+  if (active) {
+    if (c0 != 0.f) load_col<N>(nbA, src, upwind(0, c0 > 0.f), k);
+    if (c1 != 0.f) load_col<N>(nbB, src, upwind(1, c1 > 0.f), k);
+  }
+  __syncthreads();
+
+  // ---- phase X: column k, directions x1, x2
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      u[q] = su[(c * S + k) * PAD + q];
+      r[q] = 0.f;
+    }
+    if (c0 != 0.f) dir4<N, 1>(r, u, nbA, c0, T);
+    if (c1 != 0.f) dir4<N, N>(r, u, nbB, c1, T);
+#pragma unroll
+    for (int q = 0; q < S; ++q) sr[(c * S + k) * PAD + q] = r[q];
+    if (e0 != 0.f) load_row<N>(nbA, src, upwind(2, e0 > 0.f), k);
+    if (e1 != 0.f) load_row<N>(nbB, src, upwind(3, e1 > 0.f), k);
+  }
+  __syncthreads();
+  if (!active) return;
+
+  // ---- phase V: row k, directions v1, v2
+  const size_t g0 = static_cast<size_t>(cell) * NP + k;
+  const double* __restrict__ uin = p.u;
+  double ua[8];
+  if constexpr (MODE == 1) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+      if (m < S) ua[m] = __ldcs(uin + g0 + static_cast<size_t>(S) * m);
+  }
+#pragma unroll
+  for (int m = 0; m < S; ++m) {
+    u[m] = su[(c * S + m) * PAD + k];
+    r[m] = sr[(c * S + m) * PAD + k];
+  }
+  if (e0 != 0.f) dir4<N, 1>(r, u, nbA, e0, T);
+  if (e1 != 0.f) dir4<N, N>(r, u, nbB, e1, T);
+
+  // ---- scatter / fused LSRK stage update (consecutive threads, consecutive DoFs)
+  TW* __restrict__ dst = static_cast<TW*>(p.dst);
+  float nanacc = 0.f;
+  if constexpr (MODE == 0) {
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+      nanacc = fmaf(r[m], 0.f, nanacc);    // stays 0 unless a value is Inf or NaN
+      __stcs(dst + g0 + static_cast<size_t>(S) * m, cvt<TW>(r[m]));
+    }
+  } else {
+    double* __restrict__ uout = p.u;
+    const float bf = static_cast<float>(p.b_dt), af = static_cast<float>(p.a_dt);
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      double ub[8];
+      if (ch + 1 < NCH) {                // the next chunk's loads go out first
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          if (8 * (ch + 1) + m < S) ub[m] = __ldcs(uin + g0 + static_cast<size_t>(S) * (8 * (ch + 1) + m));
+      }
+#pragma unroll
+      for (int mm = 0; mm < 8; ++mm) {
+        const int m = 8 * ch + mm;
+        if (m >= S) break;
+        const size_t g = g0 + static_cast<size_t>(S) * m;
+        const float K = r[m];
+        nanacc = fmaf(K, 0.f, nanacc);
+        const double un = ua[mm] + f32_to_f64_finite(bf * K);
+        __stcs(uout + g, un);
+        if constexpr (sizeof(TW) == 4)
+          __stcs(dst + g, p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(ua[mm])));
+        else
+          __stcs(dst + g, p.last_stage ? un : ua[mm] + p.a_dt * f32_to_f64(K));
+      }
+      if (ch + 1 < NCH) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) ua[m] = ub[m];
+      }
+    }
+  }
+  if (nanacc != 0.f) atomicOr(p.err, 1);
+}
+
+template <int N, typename TIN, typename TW>
+cudaError_t launch4(KParams& p, cudaStream_t s) {
+  using C = Cell4<N>;
+  const size_t smem = 2 * static_cast<size_t>(C::BUF) * sizeof(float);
+  auto kern = p.mode == 0 ? k_cell4d<N, TIN, TW, 0> : k_cell4d<N, TIN, TW, 1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const long long grid = (p.ncells + C::CPB - 1) / C::CPB;
+  kern<<<static_cast<unsigned>(grid), C::THREADS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename TIN, typename TW>
+cudaError_t launch4_n(int n, KParams& p, cudaStream_t s) {
+  switch (n) {
+    case 2: return launch4<2, TIN, TW>(p, s);
+    case 3: return launch4<3, TIN, TW>(p, s);
+    case 4: return launch4<4, TIN, TW>(p, s);
+    case 5: return launch4<5, TIN, TW>(p, s);
+    case 6: return launch4<6, TIN, TW>(p, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cell_4d(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
+  if (p.dx != 2 || p.dv != 2 || cfg.variant != 2) return cudaErrorNotSupported;
+  // not covered: the adjoint, the delta-f stage, curved meshes, partial pencils
+  if (p.adjoint || p.kref != nullptr || p.geo_c != nullptr || p.v3_n > 0) return cudaErrorNotSupported;
+  if (p.ncells >= (1LL << 31)) return cudaErrorNotSupported;   // 32-bit cell indices
+  if (combo == kFFF) return launch4_n<float, float>(n, p, s);
+  if (combo == kFDD) return launch4_n<double, double>(n, p, s);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace dg

@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
     }
 
     // step 5: scatter / fused LSRK stage update
+    const float bf = static_cast<float>(p.b_dt), af = static_cast<float>(p.a_dt);
     for (int i = threadIdx.x; i < nc * NP; i += blockDim.x) {
       TC K = sr[i];
       if (p.adjoint) K *= node_weight<D, N, TC>(T.w, i % NP);
@@ -281,11 +282,10 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
           static_cast<TW*>(p.dst)[g] = cvt<TW>(p.last_stage ? un : uo + p.a_dt * K);
         } else {
           // FP32 sweeps: one FP64 add for the state, the rest in FP32 / integer
-          const double un = uo + f32_to_f64(static_cast<float>(p.b_dt) * K);
+          const double un = uo + f32_to_f64(bf * K);
           p.u[g] = un;
           if constexpr (sizeof(TW) == 4)
-            static_cast<TW*>(p.dst)[g] =
-                p.last_stage ? f64_to_f32(un) : fmaf(static_cast<float>(p.a_dt), K, f64_to_f32(uo));
+            static_cast<TW*>(p.dst)[g] = p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(uo));
           else
             static_cast<TW*>(p.dst)[g] = p.last_stage ? un : uo + p.a_dt * f32_to_f64(K);
         }

@@ -128,6 +128,9 @@ int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int
 // Specialised 6D, n = 4, FP32-sweep kernel (dg_cell6d.cu).  Returns
 // cudaErrorNotSupported if the configuration is not covered.
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+// Specialised 4D (dim_x = dim_v = 2) FP32-sweep kernel, n = 2..6 (dg_cell4d.cu);
+// cudaErrorNotSupported if the configuration is not covered.
+cudaError_t launch_cell_4d(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
 // Uploads the n = 4 tables of the specialised kernel (they depend on n only).
 cudaError_t init_cell6d_tables(const Tab1D<float>& t, int tab);
 // A block whose bounded mbarrier wait runs out by construction (dg_cell6d.cu).
