@@ -131,8 +131,26 @@ KParams base_params(const dg_ctx* h, int prec) {
   return p;
 }
 
-// Scratch needed by the global-memory variant of the generic kernel.
+// FP32 compute with FP64 vectors on the 128-thread 6D kernel (Gauss-Legendre):
+// the input is first rounded to FP32 into the handle's in32 buffer and the
+// kernel takes its cells from there with tensor copies (the FP64-input
+// kernel loads them with plain loads, which do not overlap the sweeps).
+bool use_in32(const dg_ctx* h, int prec) {
+  return prec == DG_PREC_MIXED && h->d == 6 && h->dx == 3 && h->n == 4 && h->uniform_sides &&
+         !h->curved && h->cfg[prec].variant == 2 && h->basis != DG_BASIS_GLL &&
+         h->kref_active == nullptr && h->ncells * 64 < (1LL << 31);
+}
+
+// Scratch needed by the global-memory variant of the generic kernel, and the
+// FP32 input copy of use_in32 (both allocated outside any graph capture).
 dg_status ensure_scratch(dg_ctx* h, int prec) {
+  if (use_in32(h, prec) && h->in32 == nullptr) {
+    cudaError_t e = cudaMalloc(&h->in32, static_cast<size_t>(h->n_dofs) * sizeof(float));
+    if (e != cudaSuccess) {
+      h->in32 = nullptr;
+      return cuda_fail(e, "FP32 input buffer");
+    }
+  }
   const int combo = combo_of(prec);
   if (generic_smem_bytes(h->d, h->n, combo, 1) != 0) return DG_OK;
   const int blocks = generic_grid_blocks(h->d, h->n, h->ncells, 1, h->cfg[prec].threads);
@@ -210,7 +228,13 @@ dg_status apply_core(dg_handle h, const void* src, void* dst, int prec, cudaStre
   p.dst = dst;
   p.mode = 0;
   p.adjoint = adjoint;
-  cudaError_t e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s);
+  cudaError_t e;
+  if (use_in32(h, prec) && h->in32 != nullptr) {
+    if ((e = launch_convert(static_cast<const double*>(src), h->in32, 1, h->n_dofs, s)) != cudaSuccess)
+      return cuda_fail(e, "FP32 input copy");
+    p.src32 = h->in32;
+  }
+  e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s);
   if (e != cudaSuccess) return cuda_fail(e, "cell kernel launch");
   return DG_OK;
 }
@@ -249,7 +273,13 @@ dg_status enqueue_stage(dg_handle h, const void* w_in, void* w_out, double* u, i
   p.last_stage = stage == 4;
   p.a_dt = stage < 4 ? kRkA[stage] * dt : kRkB[4] * dt;
   p.b_dt = kRkB[stage] * dt;
-  cudaError_t e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s);
+  cudaError_t e;
+  if (use_in32(h, prec) && h->in32 != nullptr) {
+    if ((e = launch_convert(static_cast<const double*>(w_in), h->in32, 1, h->n_dofs, s)) != cudaSuccess)
+      return cuda_fail(e, "FP32 input copy");
+    p.src32 = h->in32;
+  }
+  e = launch_cell(h, combo_of(prec), p, h->cfg[prec], s);
   if (e != cudaSuccess) return cuda_fail(e, "stage kernel launch");
   return DG_OK;
 }
@@ -313,6 +343,7 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->vp_rho);
   cudaFree(h->vp_e);
   cudaFree(h->host_stage);
+  cudaFree(h->in32);
   if (h->xfer_in) cudaStreamDestroy(h->xfer_in);
   if (h->xfer_out) cudaStreamDestroy(h->xfer_out);
   for (cudaEvent_t ev : h->xev)

@@ -1376,6 +1376,36 @@ cudaError_t encode_face_maps(FaceMaps* fm, const void* src, long long ncells) {
   return cudaSuccess;
 }
 
+// FP64 vectors, FP32 sweeps, Gauss-Legendre: the cells come from p.src32 (the
+// input rounded to FP32 beforehand) by tensor copies; the output or the stage
+// vector is written in FP64 exactly as by the FP64-input kernel.
+template <bool ADJ>
+cudaError_t launch6p_in32(const KParams& p0, cudaStream_t s) {
+  KParams p = p0;
+  p.src = p0.src32;
+  if (p.ncells * 64 >= (1LL << 31)) return cudaErrorNotSupported;
+  const void* kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell6d4p<float, double, ADJ, 0, 0>)
+                                 : reinterpret_cast<const void*>(k_cell6d4p<float, double, ADJ, 1, 0>);
+  alignas(64) CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  cudaError_t e;
+  if ((e = encode_cell_map(&tm, p.src, p.ncells)) != cudaSuccess) return e;
+  const size_t smem = 1024 + (static_cast<size_t>(kNumBuf) * kCellF + 128 * 8) * sizeof(float);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const long long grid = std::min<long long>(p.cstride[5], static_cast<long long>(sms) * per_sm);
+  if ((e = cudaMemsetAsync(p.work, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  (p.mode == 0 ? k_cell6d4p<float, double, ADJ, 0, 0> : k_cell6d4p<float, double, ADJ, 1, 0>)
+      <<<static_cast<unsigned>(grid), 128, smem, s>>>(p, tm);
+  return cudaGetLastError();
+}
+
 template <typename TIN, typename TW, bool ADJ>
 cudaError_t launch6p(KParams& p, cudaStream_t s) {
   constexpr bool kF32 = sizeof(TIN) == 4;
@@ -1383,6 +1413,10 @@ cudaError_t launch6p(KParams& p, cudaStream_t s) {
   // delta-f stages: only the Gauss-Legendre FP32 kernel (else the generic one)
   if (p.kref && (!kF32 || face || p.tab != 0 || ADJ || p.mode != 1)) return cudaErrorNotSupported;
   const bool df = p.kref != nullptr;
+  if constexpr (!kF32) {
+    // FP64 input with an FP32 copy of it: the FP32-input kernel, FP64 output
+    if (p.src32 != nullptr && p.tab == 0 && !df) return launch6p_in32<ADJ>(p, s);
+  }
   // kernels: Gauss-Legendre tables; Gauss-Lobatto with FP32 input (face
   // layers); Gauss-Lobatto with FP64 input (full cells)
   const void* kern = nullptr;

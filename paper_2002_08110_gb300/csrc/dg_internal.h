@@ -88,6 +88,9 @@ struct KParams {
   // every pencil (v3_n = 0: all of them); the upwind v3 neighbour of the
   // first cell is read from the stage vector
   int v3_lo, v3_n;
+  // 128-thread 6D kernel with FP64 input (Gauss-Legendre): an FP32 copy of
+  // src (same rounding as its own loads), read by tensor copies instead
+  const float* src32;
   // curved x-mesh (nullptr: affine), in the compute type: per x cell and x
   // point [ncx][n^dx][1 + dx*dx] = (|J_x|, |J_x| J_x^{-1} row-major); per x
   // cell, direction j, side (0: -1, 1: +1) and face point (the other x
@@ -227,6 +230,7 @@ struct dg_ctx {
   double* vp_e = nullptr;
   // device staging of the host-buffer stage call: u (FP64) and two stage vectors
   void* host_stage = nullptr; size_t host_stage_bytes = 0;
+  float* in32 = nullptr;        // FP32 copy of an FP64 kernel input (n_dofs)
   // pipelined host-buffer stage: copy streams and events (created on first use)
   static constexpr int kMaxChunks = 8;
   cudaStream_t xfer_in = nullptr, xfer_out = nullptr;
