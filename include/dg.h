@@ -41,7 +41,12 @@
  *    by dg_check().
  *  - No function throws; every function returns a dg_status.  After an
  *    error, dg_last_error() gives a message (thread-local).
- *  - A handle may be used from one host thread at a time.
+ *  - A handle may be used from one host thread at a time.  Its internal
+ *    buffers (the FP32 input copy of DG_PREC_MIXED applies and stages, the
+ *    delta-f, basis-change and host-staging buffers, the copy streams of the
+ *    host-buffer stage) are shared by its calls, so calls on one handle that
+ *    run on different streams must not overlap on the GPU; use one handle
+ *    per stream for concurrent work.
  */
 #ifndef DG_H
 #define DG_H
