@@ -12,9 +12,11 @@
  * Discretisation (fixed by this library):
  *  - PDE df/dt + div(a f) = 0 on a periodic box (Sec. 1.1, Eq. intro:advection);
  *  - tensor-product polynomials of degree k, d = dim_x + dim_v (Sec. 2.3),
- *    nodal at the k+1 Gauss-Legendre points of each direction, with the same
- *    points as quadrature (collocation: diagonal mass matrix, Sec. 1.1 and
- *    Algorithm 2 step 4);
+ *    by default nodal at the k+1 Gauss-Legendre points of each direction,
+ *    with the same points as quadrature (collocation: diagonal mass matrix,
+ *    Sec. 1.1 and Algorithm 2 step 4); dg_geometry.basis selects the
+ *    Gauss-Lobatto collocation or the paper's Gauss-Lobatto nodes with
+ *    Gauss quadrature (Sec. 5.1) instead;
  *  - weak form in reference coordinates with the phase-space Jacobian
  *    J = diag(J_x, J_v) (Sec. 1.1 Eq. into:adv:ref, Sec. 3) and the upwind flux;
  *  - element-centric evaluation over all cell pairs (Algorithms 1 and 2).
