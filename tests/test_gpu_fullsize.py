@@ -4,7 +4,7 @@ invariant that holds at any size.
 
 6D: 8^6 cells, k = 3 (1.07e9 DoFs), the specialised kernel: fused LSRK stage
 (FP32 sweeps, FP32 stage vector, FP64 state), FP32 apply and FP64-I/O apply.
-4D: 16^4 cells, sheared, FP64 apply.  5D adjoint workload: L^T on a sampled
+4D: 16^4 cells, sheared, FP64 apply and the 4D kernel's FP32-sweep stage.  5D adjoint workload: L^T on a sampled
 cell against the oracle's transposed blocks.  Mass conservation of FP64 steps
 on the full 6D mesh.
 """
@@ -136,6 +136,39 @@ def test_4d_fullsize_apply_sampled():
     for e, Ke in zip(cells, K):
         got = out[e * npc:(e + 1) * npc].cpu().numpy()
         assert np.linalg.norm(got - Ke) <= 1e-12 * np.linalg.norm(Ke)
+    dg.close()
+
+
+def test_4d_fullsize_stage_fp32_sampled():
+    """The 4D kernel (the default for dim_x = dim_v = 2) at the 4D workload's
+    full size: a fused FP32-sweep stage on sampled cells."""
+    from paper_2002_08110_gb300 import DG, PREC_FP32, reference_nodes
+    w = W.config_4d()
+    zeta, _ = reference_nodes(w.k)
+    dg = DG(e_nodes=W.e_table(w, zeta), **W.dg_kwargs(w))
+    assert dg.get_launch(PREC_FP32)["variant"] == 2
+    p = oracle_for(w)
+    u = torch.tensor(W.initial_state(w, zeta), device="cuda")
+    w_in = u.float()
+    w_out = torch.empty_like(w_in)
+    uu = u.clone()
+    dt, _ = W.time_step(w)
+    stage = 3
+    dg.rk_stage(w_in, w_out, uu, stage, dt, prec=PREC_FP32)
+    dg.check()
+    npc = p.dofs_per_cell
+    cells = _sample_cells(p, 20, seed=3)
+    K, S = _oracle_cells(p, DeviceVector(w_in), cells)
+    for e, Ke, Se in zip(cells, K, S):
+        sl = slice(e * npc, (e + 1) * npc)
+        u_old = u[sl].cpu().numpy()
+        u_ref = u_old + lsrk.B[stage] * dt * Ke
+        w_ref = u_old + lsrk.A[stage] * dt * Ke
+        err_u = np.abs(uu[sl].cpu().numpy() - u_ref)
+        err_w = np.abs(w_out[sl].double().cpu().numpy() - w_ref)
+        assert np.linalg.norm(err_u) <= 1e-5 * dt * np.linalg.norm(Se) + 1e-15 * np.linalg.norm(u_old)
+        assert np.all(err_w <= 1e-5 * dt * np.abs(Se).max() + 2.5e-7 * (np.abs(u_old) + np.abs(
+            lsrk.A[stage] * dt * Ke)) + 1e-30)
     dg.close()
 
 
