@@ -170,8 +170,8 @@ typedef struct {
                                  64 threads per cell; 2 = specialised, 128 threads per
                                  cell (default).  4D with dim_x = dim_v = 2, FP32
                                  sweeps: 2 = specialised, n^2 threads per cell, cell
-                                 in registers (default; the adjoint, the delta-f
-                                 stage and curved meshes use the generic kernel) */
+                                 in registers (default; the delta-f stage and
+                                 curved meshes use the generic kernel)       */
 } dg_launch;
 
 /* Library version (DG_ABI_VERSION). */

@@ -113,12 +113,21 @@ __device__ __forceinline__ void load_row(float (&v)[N * N], const TIN* __restric
   for (int m = 0; m < S; ++m) v[m] = cvt<float>(__ldg(row + S * m));
 }
 
+// Product of the 1D weights over the two digits of position i of a column
+// or a row.
+template <int N>
+__device__ __forceinline__ float w2(const float* w, int i) {
+  return w[i % N] * w[i / N];
+}
+
 // MODE 0: operator application (dst = K); MODE 1: fused LSRK stage.
+// ADJ: the transpose L^T = M L(-a) M^{-1} (input and neighbours scaled by the
+// inverse node weights, speeds negated, output scaled by the node weights).
 // Every global read is issued as early as its address is known, so that a
 // thread has several in flight: the upwind neighbours' columns before the
 // barrier that completes the gather, their rows before the exchange, the
 // FP64 state in chunks of 8 ahead of its use.
-template <int N, typename TIN, typename TW, int MODE>
+template <int N, typename TIN, typename TW, int MODE, bool ADJ>
 __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(const KParams p) {
   using C = Cell4<N>;
   constexpr int S = C::S, NP = C::NP, PAD = C::PAD, CPB = C::CPB;
@@ -159,17 +168,19 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
     const unsigned cv = co[2] + static_cast<unsigned>(p.ncell[2]) * co[3];
     const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * S + k) * 2;
     const float* ctv = static_cast<const float*>(p.cv_tab) + (static_cast<size_t>(cx) * S + k) * 2;
-    c0 = ctx[0];
-    c1 = ctx[1];
-    e0 = ctv[0];
-    e1 = ctv[1];
+    c0 = ADJ ? -ctx[0] : ctx[0];
+    c1 = ADJ ? -ctx[1] : ctx[1];
+    e0 = ADJ ? -ctv[0] : ctv[0];
+    e1 = ADJ ? -ctv[1] : ctv[1];
   }
 
   // gather the block's cells, each column padded to S + 1 floats
 #pragma unroll 4
   for (int i = threadIdx.x; i < nc * NP; i += C::THREADS) {
     const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
-    su[(cc * S + t) * PAD + q] = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
+    float v = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
+    if (ADJ) v *= w2<N>(T.winv, q) * w2<N>(T.winv, t);
+    su[(cc * S + t) * PAD + q] = v;
   }
   float u[S], r[S], nbA[S], nbB[S];
   if (active) {
@@ -184,6 +195,15 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
     for (int q = 0; q < S; ++q) {
       u[q] = su[(c * S + k) * PAD + q];
       r[q] = 0.f;
+    }
+    if (ADJ) {                           // the neighbours' columns at the same nodes
+      const float wk = w2<N>(T.winv, k);
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const float wq = w2<N>(T.winv, q) * wk;
+        nbA[q] = c0 != 0.f ? nbA[q] * wq : 0.f;
+        nbB[q] = c1 != 0.f ? nbB[q] * wq : 0.f;
+      }
     }
     if (c0 != 0.f) dir4<N, 1>(r, u, nbA, c0, T);
     if (c1 != 0.f) dir4<N, N>(r, u, nbB, c1, T);
@@ -209,8 +229,22 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
     u[m] = su[(c * S + m) * PAD + k];
     r[m] = sr[(c * S + m) * PAD + k];
   }
+  if (ADJ) {                             // the neighbours' rows at the same nodes
+    const float wk = w2<N>(T.winv, k);
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+      const float wm = w2<N>(T.winv, m) * wk;
+      nbA[m] = e0 != 0.f ? nbA[m] * wm : 0.f;
+      nbB[m] = e1 != 0.f ? nbB[m] * wm : 0.f;
+    }
+  }
   if (e0 != 0.f) dir4<N, 1>(r, u, nbA, e0, T);
   if (e1 != 0.f) dir4<N, N>(r, u, nbB, e1, T);
+  if (ADJ) {
+    const float wk = w2<N>(T.w, k);
+#pragma unroll
+    for (int m = 0; m < S; ++m) r[m] *= w2<N>(T.w, m) * wk;
+  }
 
   // ---- scatter / fused LSRK stage update (consecutive threads, consecutive DoFs)
   TW* __restrict__ dst = static_cast<TW*>(p.dst);
@@ -259,7 +293,8 @@ template <int N, typename TIN, typename TW>
 cudaError_t launch4(KParams& p, cudaStream_t s) {
   using C = Cell4<N>;
   const size_t smem = 2 * static_cast<size_t>(C::BUF) * sizeof(float);
-  auto kern = p.mode == 0 ? k_cell4d<N, TIN, TW, 0> : k_cell4d<N, TIN, TW, 1>;
+  auto kern = p.adjoint ? (p.mode == 0 ? k_cell4d<N, TIN, TW, 0, true> : k_cell4d<N, TIN, TW, 1, true>)
+                        : (p.mode == 0 ? k_cell4d<N, TIN, TW, 0, false> : k_cell4d<N, TIN, TW, 1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -284,8 +319,8 @@ cudaError_t launch4_n(int n, KParams& p, cudaStream_t s) {
 
 cudaError_t launch_cell_4d(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s) {
   if (p.dx != 2 || p.dv != 2 || cfg.variant != 2) return cudaErrorNotSupported;
-  // not covered: the adjoint, the delta-f stage, curved meshes, partial pencils
-  if (p.adjoint || p.kref != nullptr || p.geo_c != nullptr || p.v3_n > 0) return cudaErrorNotSupported;
+  // not covered: the delta-f stage, curved meshes, partial pencils
+  if (p.kref != nullptr || p.geo_c != nullptr || p.v3_n > 0) return cudaErrorNotSupported;
   if (p.ncells >= (1LL << 31)) return cudaErrorNotSupported;   // 32-bit cell indices
   if (combo == kFFF) return launch4_n<float, float>(n, p, s);
   if (combo == kFDD) return launch4_n<double, double>(n, p, s);

@@ -117,3 +117,33 @@ def test_4d_kernel_zero_speed_lines():
     ref = p.apply(u.astype(np.float32).astype(np.float64))
     assert np.linalg.norm(out.double().cpu().numpy() - ref) <= TOL32 * np.linalg.norm(p.apply_abs(u))
     dg.close()
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[4]],
+                         ids=lambda c: f"k{c[0]}_{'x'.join(map(str, c[1]))}")
+@pytest.mark.parametrize("prec", [1, 2])
+def test_adjoint_4d_kernel(case, prec):
+    """L^T = M L(-a) M^{-1} in the 4D kernel: the transpose identity
+    <y, L x> = <L^T y, x> against the oracle's L, and agreement with the
+    generic kernel's transpose."""
+    k, cells = case
+    dg, p = _problem(k, cells, "phase")
+    rng = np.random.default_rng(40 + k)
+    dt = torch.float32 if prec == 1 else torch.float64
+    x = torch.tensor(rng.standard_normal(p.n_dofs), device="cuda", dtype=dt)
+    y = torch.tensor(rng.standard_normal(p.n_dofs), device="cuda", dtype=dt)
+    xh, yh = x.double().cpu().numpy(), y.double().cpu().numpy()
+    outs = []
+    for variant in (2, 0):
+        _set_variant(dg, prec, variant)
+        outs.append(dg.apply_adjoint(y, prec=prec).double().cpu().numpy())
+    dg.check()
+    lhs = yh @ p.apply(xh)
+    scale = np.abs(yh) @ p.apply_abs(xh)
+    for o in outs:
+        assert abs(lhs - o @ xh) <= TOL32 * scale
+    ref = p.apply_adjoint(yh)
+    nscale = np.linalg.norm(np.abs(p.assemble()).T @ np.abs(yh))
+    for o in outs:
+        assert np.linalg.norm(o - ref) <= 4 * TOL32 * nscale
+    dg.close()
