@@ -10,15 +10,15 @@
  * low-storage Runge-Kutta scheme the paper uses (Sec. 5.4).
  *
  * Discretisation (fixed by this library):
- *  - PDE df/dt + div(a f) = 0 on a periodic box (Sec. 1.1, Eq. intro:advection);
+ *  - PDE df/dt + div(a f) = 0 on a periodic box (Sec. 1.2, Eq. intro:advection);
  *  - tensor-product polynomials of degree k, d = dim_x + dim_v (Sec. 2.3),
  *    by default nodal at the k+1 Gauss-Legendre points of each direction,
  *    with the same points as quadrature (collocation: diagonal mass matrix,
- *    Sec. 1.1 and Algorithm 2 step 4); dg_geometry.basis selects the
+ *    Sec. 1.3 and Algorithm 2 step 4); dg_geometry.basis selects the
  *    Gauss-Lobatto collocation or the paper's Gauss-Lobatto nodes with
- *    Gauss quadrature (Sec. 5.1) instead;
+ *    Gauss quadrature (Sec. 1.3, 2.5) instead;
  *  - weak form in reference coordinates with the phase-space Jacobian
- *    J = diag(J_x, J_v) (Sec. 1.1 Eq. into:adv:ref, Sec. 3) and the upwind flux;
+ *    J = diag(J_x, J_v) (Sec. 1.3 Eq. into:adv:ref, Sec. 3) and the upwind flux;
  *  - element-centric evaluation over all cell pairs (Algorithms 1 and 2).
  *
  * Supported: 1 <= dim_x <= 3, 1 <= dim_v <= 3, 2 <= d <= 6, 1 <= k <= 5.
@@ -87,7 +87,7 @@ typedef enum {
     DG_FIELD_PHASE_SPACE = 1
 } dg_field_kind;
 
-/* Nodal bases of the element (Sec. 2.3, 2.5, 5.1). */
+/* Nodal bases of the element (Sec. 1.3, 2.3, 2.5, 5.3). */
 typedef enum {
     /* Nodes and quadrature at the k+1 Gauss-Legendre points (collocation,
      * diagonal mass matrix).  The default (a zero-initialised geometry). */

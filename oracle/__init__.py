@@ -13,7 +13,7 @@ finite-element library for high-dimensional partial differential equations"
 * ``quadrature``  -- 1D Gauss-Legendre / Gauss-Lobatto rules and Lagrange
   bases (Sec. 2.3 "Elements and degrees of freedom", Sec. 2.5 "Quadrature").
 * ``dg``          -- the weak form of the advection equation in reference
-  coordinates (Sec. 1.1, Eq. "into:adv:ref") with the phase-space
+  coordinates (Sec. 1.3, Eq. "into:adv:ref") with the phase-space
   block-diagonal Jacobian (Sec. 3, first display), upwind flux, element-centric
   evaluation over cell pairs (Algorithms 1 and 2), the mass matrix and its
   inverse (Algorithm 2 step 4).  Operators are written as Kronecker products of

@@ -3,15 +3,15 @@ infrastructure only -- the product path never imports this module).
 
 What is computed (arXiv 2002.08110):
 
-* PDE (Sec. 1.1, Eq. "intro:advection"): df/dt + div(a f) = 0, periodic.
-* Weak form per cell in reference coordinates (Sec. 1.1, Eq. "into:adv:ref"):
+* PDE (Sec. 1.2, Eq. "intro:advection"): df/dt + div(a f) = 0, periodic.
+* Weak form per cell in reference coordinates (Sec. 1.3, Eq. "into:adv:ref"):
       (g, |J| df/dt) - (J^{-T} grad_xi g, |J| a f) + <g, |J| n.(a f)*> = 0,
   i.e. M df/dt = A(f) with M the mass matrix.  With the phase-space Jacobian
   J = diag(J_x, J_v) (Sec. 3, first display) the integrand of the cell term is
   grad_xi g . c f with the contravariant speed c = J^{-1} a; on an affine cell
   the face term on the face xi_j = s (s = +-1) is s c_j |J| g f* (Nanson's
   formula n dS = |J| J^{-T} n_hat dS_hat).
-* Upwind numerical flux (Sec. 1.1): f* is the trace from the side the flow
+* Upwind numerical flux (Sec. 1.3): f* is the trace from the side the flow
   leaves, i.e. from this cell where s c_j > 0, from the neighbour otherwise.
 * Element-centric evaluation over all cell pairs (c_x, c_v) (Algorithm 1) and
   the cell operator of Algorithm 2: gather, interpolate to quadrature points,
@@ -44,7 +44,7 @@ from .quadrature import Tables1D
 
 
 # ---------------------------------------------------------------------------
-# velocity fields (Sec. 1.1: a = a(t, x); Sec. 6: a = (v, E(x)))
+# velocity fields (Sec. 1.2: a = a(t, x); Sec. 6: a = (v, E(x)))
 # ---------------------------------------------------------------------------
 class ConstantField:
     """a(y_x, v) = a0, constant and uniform (Sec. 5.1 experiments)."""

@@ -74,10 +74,11 @@ class Tables1D:
                  points as quadrature (collocation; mass matrix diagonal).
     basis="gll": nodal basis at the Gauss-Lobatto points with n_q = k+1
                  Gauss-Legendre quadrature (the paper's default configuration,
-                 Sec. 5.1), i.e. a non-trivial basis change.
+                 Sec. 1.3 and 2.5, kept in Sec. 5.3), i.e. a non-trivial basis
+                 change.
     basis="gllc": nodal basis at the n = k+1 Gauss-Lobatto points with the same
                  points as quadrature (the collocation variant the paper
-                 mentions as an alternative, Sec. 5.1; exact to degree 2k-1,
+                 mentions as an alternative, Sec. 2.5 and 5.3; exact to degree 2k-1,
                  mass matrix diagonal).
 
     B[q, p]  = phi_p(zeta_q)      basis at quadrature points

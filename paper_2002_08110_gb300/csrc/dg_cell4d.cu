@@ -2,13 +2,14 @@
 //
 // It computes the same operator as the generic kernel (Algorithm 2: per
 // direction the collocated 1D operator with the upwind flux and the inverse
-// mass folded in, Gp / Gn and the lifts Lm / Lp of the tables; Sec. 3.2 /
-// Eq. 7 for the flux) but keeps every value a thread works on in registers.
+// mass folded in, Gp / Gn and the lifts Lm / Lp of the tables; the weak form
+// and its upwind flux are those of Sec. 1.3, Eq. into:adv:ref) but keeps
+// every value a thread works on in registers.
 // In phase space a cell's n^4 values form an (n^2) x (n^2) matrix: a column
 // is the n^2 x values at one v node (contiguous in memory, DoF index
 // q = x1 + n x2 + n^2 (v1 + n v2)), a row the n^2 v values at one x node.
 // The x speeds depend on the v node only and the v speeds on the x node only
-// (Sec. 5.1), so
+// (the phase-space field of the Vlasov equation, Sec. 1.2 and Sec. 6), so
 //   phase X: thread k holds column k: both x directions are line operations
 //            on its registers with one speed each; the upwind neighbour's
 //            column (a per-thread choice, so speeds may change sign inside a

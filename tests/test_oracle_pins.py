@@ -553,7 +553,7 @@ def test_vp_field_uses_minus_e_and_conserves_mass():
 
 
 # ---------------------------------------------------------------------------
-# Gauss-Lobatto collocation (the paper's alternative basis, Sec. 5.1)
+# Gauss-Lobatto collocation (the paper's alternative basis, Sec. 2.5 and 5.3)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("a", [2.0, -1.5])
 def test_gllc_k1_operator_by_hand(a):
