@@ -146,7 +146,7 @@ typedef struct {
 } dg_geometry;
 
 typedef struct {
-    long long n_dofs;         /* |C| (k+1)^d  (Sec. 2.3, Eq. totalunknowns) */
+    long long n_dofs;         /* |C| (k+1)^d  (Sec. 2.3, Eq. dealii:totalunkonwns) */
     long long n_cells;        /* |C_x| |C_v|                                */
     long long n_xcells, n_vcells;
     int dofs_per_cell;        /* (k+1)^d                                    */
