@@ -38,6 +38,22 @@ BYTES_PER_DOF = {
     "apply_fp32_fp64io": 8 + 8,
     "apply_fp64": 8 + 8,
 }
+# FP32 peak of the non-tensor pipes from the unit counts and the maximum SM
+# clock: 152 SMs x 128 FP32 lanes x 2 FLOP per fused multiply-add x 2.070 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def flop_entry(dofs, ms, d, n, stage):
+    """FP32 arithmetic of one launch of an FP32-sweep kernel against the FP32
+    peak.  Per DoF and direction the folded line operator takes 2n + 5 FLOP
+    (the neighbour's trace 2, the matrix row 2n, the lift 1 and the speed 2);
+    the stage update adds 3 (the FP64 add of the state is not counted)."""
+    per_dof = d * (2 * n + 5) + (3 if stage else 0)
+    tflops = per_dof * dofs / (ms * 1e-3) / 1e12
+    return {"per_dof": per_dof, "achieved_tflops": tflops, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+            "frac": tflops / FP32_PEAK_TFLOPS,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+
 KERNEL_SOURCES = ["dg_cell6d.cu", "dg_generic.cuh", "dg_internal.h"]
 
 
@@ -558,6 +574,9 @@ def main():
             "frac": achieved / hbm_peak, "traffic": recorded_traffic(kind if args.basis == "gl" else f"{kind}_{args.basis}"),
             "peak_kind": peak_kind, "bytes_per_dof": bpd,
             "kernel": "fused LSRK stage (cell kernel, stage mode)" if kind == "stage" else "cell kernel, operator application"}
+    # the FP32 arithmetic next to the bytes (the FP64 apply runs on the FP64 pipe)
+    roof["flops"] = (flop_entry(n, avg_launch, w.dx + w.dv, w.k + 1, kind == "stage")
+                     if kind != "apply_fp64" else None)
 
     # ---- stand-alone operator applications
     variants = {}
