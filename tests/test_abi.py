@@ -104,3 +104,34 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.dg_rk_stage(None, None, None, None, 0, 0.1, 0, 0, None) == 1
     assert lib.dg_check(None, None) == 1
     assert lib.dg_destroy(None) == 0
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/dg.h compiles as strict C99 and a C program links against the
+    library and calls its host-only entry points (no GPU needed)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use_dg.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "dg.h"\n'
+        "int main(void) {\n"
+        "  double x[4], w[4], q[4], qw[4];\n"
+        "  if (dg_version() != DG_ABI_VERSION) return 1;\n"
+        "  if (dg_reference_nodes(3, x, w) != DG_OK) return 2;\n"
+        "  if (dg_basis_nodes(DG_BASIS_GLL, 3, x, q, qw) != DG_OK) return 3;\n"
+        "  if (dg_reference_nodes(9, x, w) != DG_ERR_INVALID_ARG) return 4;\n"
+        '  printf("%.15f %.15f\\n", x[0], qw[0]);\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "use_dg"
+    pkg = os.path.join(root, "paper_2002_08110_gb300")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(root, "include"), str(src), "-o", str(exe),
+                    "-L", pkg, "-ldg", "-Wl,-rpath," + pkg], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert abs(float(out[0]) + 1.0) < 1e-15          # first Gauss-Lobatto node
+    assert abs(float(out[1]) - 1.0 / 6.0) < 1e-15     # its weight for n = 4
