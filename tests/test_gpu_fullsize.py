@@ -4,8 +4,9 @@ invariant that holds at any size.
 
 6D: 8^6 cells, k = 3 (1.07e9 DoFs), the specialised kernel: fused LSRK stage
 (FP32 sweeps, FP32 stage vector, FP64 state), FP32 apply and FP64-I/O apply.
-4D: 16^4 cells, sheared, FP64 apply and the 4D kernel's FP32-sweep stage.  5D adjoint workload: L^T on a sampled
-cell against the oracle's transposed blocks.  Mass conservation of FP64 steps
+4D: 16^4 cells, sheared, FP64 apply and the 4D kernel's FP32-sweep stage.
+5D adjoint workload: L^T on a sampled cell against the oracle's transposed
+blocks.  Mass conservation of FP64 steps
 on the full 6D mesh.
 """
 import numpy as np
