@@ -94,6 +94,7 @@ class DG:
 
     # -- lifetime --------------------------------------------------------------
     def close(self):
+        """Release the handle (dg_destroy); idempotent."""
         if getattr(self, "handle", None):
             self.lib.dg_destroy(self.handle)
             self.handle = None
@@ -118,10 +119,13 @@ class DG:
         return out
 
     def set_field(self, e_nodes):
+        """Replace the phase-space field's E at the x quadrature nodes (host
+        array, layout of ``node_coordinates(2)`` by component); dg_set_field."""
         e = np.ascontiguousarray(e_nodes, dtype=np.float64).reshape(-1)
         check(self.lib.dg_set_field(self.handle, e.ctypes.data_as(_lib.c_double_p), _stream()))
 
     def empty(self, prec=PREC_FP64, device="cuda"):
+        """An uninitialised vector of n_dofs elements of the precision's type."""
         return torch.empty(self.n_dofs, dtype=_WDTYPE[prec], device=device)
 
     def _vec(self, t, prec, name):
@@ -151,6 +155,9 @@ class DG:
         return dst
 
     def rk_stage(self, w_in, w_out, u, stage, dt, prec=PREC_FP64, adjoint=False):
+        """One fused LSRK(5,4) stage (dg_rk_stage): K = L(w_in) (L^T if
+        adjoint), u += b_s dt K in FP64, w_out = u_old + a_s dt K (or u_new at
+        the last stage)."""
         check(self.lib.dg_rk_stage(self.handle, self._vec(w_in, prec, "w_in"),
                                    self._vec(w_out, prec, "w_out"),
                                    self._vec(u, PREC_FP64, "u"), int(stage), float(dt), prec,
@@ -259,12 +266,15 @@ class DG:
 
     # -- launch configuration -----------------------------------------------------
     def get_launch(self, prec):
+        """The cell-kernel launch configuration used for ``prec``."""
         c = _lib.Launch()
         check(self.lib.dg_get_launch(self.handle, prec, ctypes.byref(c)))
         return {"threads": c.threads, "cells_per_block": c.cells_per_block,
                 "order": list(c.order)[: self.dim_x + self.dim_v], "variant": c.variant}
 
     def set_launch(self, prec, threads, cells_per_block, order=None, variant=0):
+        """Set the launch configuration for ``prec`` (validated by the library;
+        captured graphs are dropped)."""
         c = _lib.Launch()
         c.threads, c.cells_per_block, c.variant = int(threads), int(cells_per_block), int(variant)
         order = list(range(self.dim_x + self.dim_v)) if order is None else list(order)
@@ -273,6 +283,8 @@ class DG:
         check(self.lib.dg_set_launch(self.handle, prec, ctypes.byref(c)))
 
     def autotune(self, src, dst, prec):
+        """Time the candidate launch configurations on apply(src, dst), keep the
+        fastest for ``prec`` and return its time in ms."""
         best = ctypes.c_double()
         check(self.lib.dg_autotune(self.handle, self._vec(src, prec, "src"),
                                    self._vec(dst, prec, "dst"), prec, _stream(), ctypes.byref(best)))
@@ -301,6 +313,7 @@ class DGBatch:
         self.tiles, self.n_dofs = int(tiles.value), int(nd.value)
 
     def close(self):
+        """Release the batch (the member handles stay open); idempotent."""
         if getattr(self, "handle", None):
             self.lib.dg_batch_destroy(self.handle)
             self.handle = None
@@ -326,13 +339,18 @@ class DGBatch:
         return U, A, B, D
 
     def rk_step(self, us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32):
+        """Advance every member's FP64 state by nsteps LSRK(5,4) steps of its
+        own dt (w0s, w1s: per-member stage vectors of the precision's type)."""
         U, A, B, D = self._arrays(us, w0s, w1s, dts, prec)
         check(self.lib.dg_batch_rk_step(self.handle, U, A, B, D, int(nsteps), prec, _stream()))
 
     def set_launch(self, tile_dofs, threads):
+        """DoFs per work tile and threads per block of the batched launch."""
         check(self.lib.dg_batch_set_launch(self.handle, int(tile_dofs), int(threads)))
 
     def autotune(self, us, w0s, w1s, dts, prec=PREC_FP32):
+        """Time tile sizes x block sizes on one step, keep the fastest and
+        return its time per step in ms (the states are advanced by the trials)."""
         U, A, B, D = self._arrays(us, w0s, w1s, dts, prec)
         best = ctypes.c_double()
         check(self.lib.dg_batch_autotune(self.handle, U, A, B, D, prec, _stream(),
@@ -340,4 +358,5 @@ class DGBatch:
         return float(best.value)
 
     def check(self):
+        """Synchronise and raise DGError if a batched kernel saw NaN/Inf."""
         check(self.lib.dg_batch_check(self.handle, _stream()))

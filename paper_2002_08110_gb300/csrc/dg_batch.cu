@@ -556,9 +556,9 @@ dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void*
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // time one step per candidate on scratch copies: the caller's u is
-  // advanced, so the tuner runs on the caller's buffers (their contents
-  // change; documented in the header)
+  // time two steps per candidate (after one untimed step that captures its
+  // graphs) on the caller's buffers: their contents are advanced, as the
+  // header states
   for (int tdofs : tiles_c)
     for (int th : threads_c) {
       if (dg_batch_set_launch(b, tdofs, th) != DG_OK) continue;
