@@ -22,6 +22,7 @@ c_double_p = ctypes.POINTER(ctypes.c_double)
 
 
 class Geometry(ctypes.Structure):
+    """dg_geometry of include/dg.h (field, box, shear, basis, deformation)."""
     _fields_ = [("x_lo", ctypes.c_double * 3), ("x_hi", ctypes.c_double * 3),
                 ("v_lo", ctypes.c_double * 3), ("v_hi", ctypes.c_double * 3),
                 ("shear_x", ctypes.c_double * 9), ("field_kind", ctypes.c_int),
@@ -30,6 +31,7 @@ class Geometry(ctypes.Structure):
 
 
 class Info(ctypes.Structure):
+    """dg_info_t of include/dg.h (sizes and properties of a handle)."""
     _fields_ = [("n_dofs", ctypes.c_longlong), ("n_cells", ctypes.c_longlong),
                 ("n_xcells", ctypes.c_longlong), ("n_vcells", ctypes.c_longlong),
                 ("dofs_per_cell", ctypes.c_int), ("dim_x", ctypes.c_int), ("dim_v", ctypes.c_int),
@@ -39,11 +41,13 @@ class Info(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
+    """dg_launch of include/dg.h (cell-kernel launch configuration)."""
     _fields_ = [("threads", ctypes.c_int), ("cells_per_block", ctypes.c_int),
                 ("order", ctypes.c_int * 6), ("variant", ctypes.c_int)]
 
 
 class DGError(RuntimeError):
+    """A dg_status other than DG_OK, with the library's last error message."""
     def __init__(self, status, message):
         self.status = status
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -112,6 +116,7 @@ def load():
 
 
 def check(status):
+    """Raise DGError unless status is DG_OK."""
     if status != DG_OK:
         msg = load().dg_last_error()
         raise DGError(status, msg.decode() if msg else "")

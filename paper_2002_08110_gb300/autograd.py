@@ -26,12 +26,16 @@ from ._lib import PREC_FP32, PREC_FP64  # noqa: F401
 
 
 class CheckpointMismatch(RuntimeError):
-    pass
+    """A recomputed segment did not end on the stored checkpoint bit for bit."""
 
 
 class RKForward(torch.autograd.Function):
+    """u(T) = Phi^nsteps(u0) with a checkpointed adjoint backward (module doc)."""
+
     @staticmethod
     def forward(ctx, u0, dg, dt, nsteps, prec, checkpoint_every):
+        """nsteps LSRK(5,4) steps of the handle ``dg``; keeps every
+        ``checkpoint_every``-th state for the backward."""
         if checkpoint_every < 1:
             raise ValueError("checkpoint_every must be >= 1")
         u = u0.detach().to(torch.float64).contiguous().clone()
@@ -54,6 +58,8 @@ class RKForward(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_out):
+        """Phi^T applied nsteps times to grad_out, segment by segment in
+        reverse, each segment recomputed from its checkpoint and checked."""
         dg, dt, prec, every = ctx.dg, ctx.dt, ctx.prec, ctx.every
         lam = grad_out.detach().to(torch.float64).contiguous().clone()
         wdt = torch.float32 if prec == PREC_FP32 else torch.float64
