@@ -685,3 +685,256 @@ def test_curved_consistency_two_x_directions():
         errs.append(math.sqrt(diff @ (p.mass_diagonal() * diff)))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert rates[-1] > k - 0.5, rates
+
+
+# ---------------------------------------------------------------------------
+# the term scale |L| |u| (``Problem.apply_abs``): the yardstick of every
+# reduced-precision parity test.  The weak form (Sec. 1.3, Eq. into:adv:ref)
+# evaluated with the absolute value of every factor and term.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("a", [(1.0, 0.5), (-0.7, 0.3), (0.4, -1.2)])
+def test_term_scale_k0_closed_form(a):
+    """k = 0 (first-order upwind finite volumes): the operator is
+    -a_j (u_i - u_up) / h_j per direction, whose terms in absolute value are
+    |a_j| (|u_i| + |u_up|) / h_j -- no volume term (the derivative of a
+    constant is zero), the outflow trace and the upwind neighbour's trace."""
+    nx, nv = 5, 4
+    p = Problem(1, 1, 0, (nx,), (nv,), (0,), (2,), (0,), (1,), ConstantField(a))
+    U = np.random.default_rng(13).standard_normal(p.n_dofs).reshape(nv, nx)
+    h = (2.0 / nx, 1.0 / nv)
+    ref = np.zeros_like(U)
+    for axis, aj, hj in ((1, a[0], h[0]), (0, a[1], h[1])):
+        up = np.roll(U, 1 if aj > 0 else -1, axis=axis)
+        ref += abs(aj) / hj * (np.abs(U) + np.abs(up))
+    got = p.apply_abs(U.reshape(-1))
+    np.testing.assert_allclose(got, ref.reshape(-1), rtol=1e-14, atol=0)
+
+
+def _lagrange_1d_by_fit(nodes, x):
+    """Values and derivatives at x of the Lagrange polynomials through
+    ``nodes``, by monomial fits of the unit vectors (independent of the
+    oracle's product formulas)."""
+    n = len(nodes)
+    V = np.zeros((len(x), n))
+    D = np.zeros((len(x), n))
+    for p_ in range(n):
+        c = P.polyfit(nodes, np.eye(n)[p_], n - 1)
+        V[:, p_] = P.polyval(x, c)
+        D[:, p_] = P.polyval(x, P.polyder(c))
+    return V, D
+
+
+def _term_scale_dense(p, u):
+    """|M^{-1}| sum over terms |T_t| |u| with every term of the weak form as a
+    dense Kronecker matrix (cell terms per direction, outflow-face terms and
+    upwind-neighbour face terms per face), built from independently fitted
+    1D tables.  Collocation bases only (M diagonal)."""
+    d, n = p.d, p.n
+    zeta, wq = (npleg.leggauss(n) if p.basis == "gl" else gauss_lobatto(n))
+    B, Bd = _lagrange_1d_by_fit(zeta, zeta)
+    lp, _ = _lagrange_1d_by_fit(zeta, np.array([1.0]))
+    lm, _ = _lagrange_1d_by_fit(zeta, np.array([-1.0]))
+
+    def kron(mats):
+        K = np.ones((1, 1))
+        for M in mats:
+            K = np.kron(M, K)
+        return K
+
+    def weights(ws):
+        return kron([np.asarray(w_)[:, None] for w_ in ws])[:, 0]
+
+    npc = n ** d
+    out = np.zeros(p.n_dofs)
+    aB, aBd = np.abs(B), np.abs(Bd)
+    for e in range(p.ncells):
+        cc = (e // p.strides) % p.cells
+        # physical points of the cell: speeds c = J^{-1} a from the field
+        def speeds(pts):
+            axes = [p.lo[j] + p.h[j] * (cc[j] + (np.asarray(pts[j]) + 1) / 2) for j in range(d)]
+            Y = np.stack(np.meshgrid(*axes, indexing="ij"), -1)
+            a = p.field(Y[..., :p.dx], Y[..., p.dx:])
+            return (a @ np.linalg.inv(p.J).T).reshape(-1, d, order="F")
+        detJ = abs(np.linalg.det(p.J))
+        ue = np.abs(u[e * npc:(e + 1) * npc])
+        acc = np.zeros(npc)
+        Wc = weights([wq] * d)
+        C = speeds([zeta] * d)
+        for j in range(d):
+            Kd = kron([aBd if m == j else aB for m in range(d)])
+            acc += Kd.T @ (Wc * detJ * np.abs(C[:, j]) * (kron([aB] * d) @ ue))
+        for j in range(d):
+            for s in (1, -1):
+                ls, lo = (lp, lm) if s > 0 else (lm, lp)
+                pts = [zeta] * d
+                pts[j] = np.array([float(s)])
+                cj = speeds(pts)[:, j]
+                wf = weights([np.ones(1) if m == j else wq for m in range(d)])
+                Ts = kron([np.abs(ls) if m == j else aB for m in range(d)])
+                To = kron([np.abs(lo) if m == j else aB for m in range(d)])
+                nb = (e + 0)
+                cn = cc.copy()
+                cn[j] = (cn[j] + s) % p.cells[j]
+                nb = int(np.sum(cn * p.strides))
+                un = np.abs(u[nb * npc:(nb + 1) * npc])
+                own = (s * cj > 0)
+                acc += Ts.T @ (wf * detJ * np.abs(cj) * np.where(own, Ts @ ue, To @ un))
+        out[e * npc:(e + 1) * npc] = acc / (Wc * detJ)
+    return out
+
+
+def _term_scale_problems():
+    rng = np.random.default_rng(21)
+    out = []
+    for dx, dv, k, cells, kind, basis in [
+            (1, 1, 3, (3, 2), "const", "gl"), (1, 1, 2, (2, 3), "phase", "gllc"),
+            (2, 1, 2, (2, 1, 3), "const", "gl"), (1, 2, 1, (2, 2, 1), "phase", "gl"),
+            (2, 2, 1, (2, 1, 2, 1), "phase", "gl"), (1, 2, 3, (1, 2, 2), "phase", "gllc")]:
+        d = dx + dv
+        if kind == "const":
+            field = ConstantField(rng.uniform(-1, 1, d))
+        else:
+            amp = rng.uniform(0.3, 1, dv)
+            field = PhaseSpaceField(dx, dv, lambda y, amp=amp: amp * np.sin(
+                2 * np.pi * y.sum(-1, keepdims=True) + 0.3))
+        shear = None if dx == 1 else np.eye(dx) + 0.1 * np.eye(dx, k=1)
+        out.append(Problem(dx, dv, k, cells[:dx], cells[dx:], [0] * dx, [1] * dx, [-1] * dv,
+                           [1.5] * dv, field, shear=shear, basis=basis))
+    return out
+
+
+@pytest.mark.parametrize("p", _term_scale_problems(), ids=lambda p: f"{p.dx}x{p.dv}v_k{p.k}_{p.basis}")
+def test_term_scale_equals_termwise_dense_route(p):
+    """apply_abs (axis-wise sums) equals the same terms as dense Kronecker
+    matrices from independently fitted 1D tables: a term dropped, counted
+    twice, or taken from the wrong side fails."""
+    u = np.random.default_rng(22).standard_normal(p.n_dofs)
+    got = p.apply_abs(u)
+    ref = _term_scale_dense(p, u)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("p", _term_scale_problems(), ids=lambda p: f"{p.dx}x{p.dv}v_k{p.k}_{p.basis}")
+def test_term_scale_bounds_the_assembled_operator(p):
+    """|L| |u| <= apply_abs(u) row by row (the triangle inequality over the
+    terms that the assembled entries of L sum), and the bound is not loose by
+    more than the cancellation inside the collocated 1D operators: every row
+    sum of the scale stays within a factor 4 of |L| |u|."""
+    L = p.assemble()
+    u = np.random.default_rng(23).standard_normal(p.n_dofs)
+    lo = abs(L) @ np.abs(u)
+    hi = p.apply_abs(u)
+    assert np.all(lo <= hi * (1 + 1e-12))
+    assert np.all(hi <= 4 * lo)
+
+
+# ---------------------------------------------------------------------------
+# integrals with the cell quadrature (``Problem.integrals``; Sec. 2.5, the
+# tensor-product rules, and Sec. 1.3, the |J| of the reference map)
+# ---------------------------------------------------------------------------
+def _poly_integral(coef, lo, hi):
+    ci = P.polyint(coef)
+    return P.polyval(hi, ci) - P.polyval(lo, ci)
+
+
+@pytest.mark.parametrize("basis", ["gl", "gll", "gllc"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_integrals_of_polynomials_exact(basis, k):
+    """u = prod_j p_j(y_j), each p_j of degree k (gllc: k - 1 for the square)
+    on a sheared 2x + 1v box.  The nodal interpolant is u itself, and the
+    rule integrates degree 2k+1 (Gauss) or 2k-1 (Lobatto) exactly, so
+    int u = det(S) prod_j int p_j and int u^2 = det(S) prod_j int p_j^2 to
+    round-off; max |u| is the largest nodal value."""
+    rng = np.random.default_rng(31 + k)
+    dx, dv = 2, 1
+    S = np.array([[1.0, 0.1], [0.0, 1.0]]) * np.array([[1.0], [1.3]])   # det = 1.3
+    lo, hi = np.array([0.0, 0.5, -1.0]), np.array([1.0, 2.0, 1.5])
+    p = Problem(dx, dv, k, (3, 2), (2,), lo[:2], hi[:2], lo[2:], hi[2:],
+                ConstantField([1.0, 1.0, 1.0]), shear=S, basis=basis)
+    for deg, check_sq in ((k, basis != "gllc"), (k - 1, True)):
+        coefs = [rng.standard_normal(deg + 1) for _ in range(3)]
+
+        def f(yx, v):
+            return (P.polyval(yx[..., 0], coefs[0]) * P.polyval(yx[..., 1], coefs[1])
+                    * P.polyval(v[..., 0], coefs[2]))
+        u = p.interpolate(f)
+        mass, l2, umax = p.integrals(u)
+        ex_mass = np.linalg.det(S) * np.prod([_poly_integral(c, a, b)
+                                              for c, a, b in zip(coefs, lo, hi)])
+        assert abs(mass - ex_mass) <= 1e-12 * max(1.0, abs(ex_mass))
+        if check_sq:
+            ex_l2 = np.linalg.det(S) * np.prod([_poly_integral(P.polymul(c, c), a, b)
+                                                for c, a, b in zip(coefs, lo, hi)])
+            assert abs(l2 - ex_l2) <= 1e-12 * ex_l2
+        assert umax == np.max(np.abs(u))
+
+
+def test_integrals_of_squared_sines_exact():
+    """sin^2(2 pi y1) sin^2(2 pi y2) sin^2(2 pi v) = (1 - cos 4 pi y)/2 per
+    factor: on N >= 3 cells per period the composite Gauss rule sums each
+    cosine to zero (roots of unity), so int u^2 over the sheared box is
+    det(S) |box| / 8 and int u = 0 exactly.  A missing |J| factor, a wrong
+    weight or the wrong cell size fails."""
+    S = np.array([[1.0, 0.2], [0.0, 0.8]])
+    p = Problem(2, 1, 3, (3, 4), (5,), (0.0, 0.0), (1.0, 1.0), (-1.0,), (1.0,),
+                ConstantField([1.0, 1.0, 1.0]), shear=S)
+    u = p.interpolate(lambda yx, v: np.sin(2 * np.pi * yx[..., 0]) * np.sin(2 * np.pi * yx[..., 1])
+                      * np.sin(2 * np.pi * v[..., 0]))
+    mass, l2, _ = p.integrals(u)
+    vol = np.linalg.det(S) * 1.0 * 1.0 * 2.0
+    assert abs(mass) <= 1e-14
+    assert abs(l2 - vol / 8) <= 1e-13
+
+
+@pytest.mark.parametrize("basis", ["gl", "gllc"])
+def test_integrals_curved_mesh_volume(basis):
+    """The periodic deformation maps the lattice onto itself, so the physical
+    volume is the lattice volume: int 1 = |box| and int p(v) = |box_x| int p
+    exactly (the cos(2 pi y) term of |J_x| sums to zero over N >= 2 cells).
+    A missing per-point |J_x| (or one taken at the wrong point) fails."""
+    rng = np.random.default_rng(41)
+    p = Problem(2, 1, 2, (3, 2), (2,), (0.0, 0.0), (1.0, 2.0), (-1.0,), (1.0,),
+                ConstantField([1.0, 1.0, 1.0]), basis=basis, deform=[0.3, -0.25])
+    c = rng.standard_normal(2)                  # degree 1 in v: exact in both rules
+    mass1, _, _ = p.integrals(np.ones(p.n_dofs))
+    assert abs(mass1 - 2.0 * 2.0) <= 1e-13
+    u = p.interpolate(lambda yx, v: P.polyval(v[..., 0], c) + 0 * yx[..., 0])
+    mass, _, _ = p.integrals(u)
+    assert abs(mass - 2.0 * _poly_integral(c, -1.0, 1.0)) <= 1e-13
+    # and the |J_x| really varies on this mesh (the pin would be vacuous otherwise)
+    _, dj = p.jacobian(0, [p.T.zeta] * 3)
+    assert np.ptp(dj) > 0.1 * np.mean(dj)
+
+
+@pytest.mark.parametrize("mistake", ["no_volume", "no_faces", "own_trace_on_inflow",
+                                     "no_jacobian", "unit_weights"])
+def test_term_scale_and_integral_pins_catch_planted_mistakes(mistake, monkeypatch):
+    """Each mistake planted in the oracle (on the CPU) fails at least one of
+    the pins above: the term scale against the dense route and the bounds,
+    or the integrals against the closed forms."""
+    p = _term_scale_problems()[2]
+    u = np.random.default_rng(24).standard_normal(p.n_dofs)
+    dense = _term_scale_dense(p, u)
+    lo = abs(p.assemble()) @ np.abs(u)
+    q = Problem(1, 1, 3, (3,), (2,), (0.0,), (1.0,), (-1.0,), (1.0,), ConstantField([1.0, 1.0]))
+    cx, cv = np.array([0.3, -1.0, 0.5, 0.2]), np.array([1.0, 0.4, -0.7, 0.1])
+    uq = q.interpolate(lambda yx, v: P.polyval(yx[..., 0], cx) * P.polyval(v[..., 0], cv))
+    ex = _poly_integral(cx, 0.0, 1.0) * _poly_integral(cv, -1.0, 1.0)
+    if mistake == "no_volume":
+        monkeypatch.setattr(p.T, "Bd", np.zeros_like(p.T.Bd))
+    elif mistake == "no_faces":
+        monkeypatch.setattr(p, "_face_trace_abs", lambda U, j, l: np.zeros_like(
+            np.take(U, [0], axis=j)))
+    elif mistake == "own_trace_on_inflow":
+        monkeypatch.setattr(p, "neighbour", lambda cell, j, s: cell)
+    elif mistake == "no_jacobian":
+        monkeypatch.setattr(p, "_detJ", lambda cell, pts: 1.0)
+        monkeypatch.setattr(q, "_detJ", lambda cell, pts: 1.0)
+    else:
+        monkeypatch.setattr(p.T, "w", np.ones_like(p.T.w))
+        monkeypatch.setattr(q.T, "w", np.ones_like(q.T.w))
+    hi = p.apply_abs(u)
+    scale_ok = (np.allclose(hi, dense, rtol=1e-12, atol=0) and np.all(lo <= hi * (1 + 1e-12))
+                and np.all(hi <= 4 * lo))
+    integral_ok = abs(q.integrals(uq)[0] - ex) <= 1e-12
+    assert not (scale_ok and integral_ok), mistake
