@@ -63,3 +63,23 @@ def random_problem(dx, dv, k, cells, kind, seed=0, shear=None):
     dg = DG(dx, dv, k, cells[:dx], cells[dx:], x_lo, x_hi, v_lo, v_hi, field_kind=1,
             e_nodes=e_table_from_oracle(p, E), shear=shear)
     return dg, p
+
+
+def assert_term_scale(got, ref, scale, tol, floor=1e-300, what=""):
+    """Element by element: |got_i - ref_i| <= tol * scale_i + floor, where
+    scale is the term scale of each entry (the oracle's evaluation with the
+    absolute value of every factor, ``Problem.apply_abs``): rounding errors
+    of an entry scale with the terms that entry sums, not with the entry or
+    the norm of the whole vector.  Reports the worst entry on failure."""
+    got = np.asarray(got, dtype=np.float64).reshape(-1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1)
+    scale = np.abs(np.asarray(scale, dtype=np.float64)).reshape(-1)
+    err = np.abs(got - ref)
+    bound = tol * scale + floor
+    bad = err > bound
+    if np.any(bad):
+        i = int(np.argmax(err / bound))
+        raise AssertionError(
+            f"{what}: {int(bad.sum())} of {err.size} entries exceed tol {tol:g} x term scale; "
+            f"worst index {i}: |err| {err[i]:.3e}, scale {scale[i]:.3e}, ratio "
+            f"{err[i] / max(scale[i], 1e-300):.3e}")

@@ -3,18 +3,18 @@
 Every (d, k) the library supports, every precision, the adjoint, with
 ragged meshes that span several blocks and include directions with one and
 two cells (the periodic neighbour is the cell itself or the same cell on
-both sides).  Tolerances (stated per apply):
-  FP64:             ||K - K_ref|| / ||K_ref|| <= 1e-12
-  FP32 / mixed:     ||K - K_ref|| / || |L| |u| || <= 1e-5   (term scale: the
-                    oracle's evaluation with the absolute value of every
-                    factor; rounding errors scale with it, not with K)
+both sides).  Tolerances (stated per apply), element by element against the
+term scale S = |L| |u| (the oracle's evaluation with the absolute value of
+every factor; rounding errors of an entry scale with the terms it sums):
+  FP64:             |K_i - K_ref,i| <= 1e-12 S_i, and ||K - K_ref|| <= 1e-12 ||K_ref||
+  FP32 / mixed:     |K_i - K_ref,i| <= 1e-5 S_i
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
-from dg_helpers import random_problem  # noqa: E402
+from dg_helpers import assert_term_scale, random_problem  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -63,11 +63,12 @@ def test_apply_parity(case, kind, prec):
     dg, p = random_problem(dx, dv, k, cells, kind, shear=shear)
     u, out = _run(dg, p, prec, adjoint=False)
     ref = p.apply(u)
+    scale = p.apply_abs(u)
     if prec == 0:
         assert np.linalg.norm(out - ref) <= TOL64 * np.linalg.norm(ref)
+        assert_term_scale(out, ref, scale, TOL64, what="fp64 apply")
     else:
-        scale = np.linalg.norm(p.apply_abs(u))
-        assert np.linalg.norm(out - ref) <= TOL32 * scale
+        assert_term_scale(out, ref, scale, TOL32, what=f"prec {prec} apply")
     dg.close()
 
 
@@ -85,13 +86,14 @@ def test_adjoint_parity(case, kind, prec):
     dg, p = random_problem(dx, dv, k, cells, kind, seed=3, shear=shear)
     y, out = _run(dg, p, prec, adjoint=True, seed=4)
     ref = p.apply_adjoint(y)
+    # term scale of the transpose: M |L(-a)| M^{-1} |y| (L^T = M L(-a) M^{-1})
+    Md = p.mass_diagonal()
+    scale = Md * p.with_field(p.field.negated()).apply_abs(np.abs(y) / Md)
     if prec == 0:
         assert np.linalg.norm(out - ref) <= TOL64 * np.linalg.norm(ref)
+        assert_term_scale(out, ref, scale, TOL64, what="fp64 adjoint")
     else:
-        # term scale of the transpose: |L^T| |y| <= sum of the transposed |blocks|
-        L = p.assemble()
-        scale = np.linalg.norm(abs(L).T @ np.abs(y))
-        assert np.linalg.norm(out - ref) <= 4 * TOL32 * scale
+        assert_term_scale(out, ref, scale, TOL32, what=f"prec {prec} adjoint")
     dg.close()
 
 
@@ -149,13 +151,15 @@ def test_specialised_6d_kernel_matches_generic(prec, adjoint):
                 err, scale = _dot_identity(dg, p, prec, seed=10 + variant)
                 assert err <= TOL32 * scale, name
         dg.check()
-        scale = np.linalg.norm(p.apply_abs(uin))
-        if not adjoint:
+        if adjoint:
+            Md = p.mass_diagonal()
+            scale = Md * p.with_field(p.field.negated()).apply_abs(np.abs(uin) / Md)
+            ref = Md * p.with_field(p.field.negated()).apply(uin / Md)
+        else:
+            scale = p.apply_abs(uin)
             ref = p.apply(uin)
-            for o in outs:
-                assert np.linalg.norm(o - ref) <= TOL32 * scale, name
-        for o in outs[1:]:
-            assert np.linalg.norm(outs[0] - o) <= 4 * TOL32 * scale, name
+        for v, o in enumerate(outs):
+            assert_term_scale(o, ref, scale, TOL32, what=f"{name} variant {v}")
         dg.close()
 
 
@@ -166,8 +170,9 @@ def test_sign_change_inside_cells_uses_generic_path():
     assert dg.info.uniform_sides == 0
     u = np.random.default_rng(1).standard_normal(p.n_dofs)
     out = dg.apply(torch.tensor(u, device="cuda", dtype=torch.float32), prec=1)
-    ref = p.apply(u.astype(np.float32).astype(np.float64))
-    assert np.linalg.norm(out.double().cpu().numpy() - ref) <= TOL32 * np.linalg.norm(p.apply_abs(u))
+    uin = u.astype(np.float32).astype(np.float64)
+    assert_term_scale(out.double().cpu().numpy(), p.apply(uin), p.apply_abs(uin), TOL32,
+                      what="sign change inside cells")
     dg.close()
 
 
@@ -208,3 +213,4 @@ def test_zero_velocity_gives_exact_zero(cells):
     dg.check()
     assert torch.equal(uu, u)
     dg.close()
+

@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 from oracle import lsrk  # noqa: E402
 from oracle import vp as ovp  # noqa: E402
 from oracle.dg import ConstantField, PhaseSpaceField, Problem  # noqa: E402
+from dg_helpers import assert_term_scale  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -85,10 +86,11 @@ def test_gll_collocation_apply(case, kind):
     ref = p.apply(u)
     out = dg.apply(torch.tensor(u, device="cuda")).cpu().numpy()
     assert np.linalg.norm(out - ref) <= TOL64 * np.linalg.norm(ref)
+    assert_term_scale(out, ref, p.apply_abs(u), TOL64, what="gllc fp64")
     u32 = torch.tensor(u, device="cuda", dtype=torch.float32)
     uin = u32.double().cpu().numpy()
     out32 = dg.apply(u32, prec=1).double().cpu().numpy()
-    assert np.linalg.norm(out32 - p.apply(uin)) <= TOL32 * np.linalg.norm(p.apply_abs(uin))
+    assert_term_scale(out32, p.apply(uin), p.apply_abs(uin), TOL32, what="gllc fp32")
     dg.check()
     dg.close()
 
@@ -104,11 +106,11 @@ def test_gll_collocation_6d_kernels(prec):
     ut = torch.tensor(u, device="cuda", dtype=dt)
     uin = ut.double().cpu().numpy()
     ref = p.apply(uin)
-    scale = np.linalg.norm(p.apply_abs(uin))
+    scale = p.apply_abs(uin)
     for variant in (0, 1, 2):
         dg.set_launch(prec, threads=256, cells_per_block=1, variant=variant)
         out = dg.apply(ut, prec=prec).double().cpu().numpy()
-        assert np.linalg.norm(out - ref) <= TOL32 * scale, variant
+        assert_term_scale(out, ref, scale, TOL32, what=f"variant {variant}")
     dg.check()
     dg.close()
 
@@ -130,8 +132,8 @@ def test_gll_collocation_6d_adjoint():
     yy = np.abs(y.double().cpu().numpy())
     scale = Md * p.with_field(p.field.negated()).apply_abs(yy / Md)
     ref = Md * p.with_field(p.field.negated()).apply(y.double().cpu().numpy() / Md)
-    for o in outs:
-        assert np.linalg.norm(o - ref) <= TOL32 * np.linalg.norm(scale)
+    for v, o in enumerate(outs):
+        assert_term_scale(o, ref, scale, TOL32, what=f"adjoint variant {v}")
     dg.close()
 
 
@@ -243,10 +245,14 @@ def test_gll_6d_workload_keeps_the_specialised_kernel():
     u = W.separable_state(w, nodes, xp=torch, device="cuda").float()
     uin = u.double().cpu().numpy()
     ref = p.apply(uin)
-    scale = np.linalg.norm(p.apply_abs(uin))
+    scale = p.apply_abs(uin)
+    # speeds below 1e-12 of a cell's largest carry no flux in the FP32 tables:
+    # entries whose every term comes from such speeds (v = 0 and x at a zero
+    # of E) are exact only to that level, an absolute floor far below FP32
+    floor = 1e-12 * np.max(np.abs(scale))
     for variant in (0, 2):
         dg.set_launch(1, threads=256, cells_per_block=1, variant=variant)
         out = dg.apply(u, prec=1).double().cpu().numpy()
-        assert np.linalg.norm(out - ref) <= TOL32 * scale, variant
+        assert_term_scale(out, ref, scale, TOL32, floor=floor, what=f"6d gllc variant {variant}")
     dg.check()
     dg.close()

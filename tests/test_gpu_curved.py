@@ -8,6 +8,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import lsrk  # noqa: E402
 from oracle.dg import ConstantField, PhaseSpaceField, Problem  # noqa: E402
+from dg_helpers import assert_term_scale  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -71,11 +72,12 @@ def test_curved_apply(case, kind):
     ref = p.apply(u)
     out = dg.apply(torch.tensor(u, device="cuda")).cpu().numpy()
     assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert_term_scale(out, ref, p.apply_abs(u), 1e-12, what="curved fp64")
     for prec in (1, 2):
         x = torch.tensor(u, device="cuda", dtype=torch.float32 if prec == 1 else torch.float64)
         uin = x.double().cpu().numpy()
         o = dg.apply(x, prec=prec).double().cpu().numpy()
-        assert np.linalg.norm(o - p.apply(uin)) <= 1e-5 * np.linalg.norm(p.apply_abs(uin)), prec
+        assert_term_scale(o, p.apply(uin), p.apply_abs(uin), 1e-5, what=f"curved prec {prec}")
     dg.check()
     dg.close()
 
@@ -86,6 +88,7 @@ def test_curved_gll_collocation_apply():
     ref = p.apply(u)
     out = dg.apply(torch.tensor(u, device="cuda")).cpu().numpy()
     assert np.linalg.norm(out - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert_term_scale(out, ref, p.apply_abs(u), 1e-12, what="curved gllc fp64")
     dg.close()
 
 
