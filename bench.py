@@ -193,78 +193,98 @@ def barrier(world):
 
 
 # ---------------------------------------------------------------------------
-# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# the CPU oracle (cpu_baseline and the reference arm): the sum-factorised FP64
+# OpenMP evaluation of oracle/cpu_sumfac.cpp on all host cores
 # ---------------------------------------------------------------------------
-def _oracle_sample_worker(cells_per_dim, n_cells, reps, q):
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 1e6
+    except Exception:
+        pass
+    return 0.0
+
+
+def _sumfac_worker(cells_per_dim, reps, slabs, q):
+    """One fused LSRK stage (FP64) of the 6D workload per repetition, on the
+    v3 slabs [0, slabs) of the mesh (slabs = all: the whole mesh)."""
     import numpy as np
     import workloads as W
     from oracle import lsrk
-    from oracle.dg import PhaseSpaceField, Problem
+    from oracle.sumfac import SumFac, threads
     w = W.config_6d(cells=cells_per_dim)
-    p = Problem(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
-                PhaseSpaceField(w.dx, w.dv, W.e_function(w)))
-    rng = np.random.default_rng(0)
-    cells = sorted(int(c) for c in rng.choice(p.ncells, size=n_cells, replace=False))
-
-    class Cells:
-        """The 6D initial state on the sampled cells and their neighbours only,
-        materialised before the timed region."""
-        shape = (p.n_dofs,)
-
-        def __init__(self):
-            self.cache = {}
-            for e in cells:
-                for c in [e] + [p.neighbour(e, j, s) for j in range(p.d) for s in (1, -1)]:
-                    if c not in self.cache:
-                        self.cache[c] = p.interpolate(lambda yx, v: _u0(w, yx, v), [c])
-
-        def __getitem__(self, s):
-            return self.cache[s.start // p.dofs_per_cell]
-
-    u = Cells()
+    zeta = np.polynomial.legendre.leggauss(w.n)[0]
+    sf = SumFac(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
+                e_nodes=W.e_table(w, zeta))
+    u = W.separable_state(w, zeta)
+    w_in = u.copy()
+    w_out = np.empty_like(u)
+    dt, _ = W.time_step(w)
+    per_slab = sf.ncells // w.cells_v[-1]
+    cells = (0, per_slab * slabs)
     times = []
-    for _ in range(reps):
+    for r in range(reps):
         t0 = time.perf_counter()
-        K = np.stack([p.apply_mass_inverse(p.cell_residual(u, e)).reshape(-1, order="F")
-                      for e in cells])
-        # the stage update of the sampled cells (LSRK stage 0)
-        for i, e in enumerate(cells):
-            uo = u[slice(e * p.dofs_per_cell, (e + 1) * p.dofs_per_cell)]
-            _ = uo + lsrk.B[0] * 1e-3 * K[i], uo + lsrk.A[0] * 1e-3 * K[i]
+        sf.rk_stage(w_in, w_out, u, lsrk.A[0] * dt, lsrk.B[0] * dt, cells=cells)
         times.append(time.perf_counter() - t0)
-    q.put({"seconds": times, "dofs": n_cells * p.dofs_per_cell, "cells": n_cells})
+    q.put({"seconds": times, "dofs": (cells[1] - cells[0]) * w.n ** w.d, "threads": threads(),
+           "total_dofs": sf.n_dofs, "slabs": slabs, "of_slabs": w.cells_v[-1]})
 
 
-def _u0(w, yx, v):
-    import numpy as np
-    f = w.u0_factors
-    out = np.ones(yx.shape[:-1])
-    for j in range(w.dx):
-        out = out * f[j](yx[..., j])
-    for j in range(w.dv):
-        out = out * f[w.dx + j](v[..., j])
-    return out
-
-
-def oracle_sample(cells_per_dim, n_cells, reps):
+def cpu_oracle(cells_per_dim, reps, slabs=None):
+    """Times the CPU oracle in a fresh (spawned) process: ``reps`` fused
+    stages on ``slabs`` v3 slabs of the 6D mesh (None: all of them)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    pr = ctx.Process(target=_oracle_sample_worker, args=(cells_per_dim, n_cells, reps, q))
+    qu = ctx.Queue()
+    pr = ctx.Process(target=_sumfac_worker, args=(cells_per_dim, reps, slabs or cells_per_dim, qu))
     pr.start()
-    res = q.get()
+    res = qu.get()
     pr.join()
+    res["cpu"] = _cpu_model()
     return res
 
 
+def _cpu_line(res, value):
+    whole = res["slabs"] == res["of_slabs"]
+    return {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+            "implementation": "oracle/cpu_sumfac.cpp: FP64 sum factorisation, OpenMP over cells",
+            "cpu": res["cpu"],
+            "sample": ("the whole 6D mesh, one fused FP64 LSRK stage per step" if whole else
+                       f"{res['slabs']} of {res['of_slabs']} v3 slabs of the 6D mesh "
+                       f"({res['dofs']} of {res['total_dofs']} DoFs) per step, one fused FP64 "
+                       "LSRK stage")}
+
+
 def reference_arm(args, world, rank):
-    """--impl reference: the FP64 oracle, as it stands, on host cores."""
+    """--impl reference: the CPU oracle, as it stands, on all host cores."""
     if rank != 0:
         return
-    n_cells = 40
-    res = oracle_sample(args.cells, n_cells, args.warmup + args.steps)
+    need = 3 * 8 * (args.cells ** 6) * 64 / 1e9 + 10
+    if _mem_available_gb() < need:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the CPU oracle needs about {need:.0f} GB of host memory"}), flush=True)
+        return
+    # one v3 slab per step keeps warm-up + steps within a few minutes
+    res = cpu_oracle(args.cells, args.warmup + args.steps, slabs=1)
     ts = res["seconds"][args.warmup:]
     total = sum(ts)
     value = res["dofs"] * len(ts) / total / 1e9
@@ -273,10 +293,9 @@ def reference_arm(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"6d_k3_{args.cells}^6", "stage": "LSRK(5,4) stage 0",
-                   "sample": f"{n_cells} cells x 4096 DoFs per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n_cells} random cells of the 6D mesh per step, FP64 numpy"},
+        "config": {"workload": f"6d_k3_{args.cells}^6", "step": "fused LSRK(5,4) stage, FP64",
+                   "sample": f"{res['slabs']} of {res['of_slabs']} v3 slabs per step"},
+        "cpu_baseline": _cpu_line(res, value),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -317,21 +336,29 @@ def measure_configs(torch, hbm_peak):
                 "frac_hbm": gbs / hbm_peak, "bytes_per_dof": bpd}
 
     # 6D: FP32 sweeps / FP64 state against the plain FP64 path on the same
-    # GPU -- error per operator application and after a number of steps
+    # GPU -- error per operator application and at the workload's final time
+    # (its 50 steps); the temporal error of the run, estimated from a second
+    # run at half the step (Richardson: (16/15) ||u_dt - u_dt/2|| for a
+    # fourth-order scheme), says what "the same final-time accuracy" means
     w = W.config_6d()
     dg, zeta = make(w)
-    dt, _ = W.time_step(w)
+    dt, nacc = W.time_step(w)
     u0 = W.separable_state(w, zeta, xp=torch, device="cuda")
     k64 = dg.apply(u0, prec=PREC_FP64)
     k32 = dg.apply(u0.float(), prec=PREC_FP32).double()
     rel_apply = float(torch.linalg.vector_norm(k32 - k64) / torch.linalg.vector_norm(k64))
     del k32
-    nacc = 10
     u64 = u0.clone()
     ms64 = _timed(torch, lambda: dg.rk_step(u64, dt, nsteps=nacc, prec=PREC_FP64), 1)
     u32 = u0.clone()
     ms32 = _timed(torch, lambda: dg.rk_step(u32, dt, nsteps=nacc, prec=PREC_FP32), 1)
+    u32h = u0.clone()
+    dg.rk_step(u32h, dt / 2, nsteps=2 * nacc, prec=PREC_FP32)
     dg.check()
+    nrm = lambda x: float(torch.linalg.vector_norm(x))
+    n64 = nrm(u64)
+    time_err = 16.0 / 15.0 * nrm(u32 - u32h) / n64
+    del u32h
     # delta-f form around the Maxwellian equilibrium: FP32 sweeps on u - u_eq
     u_eq = W.separable_state(W.equilibrium_6d(w), zeta, xp=torch, device="cuda")
     dg.set_reference(u_eq)
@@ -343,22 +370,25 @@ def measure_configs(torch, hbm_peak):
     udf.copy_(u0)
     msdf = _timed(torch, lambda: dg.rk_step_df(udf, dt, nsteps=nacc), 1)
     dg.check()
-    m0 = dg.integrals(u0)[0]
+    m0, l0, _ = dg.integrals(u0)
+
+    def drift(x):
+        m, l2, _ = dg.integrals(x)
+        return {"mass_drift": (m - m0) / m0, "l2_change": (l2 - l0) / l0}
     out["6d_fp32_vs_fp64"] = {
-        "workload": w.name, "steps": nacc,
-        "apply_rel_l2_diff": rel_apply,
-        "state_rel_l2_diff_after_steps": float(torch.linalg.vector_norm(u32 - u64) /
-                                               torch.linalg.vector_norm(u64)),
-        "mass_drift_fp64": (dg.integrals(u64)[0] - m0) / m0,
-        "mass_drift_fp32_fp64state": (dg.integrals(u32)[0] - m0) / m0,
-        "ms_per_step_fp64": ms64 / nacc, "ms_per_step_fp32_fp64state": ms32 / nacc,
-        "apply_rel_l2_diff_deltaf": rel_apply_df,
-        "state_rel_l2_diff_after_steps_deltaf": float(torch.linalg.vector_norm(udf - u64) /
-                                                      torch.linalg.vector_norm(u64)),
-        "ms_per_step_deltaf": msdf / nacc,
+        "workload": w.name, "steps": nacc, "final_time": dt * nacc,
+        "apply_rel_l2_diff_fp32": rel_apply, "apply_rel_l2_diff_deltaf": rel_apply_df,
+        "state_change_rel_l2": nrm(u64 - u0) / nrm(u0),
+        "temporal_error_estimate_rel_l2": time_err,
+        "fp64": {"ms_per_step": ms64 / nacc, **drift(u64)},
+        "fp32_sweeps_fp64_state": {"ms_per_step": ms32 / nacc, **drift(u32),
+                                   "state_rel_l2_diff_vs_fp64": nrm(u32 - u64) / n64},
+        "deltaf_fp32_sweeps": {"ms_per_step": msdf / nacc, **drift(udf),
+                               "state_rel_l2_diff_vs_fp64": nrm(udf - u64) / n64},
         "note": "K of the FP64 path matches the FP64 oracle to 1e-12 (tests); the plain relative "
                 "difference of K is large for smooth data (K << its terms); see tests for the "
-                "term-scale error"}
+                "term-scale error.  The final-time differences against FP64 are to be read "
+                "against the temporal error estimate of the run"}
     dg.close()
     del u0, u64, u32, k64, udf
     torch.cuda.empty_cache()
@@ -649,10 +679,11 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        res = oracle_sample(args.cells, 1000, 1)
+        # the whole mesh if the host has the memory (3 FP64 vectors), else one v3 slab
+        whole = _mem_available_gb() >= 3 * 8 * n / 1e9 + 10
+        res = cpu_oracle(args.cells, 1, slabs=None if whole else 1)
         sec = min(res["seconds"])
-        cpu = {"value": res["dofs"] / sec / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{res['cells']} random cells of the 6D mesh, one fused stage, FP64 numpy"}
+        cpu = _cpu_line(res, res["dofs"] / sec / 1e9)
 
     if rank == 0:
         line = {
