@@ -57,7 +57,7 @@
 extern "C" {
 #endif
 
-#define DG_ABI_VERSION 3
+#define DG_ABI_VERSION 4
 
 typedef struct dg_ctx* dg_handle;
 typedef struct dg_batch_ctx* dg_batch;
@@ -69,7 +69,12 @@ typedef enum {
     DG_ERR_CUDA = 3,          /* a CUDA runtime call failed                 */
     DG_ERR_OOM = 4,           /* device or host allocation failed           */
     DG_ERR_NONFINITE = 5,     /* a kernel produced NaN or Inf               */
-    DG_ERR_TIMEOUT = 6        /* a bounded wait inside a kernel gave up     */
+    DG_ERR_TIMEOUT = 6,       /* a bounded wait inside a kernel gave up     */
+    DG_ERR_BOUNDS = 7         /* bounds-check build only (libdg_bounds.so,
+                                 compiled with -DDG_BOUNDS_CHECK): a kernel
+                                 computed a cell, neighbour, tile or slab
+                                 index out of its range (the access was
+                                 redirected to index 0; results invalid)   */
 } dg_status;
 
 typedef enum {
@@ -390,37 +395,46 @@ dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, i
 
 /*
  * The integrals of dg_integrals() for callers that cannot allocate device
- * memory -- for example code that runs while a CUDA graph is being captured,
- * code inside a framework whose allocator owns all device memory, or a long
- * run that must not call cudaMalloc after start-up (it synchronises the
- * device and can fail on a fragmented heap).  It needs no handle and calls no
- * cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
- * array of 98,328 bytes compiled into the library, which every GPU that
- * loads the library holds until the process exits.  The paper has no
- * counterpart to this entry point.
+ * memory: for example code inside a framework whose allocator owns all
+ * device memory, or a long run that must not call cudaMalloc after start-up
+ * (cudaMalloc synchronises the device and can fail on a fragmented heap).  It
+ * needs no handle and calls no cudaMalloc, cudaFree or other allocating
+ * routine: its scratch is a fixed array of 98,328 bytes compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The paper has no counterpart to this entry point.
+ *
+ * Elements covered: the collocated bases on affine meshes, i.e. basis
+ * DG_BASIS_GL (Gauss-Legendre weights) or DG_BASIS_GLL (Gauss-Lobatto
+ * weights) with one |J| for every cell.  DG_BASIS_GLL_GAUSS (whose states
+ * need a change of basis first) is rejected with DG_ERR_UNSUPPORTED.  A
+ * curved mesh (dg_geometry.deform) has a |J| per point and is not covered:
+ * use dg_integrals for it.
  *
  * u: device vector of n_cells * (degree+1)^dim FP64 values in the layout of
  * this header (16-byte aligned); det_jacobian: |J| of every cell
  * (dg_info.det_jacobian); out: host array of 3 doubles, receives
  * (int u, int u^2, max |u_i|).  At most 2^32 DoFs per call: larger vectors
- * are rejected with DG_ERR_INVALID_ARG (use dg_integrals).  Synchronises
- * ``stream``.
+ * are rejected with DG_ERR_INVALID_ARG (use dg_integrals).  The call
+ * synchronises ``stream`` (it reads the three results back into ``out``).
  *
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls on a device share the one array and a call
- * leaves its partial sums there; calls that overlap on the GPU (for instance
- * on two streams at once) race on it, so serialise them.  Every slot a call
- * reads is written by that call first, so nothing needs clearing.
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; the address is not valid across cudaDeviceReset, so do not
+ * use this call after resetting the device.  All calls on a device share the
+ * one array and a call leaves its partial sums there; calls that overlap on
+ * the GPU (for instance on two streams at once) race on it, so serialise
+ * them.  Every slot a call reads is written by that call first, so nothing
+ * needs clearing.
  */
-dg_status dg_integrals_noalloc(const double* u, long long n_cells, int dim, int degree,
+dg_status dg_integrals_noalloc(const double* u, long long n_cells, int dim, int degree, int basis,
                                double det_jacobian, double* out, void* stream);
 
 /*
  * Synchronise ``stream`` and report device-side errors latched since the
- * last check: DG_ERR_TIMEOUT if a kernel's bounded wait for an asynchronous
- * copy gave up (its results are invalid), else DG_ERR_NONFINITE if any kernel
- * produced NaN or Inf.  Clears the latch.
+ * last check: DG_ERR_BOUNDS (bounds-check build only) if a kernel computed an
+ * index out of its range, else DG_ERR_TIMEOUT if a kernel's bounded wait for
+ * an asynchronous copy gave up (its results are invalid in both cases), else
+ * DG_ERR_NONFINITE if any kernel produced NaN or Inf.  Clears the latch.
  */
 dg_status dg_check(dg_handle h, void* stream);
 
@@ -451,14 +465,19 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
                       double* best_ms);
 
 /*
- * Batched execution of independent problems (constant velocity only).
+ * Batched execution of independent problems (constant velocity only; d = 3
+ * or 4).  The paper runs one problem at a time; advancing many independent
+ * problems together is this library's addition.
  * dg_batch_create groups ``count`` handles (each stays owned by the caller
  * and must outlive the batch).  dg_batch_rk_step advances every member i by
  * nsteps LSRK(5,4) steps of size dt[i] on its FP64 state u[i] with stage
- * vectors w0[i], w1[i] (host arrays of device pointers); each stage of all
- * members is one persistent launch that takes work tiles from a device
- * queue, and each step is replayed from a CUDA graph.  prec: DG_PREC_FP64
- * or DG_PREC_FP32 (FP32 stage vectors and sweeps, FP64 state).
+ * vectors w0[i], w1[i] (host arrays of device pointers).  Members are grouped
+ * by (dimension, degree); each stage of a group is one persistent launch of
+ * a kernel specialised for that pair, which takes work tiles (a run of one
+ * member's cells) from a device queue, and each step (5 stages of every
+ * group) is replayed from a CUDA graph.  prec: DG_PREC_FP64 or DG_PREC_FP32
+ * (FP32 stage vectors and sweeps, FP64 state); with DG_PREC_FP32 the d = 4
+ * groups run the register-resident 4D cell algorithm.
  */
 dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out);
 dg_status dg_batch_destroy(dg_batch b);
@@ -468,15 +487,48 @@ dg_status dg_batch_rk_step(dg_batch b, double* const* u, void* const* w0, void* 
 dg_status dg_batch_info(dg_batch b, long long* tiles, long long* n_dofs);
 /* dg_check for a batch: synchronise and report non-finite results. */
 dg_status dg_batch_check(dg_batch b, void* stream);
-/* Tile size (DoFs per work tile, whole cells, >= one cell) and threads per
- * block of the batched kernel (defaults 4096 and 256). */
+/* Launch configuration of the batched kernels. */
+typedef struct {
+    int tile_dofs;   /* shared-memory kernel: DoFs per work tile (whole cells,
+                        >= one cell), 64..65536; default 4096                 */
+    int threads;     /* shared-memory kernel: threads per block; default 256 */
+    int threads4;    /* 4D register kernel: threads per block, 128, 256 or 512
+                        (n^2 per cell, so threads4 / n^2 cells per block and
+                        per tile; 512 only for n <= 4); default 128           */
+    int order;       /* direction order, bits: 1 = the second x direction
+                        first, 2 = the second v direction first (4D register
+                        kernel); 4 = all directions in reverse order (shared-
+                        memory kernel).  Results differ only by rounding.     */
+    int r4_max_n;    /* FP32 d = 4 groups with n = degree + 1 <= r4_max_n run
+                        the 4D register kernel, the others the shared-memory
+                        kernel (1: none); default 4                           */
+} dg_batch_launch;
+/* One configuration timed by dg_batch_autotune and its time per step (ms). */
+typedef struct {
+    int tile_dofs, threads, threads4, order, r4_max_n;
+    double ms;
+} dg_batch_trial;
+/* Tile size and threads per block of the shared-memory kernel (the rest of
+ * the configuration unchanged). */
 dg_status dg_batch_set_launch(dg_batch b, int tile_dofs, int threads);
-/* Autotuner of the batched launch: times one LSRK step for each candidate
- * tile size and block size on the caller's vectors (which are advanced by
+/* Set / read the whole configuration (validated; captured graphs are
+ * dropped). */
+dg_status dg_batch_set_launch_ex(dg_batch b, const dg_batch_launch* cfg);
+dg_status dg_batch_get_launch(dg_batch b, dg_batch_launch* cfg);
+/* Autotuner of the batched launch: times one LSRK step (after one untimed
+ * step) for each candidate on the caller's vectors (which are advanced by
  * those steps) and keeps the fastest; best_ms (may be NULL) receives its time
- * per step. */
+ * per step.  The groups are separate launches whose times add, so it tunes
+ * by coordinate descent: which 4D groups run the register kernel, then its
+ * block size and direction order, then the shared-memory kernel's tile size
+ * and block size, then its direction order; parameters that no group of the
+ * batch uses are not varied. */
 dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void* const* w1,
                             const double* dt, int prec, void* stream, double* best_ms);
+/* The configurations the last dg_batch_autotune timed, in the order tried:
+ * *count receives their number, and up to max_trials of them are written to
+ * trials (host array, may be NULL). */
+dg_status dg_batch_autotune_record(dg_batch b, dg_batch_trial* trials, int max_trials, int* count);
 
 #ifdef __cplusplus
 }

@@ -9,12 +9,15 @@ import os
 import re
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libdg.so")
+# DG_LIBRARY_VARIANT=bounds selects the bounds-check build (libdg_bounds.so,
+# every computed index checked on the device; see DG_ERR_BOUNDS)
+_VARIANT = os.environ.get("DG_LIBRARY_VARIANT", "")
+LIB_PATH = os.path.join(PKG, "libdg_bounds.so" if _VARIANT == "bounds" else "libdg.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "dg.h")
 
 DG_OK = 0
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID_ARG", 2: "DG_ERR_UNSUPPORTED", 3: "DG_ERR_CUDA",
-                4: "DG_ERR_OOM", 5: "DG_ERR_NONFINITE", 6: "DG_ERR_TIMEOUT"}
+                4: "DG_ERR_OOM", 5: "DG_ERR_NONFINITE", 6: "DG_ERR_TIMEOUT", 7: "DG_ERR_BOUNDS"}
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 BASIS_GL, BASIS_GLL, BASIS_GLL_GAUSS = 0, 1, 2
 
@@ -44,6 +47,19 @@ class Launch(ctypes.Structure):
     """dg_launch of include/dg.h (cell-kernel launch configuration)."""
     _fields_ = [("threads", ctypes.c_int), ("cells_per_block", ctypes.c_int),
                 ("order", ctypes.c_int * 6), ("variant", ctypes.c_int)]
+
+
+class BatchLaunch(ctypes.Structure):
+    """dg_batch_launch of include/dg.h (batched-kernel launch configuration)."""
+    _fields_ = [("tile_dofs", ctypes.c_int), ("threads", ctypes.c_int),
+                ("threads4", ctypes.c_int), ("order", ctypes.c_int), ("r4_max_n", ctypes.c_int)]
+
+
+class BatchTrial(ctypes.Structure):
+    """dg_batch_trial of include/dg.h (one configuration the autotuner timed)."""
+    _fields_ = [("tile_dofs", ctypes.c_int), ("threads", ctypes.c_int),
+                ("threads4", ctypes.c_int), ("order", ctypes.c_int), ("r4_max_n", ctypes.c_int),
+                ("ms", ctypes.c_double)]
 
 
 class DGError(RuntimeError):
@@ -82,7 +98,7 @@ def load():
         "dg_rk_stage": (i, [vp, vp, vp, vp, i, d, i, i, vp]),
         "dg_rk_step": (i, [vp, vp, vp, vp, d, i, i, i, vp]),
         "dg_integrals": (i, [vp, vp, c_double_p, vp]),
-        "dg_integrals_noalloc": (i, [vp, ll, i, i, d, c_double_p, vp]),
+        "dg_integrals_noalloc": (i, [vp, ll, i, i, i, d, c_double_p, vp]),
         "dg_check": (i, [vp, vp]),
         "dg_selftest_wait": (i, [vp, vp]),
         "dg_basis_nodes": (i, [i, i, vp, vp, vp]),
@@ -104,6 +120,9 @@ def load():
         "dg_batch_info": (i, [vp, ctypes.POINTER(ll), ctypes.POINTER(ll)]),
         "dg_batch_check": (i, [vp, vp]),
         "dg_batch_set_launch": (i, [vp, i, i]),
+        "dg_batch_set_launch_ex": (i, [vp, ctypes.POINTER(BatchLaunch)]),
+        "dg_batch_get_launch": (i, [vp, ctypes.POINTER(BatchLaunch)]),
+        "dg_batch_autotune_record": (i, [vp, ctypes.POINTER(BatchTrial), i, ctypes.POINTER(i)]),
         "dg_batch_autotune": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                   c_double_p, i, vp, c_double_p]),
     }

@@ -344,13 +344,40 @@ class DGBatch:
         U, A, B, D = self._arrays(us, w0s, w1s, dts, prec)
         check(self.lib.dg_batch_rk_step(self.handle, U, A, B, D, int(nsteps), prec, _stream()))
 
-    def set_launch(self, tile_dofs, threads):
-        """DoFs per work tile and threads per block of the batched launch."""
-        check(self.lib.dg_batch_set_launch(self.handle, int(tile_dofs), int(threads)))
+    def set_launch(self, tile_dofs, threads, threads4=None, order=None, r4_max_n=None):
+        """Launch configuration of the batched kernels: DoFs per work tile and
+        threads per block of the shared-memory kernel, threads per block of the
+        4D register kernel (n^2 per cell), the direction-order bits, and the
+        largest n of the FP32 4D groups that run the register kernel
+        (dg_batch_launch)."""
+        c = self.get_launch()
+        c.update(tile_dofs=int(tile_dofs), threads=int(threads))
+        for k, v in (("threads4", threads4), ("order", order), ("r4_max_n", r4_max_n)):
+            if v is not None:
+                c[k] = int(v)
+        check(self.lib.dg_batch_set_launch_ex(self.handle, ctypes.byref(_lib.BatchLaunch(**c))))
+
+    def get_launch(self):
+        """The current dg_batch_launch as a dict."""
+        c = _lib.BatchLaunch()
+        check(self.lib.dg_batch_get_launch(self.handle, ctypes.byref(c)))
+        return {"tile_dofs": c.tile_dofs, "threads": c.threads, "threads4": c.threads4,
+                "order": c.order, "r4_max_n": c.r4_max_n}
+
+    def autotune_record(self):
+        """The configurations the last autotune timed (list of dicts with ms)."""
+        n = ctypes.c_int()
+        check(self.lib.dg_batch_autotune_record(self.handle, None, 0, ctypes.byref(n)))
+        arr = (_lib.BatchTrial * max(1, n.value))()
+        check(self.lib.dg_batch_autotune_record(self.handle, arr, n.value, ctypes.byref(n)))
+        return [{"tile_dofs": t.tile_dofs, "threads": t.threads, "threads4": t.threads4,
+                 "order": t.order, "r4_max_n": t.r4_max_n, "ms": t.ms} for t in arr[:n.value]]
 
     def autotune(self, us, w0s, w1s, dts, prec=PREC_FP32):
-        """Time tile sizes x block sizes on one step, keep the fastest and
-        return its time per step in ms (the states are advanced by the trials)."""
+        """Time launch configurations (block sizes, so cells per block; tile
+        size; direction order) on one step each, keep the fastest and return
+        its time per step in ms (the states are advanced by the trials); the
+        record of what was timed is ``autotune_record()``."""
         U, A, B, D = self._arrays(us, w0s, w1s, dts, prec)
         best = ctypes.c_double()
         check(self.lib.dg_batch_autotune(self.handle, U, A, B, D, prec, _stream(),

@@ -5,6 +5,11 @@ Every translation unit under ``csrc/`` is compiled by nvcc in parallel
 ``paper_2002_08110_gb300/libdg.so`` with the CUDA runtime linked statically.
 Object files go to ``_build/`` at the repository root.  Rebuilds only what
 changed (source or header newer than its object).
+
+``build(variant="bounds")`` makes the bounds-check library
+``libdg_bounds.so`` instead (``-DDG_BOUNDS_CHECK``: every computed cell,
+neighbour, tile and slab index is checked on the device and a violation is
+reported by dg_check as DG_ERR_BOUNDS), with its objects in ``_build_bounds/``.
 """
 import concurrent.futures as cf
 import os
@@ -17,6 +22,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libdg.so")
+VARIANTS = {"": (BUILD, LIB, []),
+            "bounds": (os.path.join(ROOT, "_build_bounds"), os.path.join(PKG, "libdg_bounds.so"),
+                       ["-DDG_BOUNDS_CHECK"])}
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -45,11 +53,13 @@ def _compile(src, obj, nvcc, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, jobs=None, extra_flags=None):
-    """Compile and link; returns the path of libdg.so."""
+def build(verbose=False, jobs=None, extra_flags=None, variant=""):
+    """Compile and link; returns the path of the library (libdg.so, or
+    libdg_bounds.so for variant="bounds")."""
     nvcc = _nvcc()
+    BUILD, LIB, vflags = VARIANTS[variant]
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra_flags or [])
+    extra = list(extra_flags or []) + vflags
     srcs = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
     newest_header = max(os.path.getmtime(h) for h in _headers())
     todo = []

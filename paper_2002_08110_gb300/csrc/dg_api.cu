@@ -151,6 +151,7 @@ dg_status ensure_scratch(dg_ctx* h, int prec) {
       return cuda_fail(e, "FP32 input buffer");
     }
   }
+
   const int combo = combo_of(prec);
   if (generic_smem_bytes(h->d, h->n, combo, 1) != 0) return DG_OK;
   const int blocks = generic_grid_blocks(h->d, h->n, h->ncells, 1, h->cfg[prec].threads);
@@ -1369,6 +1370,7 @@ dg_status dg_check(dg_handle h, void* stream) {
       (e = cudaMemcpy(&flag, h->err_d, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
       (e = cudaMemset(h->err_d, 0, sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "dg_check");
+  if (flag & 4) return fail(DG_ERR_BOUNDS, "a kernel computed an index out of its range");
   if (flag & 2) return fail(DG_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
   if (flag & 1) return fail(DG_ERR_NONFINITE, "a kernel produced a non-finite value");
   return DG_OK;

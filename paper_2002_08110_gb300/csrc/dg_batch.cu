@@ -2,16 +2,21 @@
 //
 // Every member is a constant-velocity problem (Sec. 5.1 setting) of its own
 // dimension (dim_x = 2, dim_v = 1 or 2 here: d = 3 or 4), degree and mesh.
-// Each LSRK(5,4) stage of all members is ONE persistent launch: blocks take
-// work tiles (a member and a run of its cells) from a device queue with an
-// atomic counter, and process each tile with the element-centric cell
-// algorithm specialised at compile time for the tile's (d, n) (a switch over
-// the supported pairs).  Tiles of one member are consecutive in the queue so
-// that neighbouring cells are processed close in time (L2 reuse), and the
-// queue interleaves nothing else, so load balance comes from the dynamic
-// assignment.  One step = 5 stage launches (+ a counter reset), replayed from
-// a CUDA graph.  The tile size (DoFs per tile) and the block size are chosen
-// by dg_batch_autotune.
+// Members are grouped by (d, n); each LSRK(5,4) stage of a group is ONE
+// persistent launch of a kernel specialised for that (d, n): blocks take work
+// tiles (a member and a run of its cells) from a device queue with an atomic
+// counter.  Tiles of one member are consecutive in the queue so that
+// neighbouring cells are processed close in time (L2 reuse); load balance
+// comes from the dynamic assignment.  One step = 5 x (number of groups)
+// launches (+ counter resets), replayed from a CUDA graph.
+//
+// Kernels: for FP32 stage vectors, the d = 4 groups (dim_x = dim_v = 2) run
+// the register-resident 4D cell algorithm (dg_cell4d.cuh: a thread holds a
+// column, then a row, of a cell's n^2 x n^2 matrix; a tile is one block's
+// cells); every other group runs the shared-memory cell algorithm below
+// (tiles of about tile_dofs DoFs).  Block sizes (so cells per block), tile
+// size and the order of the directions are chosen by dg_batch_autotune,
+// which keeps a record of the configurations it timed.
 //
 // Per member and stage: K = M^{-1} A(w_in); u += b_s dt K (FP64);
 // w_out = u_old + a_s dt K (s < 4) or u_new (s = 4), exactly as the
@@ -21,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dg_cell4d.cuh"
 #include "dg_generic.cuh"
 
 namespace dg {
@@ -58,6 +64,9 @@ struct BParams {
   int nbt_off;     // byte offset of the per-cell neighbour table in shared memory
   double a, b;     // a_s (or b_4 at the last stage), b_s
   int last_stage;
+  int ninst;       // number of members (bounds checks)
+  int order;       // bit 0 / 1: second x / v direction first (4D register kernel);
+                   // bit 2: directions in reverse order (shared-memory kernel)
 };
 
 template <typename T>
@@ -74,11 +83,15 @@ __device__ __forceinline__ double speed<double>(const BInst& I, int j) { return 
 template <>
 __device__ __forceinline__ float speed<float>(const BInst& I, int j) { return I.c32[j]; }
 
-__device__ __forceinline__ int nb_cell(const BInst& I, int cell, int j, int s) {
+__device__ __forceinline__ int nb_cell(const BInst& I, int cell, int j, int s, int* err) {
   const int st = I.cstride[j], nj = I.ncell[j];
   const int cj = (cell / st) % nj;
-  if (s < 0) return cj == 0 ? cell + (nj - 1) * st : cell - st;
-  return cj == nj - 1 ? cell - (nj - 1) * st : cell + st;
+  int nb;
+  if (s < 0) nb = cj == 0 ? cell + (nj - 1) * st : cell - st;
+  else nb = cj == nj - 1 ? cell - (nj - 1) * st : cell + st;
+  DG_BOUND(err, nb, I.ncells);
+  (void)err;
+  return nb;
 }
 
 // One tile of member I: cells [c0, c0 + nc), d = D, n = N, compute type TC,
@@ -100,12 +113,13 @@ __device__ void process_tile(const BInst& I, const BParams& bp, int c0, int nc, 
   for (int c = threadIdx.x; c < nc; c += blockDim.x)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      nbt[c * 2 * kBatchMaxDim + 2 * j] = nb_cell(I, c0 + c, j, -1);
-      nbt[c * 2 * kBatchMaxDim + 2 * j + 1] = nb_cell(I, c0 + c, j, 1);
+      nbt[c * 2 * kBatchMaxDim + 2 * j] = nb_cell(I, c0 + c, j, -1, bp.err);
+      nbt[c * 2 * kBatchMaxDim + 2 * j + 1] = nb_cell(I, c0 + c, j, 1, bp.err);
     }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
+  for (int jj = 0; jj < D; ++jj) {
+    const int j = (bp.order & 4) ? D - 1 - jj : jj;
     int sj = 1;
     for (int m = 0; m < j; ++m) sj *= N;
     const TC cj = speed<TC>(I, j);
@@ -177,6 +191,15 @@ __global__ void __launch_bounds__(512) k_batch(const BParams bp) {
     __syncthreads();
     if (tix >= bp.ntiles) break;
     const Tile tl = bp.tiles[tix];
+#ifdef DG_BOUNDS_CHECK
+    // a tile names a member and a run of its cells
+    if (tl.inst < 0 || tl.inst >= bp.ninst || tl.cell0 < 0 || tl.ncells < 1 ||
+        tl.cell0 + tl.ncells > bp.inst[tl.inst < 0 || tl.inst >= bp.ninst ? 0 : tl.inst].ncells) {
+      if (threadIdx.x == 0) atomicOr(bp.err, 4);
+      __syncthreads();
+      continue;
+    }
+#endif
     const BInst I = bp.inst[tl.inst];
     if (bp.mode == 0) {
       TW* w0 = static_cast<TW*>(const_cast<void*>(I.w[bp.parity & 1]));
@@ -207,6 +230,188 @@ __global__ void __launch_bounds__(512) k_batch(const BParams bp) {
   if (bad) atomicOr(bp.err, 1);
 }
 
+// The 4D register kernel over the tiles of one (d = 4, n) group: each tile is
+// up to CPB consecutive cells of one member, n^2 threads per cell, the cell
+// algorithm of k_cell4d (stage mode, FP32 stage vectors, FP64 state) with the
+// member's constant speeds.  bp.order picks which x and which v direction
+// goes first.
+template <int N, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
+  constexpr int S = N * N, NP = S * S, PAD = S + 1, CPB = THREADS / S, BUF = CPB * S * PAD;
+  constexpr int NCH = (S + 7) / 8;
+  extern __shared__ __align__(16) unsigned char bsm4[];
+  float* const su = reinterpret_cast<float*>(bsm4);
+  float* const sr = su + BUF;
+  __shared__ int s_tile;
+  const Tab1D<float>& T = c_bt32[N];
+  const int c = threadIdx.x / S;
+  const int k = threadIdx.x - c * S;
+  float nanacc = 0.f;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
+    __syncthreads();
+    const int tix = s_tile;
+    if (tix >= bp.ntiles) break;
+    const Tile tl = bp.tiles[tix];
+#ifdef DG_BOUNDS_CHECK
+    // a tile names a member and a run of its cells
+    if (tl.inst < 0 || tl.inst >= bp.ninst || tl.cell0 < 0 || tl.ncells < 1 ||
+        tl.cell0 + tl.ncells > bp.inst[tl.inst < 0 || tl.inst >= bp.ninst ? 0 : tl.inst].ncells) {
+      if (threadIdx.x == 0) atomicOr(bp.err, 4);
+      __syncthreads();
+      continue;
+    }
+#endif
+    const BInst& I = bp.inst[tl.inst];
+    const float* __restrict__ src = static_cast<const float*>(I.w[(bp.stage + bp.parity) & 1]);
+    float* __restrict__ dst = static_cast<float*>(const_cast<void*>(I.w[(bp.stage + 1 + bp.parity) & 1]));
+    const unsigned cell0 = static_cast<unsigned>(tl.cell0);
+    const int nc = tl.ncells;
+    const bool active = c < nc;
+    const unsigned cell = cell0 + static_cast<unsigned>(c);
+    unsigned co[4];
+    {
+      unsigned rem = cell;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const unsigned nj = static_cast<unsigned>(I.ncell[j]);
+        co[j] = rem % nj;
+        rem /= nj;
+      }
+    }
+    auto upwind = [&](int j, bool pos) -> unsigned {
+      const unsigned st = static_cast<unsigned>(I.cstride[j]);
+      const unsigned nj = static_cast<unsigned>(I.ncell[j]);
+      unsigned nb;
+      if (pos) nb = co[j] == 0 ? cell + (nj - 1) * st : cell - st;
+      else nb = co[j] == nj - 1 ? cell - (nj - 1) * st : cell + st;
+      DG_BOUND(bp.err, nb, I.ncells);
+      return nb;
+    };
+    const float c0 = I.c32[0], c1 = I.c32[1], e0 = I.c32[2], e1 = I.c32[3];
+    for (int i = threadIdx.x; i < nc * NP; i += THREADS) {
+      const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
+      su[(cc * S + t) * PAD + q] = src[static_cast<size_t>(cell0) * NP + i];
+    }
+    float u[S], r[S], nbA[S], nbB[S];
+    if (active) {
+      if (c0 != 0.f) load_col<N>(nbA, src, upwind(0, c0 > 0.f), k);
+      if (c1 != 0.f) load_col<N>(nbB, src, upwind(1, c1 > 0.f), k);
+    }
+    __syncthreads();
+    // phase X: column k, directions x1, x2 (order by bit 0)
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        u[q] = su[(c * S + k) * PAD + q];
+        r[q] = 0.f;
+      }
+      if (bp.order & 1) {
+        if (c1 != 0.f) dir4<N, N>(r, u, nbB, c1, T);
+        if (c0 != 0.f) dir4<N, 1>(r, u, nbA, c0, T);
+      } else {
+        if (c0 != 0.f) dir4<N, 1>(r, u, nbA, c0, T);
+        if (c1 != 0.f) dir4<N, N>(r, u, nbB, c1, T);
+      }
+#pragma unroll
+      for (int q = 0; q < S; ++q) sr[(c * S + k) * PAD + q] = r[q];
+      if (e0 != 0.f) load_row<N>(nbA, src, upwind(2, e0 > 0.f), k);
+      if (e1 != 0.f) load_row<N>(nbB, src, upwind(3, e1 > 0.f), k);
+    }
+    __syncthreads();
+    if (active) {
+      // phase V: row k, directions v1, v2 (order by bit 1)
+      const size_t g0 = static_cast<size_t>(cell) * NP + k;
+      double ua[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        if (m < S) ua[m] = __ldcs(I.u + g0 + static_cast<size_t>(S) * m);
+#pragma unroll
+      for (int m = 0; m < S; ++m) {
+        u[m] = su[(c * S + m) * PAD + k];
+        r[m] = sr[(c * S + m) * PAD + k];
+      }
+      if (bp.order & 2) {
+        if (e1 != 0.f) dir4<N, N>(r, u, nbB, e1, T);
+        if (e0 != 0.f) dir4<N, 1>(r, u, nbA, e0, T);
+      } else {
+        if (e0 != 0.f) dir4<N, 1>(r, u, nbA, e0, T);
+        if (e1 != 0.f) dir4<N, N>(r, u, nbB, e1, T);
+      }
+      // fused LSRK stage update: one FP64 add per value
+      const float bf = static_cast<float>(bp.b * I.dt), af = static_cast<float>(bp.a * I.dt);
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) {
+        double ub[8];
+        if (ch + 1 < NCH) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m)
+            if (8 * (ch + 1) + m < S) ub[m] = __ldcs(I.u + g0 + static_cast<size_t>(S) * (8 * (ch + 1) + m));
+        }
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+          const int m = 8 * ch + mm;
+          if (m >= S) break;
+          const size_t g = g0 + static_cast<size_t>(S) * m;
+          const float K = r[m];
+          nanacc = fmaf(K, 0.f, nanacc);
+          const double un = ua[mm] + f32_to_f64_finite(bf * K);
+          __stcs(I.u + g, un);
+          __stcs(dst + g, bp.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(ua[mm])));
+        }
+        if (ch + 1 < NCH) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) ua[m] = ub[m];
+        }
+      }
+    }
+    __syncthreads();        // su / sr and s_tile are reused by the next tile
+  }
+  if (nanacc != 0.f) atomicOr(bp.err, 1);
+}
+
+template <int N>
+size_t batch4_smem(int threads) {
+  const int S = N * N;
+  return 2 * static_cast<size_t>(threads / S) * S * (S + 1) * sizeof(float);
+}
+
+template <int N, int THREADS>
+cudaError_t launch_batch4_t(const BParams& bp, cudaStream_t s) {
+  auto kern = k_batch4<N, THREADS>;
+  const size_t smem = batch4_smem<N>(THREADS);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(bp.ntiles, std::max(1, sms * std::max(1, per_sm)));
+  kern<<<std::max(1, grid), THREADS, smem, s>>>(bp);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_batch4_n(int threads, const BParams& bp, cudaStream_t s) {
+  if (threads == 128) return launch_batch4_t<N, 128>(bp, s);
+  if (threads == 256) return launch_batch4_t<N, 256>(bp, s);
+  if (threads == 512) return launch_batch4_t<N, 512>(bp, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch4(int n, int threads, const BParams& bp, cudaStream_t s) {
+  switch (n) {
+    case 2: return launch_batch4_n<2>(threads, bp, s);
+    case 3: return launch_batch4_n<3>(threads, bp, s);
+    case 4: return launch_batch4_n<4>(threads, bp, s);
+    case 5: return launch_batch4_n<5>(threads, bp, s);
+    case 6: return launch_batch4_n<6>(threads, bp, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 }  // namespace
 }  // namespace dg
 
@@ -218,16 +423,28 @@ struct dg_batch_ctx {
   std::vector<BInst> inst;        // host copy (pointers filled per call)
   std::vector<long long> npc;
   long long n_dofs = 0;
-  int tile_dofs = 4096;
-  int threads = 256;
-  std::vector<Tile> tiles;
-  size_t smem64 = 0, smem32 = 0;  // bytes of dynamic shared memory
-  int nbt_off64 = 0, nbt_off32 = 0;  // offset of the neighbour table in it
+  // launch configuration (dg_batch_launch)
+  int tile_dofs = 4096;           // shared-memory kernel: DoFs per tile
+  int threads = 256;              // shared-memory kernel: threads per block
+  int threads4 = 128;             // 4D register kernel: threads per block (n^2 per cell)
+  int order = 0;                  // direction order bits (BParams::order)
+  int r4_max_n = 4;               // FP32 4D groups with n <= this run the register kernel
+  // members grouped by (d, n); each group's tiles for the two kernels
+  struct Group {
+    int d = 0, n = 0;
+    std::vector<int> members;
+    std::vector<Tile> tiles_sm, tiles_r4;   // shared-memory / 4D register tiles
+    Tile* tiles_sm_d = nullptr;
+    Tile* tiles_r4_d = nullptr;
+    size_t smem64 = 0, smem32 = 0;          // shared-memory kernel, bytes
+    int nbt_off64 = 0, nbt_off32 = 0;
+  };
+  std::vector<Group> groups;
   BInst* inst_d = nullptr;
-  Tile* tiles_d = nullptr;
-  int* counters_d = nullptr;      // one per stage (+ the conversion pass)
+  int* counters_d = nullptr;      // one per stage and group
   int* err_d = nullptr;
   cudaStream_t capture_stream = nullptr;
+  std::vector<dg_batch_trial> trials;   // the last autotune's record
   struct Key {
     std::vector<const void*> ptrs;
     std::vector<double> dts;
@@ -242,13 +459,21 @@ struct dg_batch_ctx {
 
 namespace {
 
+void free_tiles(dg_batch b) {
+  for (auto& g : b->groups) {
+    cudaFree(g.tiles_sm_d);
+    cudaFree(g.tiles_r4_d);
+    g.tiles_sm_d = g.tiles_r4_d = nullptr;
+  }
+}
+
 void free_batch(dg_batch b) {
   if (!b) return;
   for (int i = 0; i < 2; ++i)
     if (b->gexec[i]) cudaGraphExecDestroy(b->gexec[i]);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  free_tiles(b);
   cudaFree(b->inst_d);
-  cudaFree(b->tiles_d);
   cudaFree(b->counters_d);
   cudaFree(b->err_d);
   delete b;
@@ -262,38 +487,59 @@ void drop_graphs(dg_batch b) {
     }
 }
 
-// Tiles of `tile_dofs` DoFs (whole cells, at least one), member by member.
+// Does group g run the 4D register kernel at this precision?
+bool uses_r4(const dg_batch_ctx* b, const dg_batch_ctx::Group& g, int prec) {
+  return prec == DG_PREC_FP32 && g.d == 4 && g.n <= b->r4_max_n;
+}
+
+cudaError_t upload(Tile** dst, const std::vector<Tile>& v) {
+  cudaFree(*dst);
+  *dst = nullptr;
+  cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(Tile));
+  if (e == cudaSuccess && !v.empty())
+    e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(Tile), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Tiles of every group: `tile_dofs` DoFs (whole cells, at least one) for the
+// shared-memory kernel, one block's cells (threads4 / n^2) for the 4D
+// register kernel; member by member.
 dg_status build_tiles(dg_batch b) {
-  b->tiles.clear();
-  size_t max_cells_dofs = 0, max_cells = 0;
-  for (int m = 0; m < b->count; ++m) {
-    const int npc = static_cast<int>(b->npc[m]);
+  for (auto& g : b->groups) {
+    g.tiles_sm.clear();
+    g.tiles_r4.clear();
+    size_t max_cells_dofs = 0, max_cells = 0;
+    const int npc = static_cast<int>(b->npc[g.members[0]]);
     const int per = std::max(1, b->tile_dofs / npc);
-    const int nc = b->inst[m].ncells;
-    for (int c = 0; c < nc; c += per) {
-      Tile t{m, c, std::min(per, nc - c)};
-      b->tiles.push_back(t);
+    const int per4 = std::max(1, b->threads4 / (g.n * g.n));
+    for (int m : g.members) {
+      const int nc = b->inst[m].ncells;
+      for (int c = 0; c < nc; c += per) g.tiles_sm.push_back(Tile{m, c, std::min(per, nc - c)});
+      if (g.d == 4)
+        for (int c = 0; c < nc; c += per4) g.tiles_r4.push_back(Tile{m, c, std::min(per4, nc - c)});
+      max_cells_dofs = std::max(max_cells_dofs, static_cast<size_t>(per) * npc);
+      max_cells = std::max(max_cells, static_cast<size_t>(per));
     }
-    max_cells_dofs = std::max(max_cells_dofs, static_cast<size_t>(per) * npc);
-    max_cells = std::max(max_cells, static_cast<size_t>(per));
+    // the tile's values and residuals, then its cells' neighbour table
+    g.nbt_off64 = static_cast<int>(max_cells_dofs * 2 * sizeof(double));
+    g.nbt_off32 = static_cast<int>(max_cells_dofs * 2 * sizeof(float));
+    const size_t nbt_bytes = max_cells * 2 * kBatchMaxDim * sizeof(int);
+    g.smem64 = g.nbt_off64 + nbt_bytes;
+    g.smem32 = g.nbt_off32 + nbt_bytes;
+    if (g.smem64 > 200 * 1024) g.smem64 = 0;  // FP64 not possible at this tile size
+    if (g.smem32 > 200 * 1024) return report(DG_ERR_INVALID_ARG, "tile too large for shared memory");
+    cudaError_t e = upload(&g.tiles_sm_d, g.tiles_sm);
+    if (e == cudaSuccess) e = upload(&g.tiles_r4_d, g.tiles_r4);
+    if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
   }
-  // the tile's values and residuals, then its cells' neighbour table
-  b->nbt_off64 = static_cast<int>(max_cells_dofs * 2 * sizeof(double));
-  b->nbt_off32 = static_cast<int>(max_cells_dofs * 2 * sizeof(float));
-  const size_t nbt_bytes = max_cells * 2 * kBatchMaxDim * sizeof(int);
-  b->smem64 = b->nbt_off64 + nbt_bytes;
-  b->smem32 = b->nbt_off32 + nbt_bytes;
-  if (b->smem64 > 200 * 1024) b->smem64 = 0;  // FP64 not possible at this tile size
-  if (b->smem32 > 200 * 1024) return report(DG_ERR_INVALID_ARG, "tile too large for shared memory");
-  cudaFree(b->tiles_d);
-  b->tiles_d = nullptr;
-  cudaError_t e = cudaMalloc(&b->tiles_d, b->tiles.size() * sizeof(Tile));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->tiles_d, b->tiles.data(), b->tiles.size() * sizeof(Tile),
-                   cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
   drop_graphs(b);
   return DG_OK;
+}
+
+long long tile_count(const dg_batch_ctx* b, int prec) {
+  long long t = 0;
+  for (const auto& g : b->groups) t += uses_r4(b, g, prec) ? g.tiles_r4.size() : g.tiles_sm.size();
+  return t;
 }
 
 template <typename TC, typename TW>
@@ -307,34 +553,43 @@ cudaError_t launch_batch(dg_batch b, const BParams& bp, size_t smem, cudaStream_
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads, smem);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, sms * std::max(1, per_sm));
-  kern<<<grid, b->threads, smem, s>>>(bp);
+  const int grid = std::min(bp.ntiles, std::max(1, sms * std::max(1, per_sm)));
+  kern<<<std::max(1, grid), b->threads, smem, s>>>(bp);
   return cudaGetLastError();
 }
 
 dg_status enqueue_step(dg_batch b, int prec, int parity, cudaStream_t s) {
   double A[4], B[5];
   lsrk_coefficients(A, B);
-  cudaError_t e = cudaMemsetAsync(b->counters_d, 0, 5 * sizeof(int), s);
+  const int G = static_cast<int>(b->groups.size());
+  cudaError_t e = cudaMemsetAsync(b->counters_d, 0, 5 * G * sizeof(int), s);
   if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
-  for (int st = 0; st < 5; ++st) {
-    BParams bp{};
-    bp.inst = b->inst_d;
-    bp.tiles = b->tiles_d;
-    bp.ntiles = static_cast<int>(b->tiles.size());
-    bp.counter = b->counters_d + st;
-    bp.err = b->err_d;
-    bp.mode = 1;
-    bp.stage = st;
-    bp.parity = parity;
-    bp.a = st < 4 ? A[st] : B[4];
-    bp.b = B[st];
-    bp.last_stage = st == 4;
-    bp.nbt_off = prec == DG_PREC_FP64 ? b->nbt_off64 : b->nbt_off32;
-    e = prec == DG_PREC_FP64 ? launch_batch<double, double>(b, bp, b->smem64, s)
-                             : launch_batch<float, float>(b, bp, b->smem32, s);
-    if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
-  }
+  for (int st = 0; st < 5; ++st)
+    for (int gi = 0; gi < G; ++gi) {
+      const auto& g = b->groups[gi];
+      const bool r4 = uses_r4(b, g, prec);
+      BParams bp{};
+      bp.inst = b->inst_d;
+      bp.tiles = r4 ? g.tiles_r4_d : g.tiles_sm_d;
+      bp.ntiles = static_cast<int>(r4 ? g.tiles_r4.size() : g.tiles_sm.size());
+      bp.counter = b->counters_d + st * G + gi;
+      bp.err = b->err_d;
+      bp.mode = 1;
+      bp.stage = st;
+      bp.parity = parity;
+      bp.a = st < 4 ? A[st] : B[4];
+      bp.b = B[st];
+      bp.last_stage = st == 4;
+      bp.order = b->order;
+      bp.ninst = b->count;
+      bp.nbt_off = prec == DG_PREC_FP64 ? g.nbt_off64 : g.nbt_off32;
+      if (r4)
+        e = launch_batch4(g.n, b->threads4, bp, s);
+      else
+        e = prec == DG_PREC_FP64 ? launch_batch<double, double>(b, bp, g.smem64, s)
+                                 : launch_batch<float, float>(b, bp, g.smem32, s);
+      if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
+    }
   return DG_OK;
 }
 
@@ -378,6 +633,17 @@ dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out) {
     b->inst.push_back(I);
     b->npc.push_back(h->npc);
     b->n_dofs += h->n_dofs;
+    // group by (d, n)
+    int gi = 0;
+    while (gi < static_cast<int>(b->groups.size()) &&
+           !(b->groups[gi].d == h->d && b->groups[gi].n == h->n))
+      ++gi;
+    if (gi == static_cast<int>(b->groups.size())) {
+      b->groups.emplace_back();
+      b->groups.back().d = h->d;
+      b->groups.back().n = h->n;
+    }
+    b->groups[gi].members.push_back(m);
   }
   // tables for every n
   Tab1D<double> t64[kMaxN + 1];
@@ -394,7 +660,7 @@ dg_status dg_batch_create(int count, const dg_handle* handles, dg_batch* out) {
   if ((e = cudaMemcpyToSymbol(c_bt64, t64, sizeof(t64))) != cudaSuccess ||
       (e = cudaMemcpyToSymbol(c_bt32, t32, sizeof(t32))) != cudaSuccess ||
       (e = cudaMalloc(&b->inst_d, sizeof(BInst) * count)) != cudaSuccess ||
-      (e = cudaMalloc(&b->counters_d, 8 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->counters_d, 5 * b->groups.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&b->err_d, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(b->err_d, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -417,7 +683,7 @@ dg_status dg_batch_destroy(dg_batch b) {
 
 dg_status dg_batch_info(dg_batch b, long long* tiles, long long* n_dofs) {
   if (b == nullptr) return report(DG_ERR_INVALID_ARG, "batch is NULL");
-  if (tiles) *tiles = static_cast<long long>(b->tiles.size());
+  if (tiles) *tiles = tile_count(b, DG_PREC_FP32);
   if (n_dofs) *n_dofs = b->n_dofs;
   return DG_OK;
 }
@@ -429,8 +695,9 @@ dg_status dg_batch_rk_step(dg_batch b, double* const* u, void* const* w0, void* 
   if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
     return report(DG_ERR_INVALID_ARG, "batched precision must be DG_PREC_FP64 or DG_PREC_FP32");
   if (nsteps < 0) return report(DG_ERR_INVALID_ARG, "nsteps must be >= 0");
-  if (prec == DG_PREC_FP64 && b->smem64 == 0)
-    return report(DG_ERR_UNSUPPORTED, "FP64 batches need a smaller tile size");
+  for (const auto& g : b->groups)
+    if (prec == DG_PREC_FP64 && g.smem64 == 0)
+      return report(DG_ERR_UNSUPPORTED, "FP64 batches need a smaller tile size");
   for (int m = 0; m < b->count; ++m) {
     if (!u[m] || !w0[m] || !w1[m] || !std::isfinite(dt[m]))
       return report(DG_ERR_INVALID_ARG, "NULL vector or non-finite dt in batch member");
@@ -450,21 +717,11 @@ dg_status dg_batch_rk_step(dg_batch b, double* const* u, void* const* w0, void* 
   cudaError_t e = cudaMemcpyAsync(b->inst_d, b->inst.data(), sizeof(BInst) * b->count,
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
-  // w0 = u for every member (one persistent pass over all tiles)
-  {
-    BParams bp{};
-    bp.inst = b->inst_d;
-    bp.tiles = b->tiles_d;
-    bp.ntiles = static_cast<int>(b->tiles.size());
-    bp.counter = b->counters_d + 5;
-    bp.err = b->err_d;
-    bp.mode = 0;
-    bp.parity = 0;
-    if ((e = cudaMemsetAsync(b->counters_d + 5, 0, sizeof(int), s)) != cudaSuccess)
+  // w0 = u for every member (one streaming pass per member)
+  for (int m = 0; m < b->count; ++m) {
+    const long long n = static_cast<long long>(b->inst[m].ncells) * b->inst[m].npc;
+    if ((e = launch_convert(u[m], w0[m], prec == DG_PREC_FP32 ? 1 : 0, n, s)) != cudaSuccess)
       return report(DG_ERR_CUDA, cudaGetErrorString(e));
-    e = prec == DG_PREC_FP64 ? launch_batch<double, double>(b, bp, 0, s)
-                             : launch_batch<float, float>(b, bp, 0, s);
-    if (e != cudaSuccess) return report(DG_ERR_CUDA, cudaGetErrorString(e));
   }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess)
@@ -525,62 +782,129 @@ dg_status dg_batch_check(dg_batch b, void* stream) {
       (e = cudaMemcpy(&flag, b->err_d, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
       (e = cudaMemset(b->err_d, 0, sizeof(int))) != cudaSuccess)
     return report(DG_ERR_CUDA, cudaGetErrorString(e));
+  if (flag & 4) return report(DG_ERR_BOUNDS, "a batched kernel computed an index out of its range");
   if (flag & 1) return report(DG_ERR_NONFINITE, "a batched kernel produced a non-finite value");
+  return DG_OK;
+}
+
+dg_status dg_batch_set_launch_ex(dg_batch b, const dg_batch_launch* cfg) {
+  if (b == nullptr || cfg == nullptr) return report(DG_ERR_INVALID_ARG, "NULL argument");
+  if (cfg->tile_dofs < 64 || cfg->tile_dofs > (1 << 16) || cfg->threads < 32 || cfg->threads > 512 ||
+      cfg->threads % 32)
+    return report(DG_ERR_INVALID_ARG, "tile_dofs in [64, 65536], threads a multiple of 32 <= 512");
+  if (cfg->threads4 != 128 && cfg->threads4 != 256 && cfg->threads4 != 512)
+    return report(DG_ERR_INVALID_ARG, "threads4 must be 128, 256 or 512");
+  if (cfg->order < 0 || cfg->order > 7) return report(DG_ERR_INVALID_ARG, "order bits in [0, 7]");
+  if (cfg->r4_max_n < 1 || cfg->r4_max_n > kMaxN)
+    return report(DG_ERR_INVALID_ARG, "r4_max_n in [1, 6]");
+  for (const auto& g : b->groups)
+    if (g.d == 4 && g.n <= cfg->r4_max_n &&
+        (cfg->threads4 < g.n * g.n || (cfg->threads4 == 512 && g.n > 4)))
+      return report(DG_ERR_INVALID_ARG,
+                    "threads4 too small (or 512 with n > 4) for a 4D group of the register kernel");
+  const dg_batch_launch old{b->tile_dofs, b->threads, b->threads4, b->order, b->r4_max_n};
+  auto set = [b](const dg_batch_launch& c) {
+    b->tile_dofs = c.tile_dofs;
+    b->threads = c.threads;
+    b->threads4 = c.threads4;
+    b->order = c.order;
+    b->r4_max_n = c.r4_max_n;
+  };
+  set(*cfg);
+  dg_status st = build_tiles(b);
+  if (st != DG_OK) {
+    set(old);
+    build_tiles(b);
+  }
+  return st;
+}
+
+dg_status dg_batch_get_launch(dg_batch b, dg_batch_launch* cfg) {
+  if (b == nullptr || cfg == nullptr) return report(DG_ERR_INVALID_ARG, "NULL argument");
+  *cfg = dg_batch_launch{b->tile_dofs, b->threads, b->threads4, b->order, b->r4_max_n};
   return DG_OK;
 }
 
 dg_status dg_batch_set_launch(dg_batch b, int tile_dofs, int threads) {
   if (b == nullptr) return report(DG_ERR_INVALID_ARG, "batch is NULL");
-  if (tile_dofs < 64 || tile_dofs > (1 << 16) || threads < 32 || threads > 512 || threads % 32)
-    return report(DG_ERR_INVALID_ARG, "tile_dofs in [64, 65536], threads a multiple of 32 <= 512");
-  const int old_tile = b->tile_dofs, old_threads = b->threads;
-  b->tile_dofs = tile_dofs;
-  b->threads = threads;
-  dg_status st = build_tiles(b);
-  if (st != DG_OK) {
-    b->tile_dofs = old_tile;
-    b->threads = old_threads;
-    build_tiles(b);
-  }
-  return st;
+  const dg_batch_launch c{tile_dofs, threads, b->threads4, b->order, b->r4_max_n};
+  return dg_batch_set_launch_ex(b, &c);
 }
 
 dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void* const* w1,
                             const double* dt, int prec, void* stream, double* best_ms) {
   if (b == nullptr) return report(DG_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int tiles_c[] = {1024, 2048, 4096, 8192};
-  const int threads_c[] = {128, 256, 512};
+  // candidates: the shared-memory kernel's tile size and block size, the 4D
+  // register kernel's block size (cells per block = threads4 / n^2) and the
+  // order of the directions (both kernels); what does not apply to any group
+  // of this batch is not varied
+  bool any4 = false, anysm = false;
+  for (const auto& g : b->groups) {
+    if (prec == DG_PREC_FP32 && g.d == 4) any4 = true;
+    if (!(prec == DG_PREC_FP32 && g.d == 4 && g.n <= 4)) anysm = true;
+  }
+  b->trials.clear();
   double best = 1e300;
-  int bt = b->tile_dofs, bth = b->threads;
+  dg_batch_launch bcfg{b->tile_dofs, b->threads, b->threads4, b->order, b->r4_max_n};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   // time two steps per candidate (after one untimed step that captures its
   // graphs) on the caller's buffers: their contents are advanced, as the
   // header states
-  for (int tdofs : tiles_c)
-    for (int th : threads_c) {
-      if (dg_batch_set_launch(b, tdofs, th) != DG_OK) continue;
-      if (prec == DG_PREC_FP64 && b->smem64 == 0) continue;
-      if (dg_batch_rk_step(b, u, w0, w1, dt, 1, prec, stream) != DG_OK) continue;  // warm-up / capture
-      cudaEventRecord(e0, s);
-      if (dg_batch_rk_step(b, u, w0, w1, dt, 2, prec, stream) != DG_OK) continue;
-      cudaEventRecord(e1, s);
-      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms / 2 < best) {
-        best = ms / 2;
-        bt = tdofs;
-        bth = th;
-      }
+  auto trial = [&](const dg_batch_launch& c) {
+    if (dg_batch_set_launch_ex(b, &c) != DG_OK) return;
+    if (dg_batch_rk_step(b, u, w0, w1, dt, 1, prec, stream) != DG_OK) return;  // warm-up / capture
+    cudaEventRecord(e0, s);
+    if (dg_batch_rk_step(b, u, w0, w1, dt, 2, prec, stream) != DG_OK) return;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->trials.push_back(
+        dg_batch_trial{c.tile_dofs, c.threads, c.threads4, c.order, c.r4_max_n, 0.5 * ms});
+    if (ms / 2 < best) {
+      best = ms / 2;
+      bcfg = c;
     }
+  };
+  // The groups are separate launches whose times add up, so the parameters
+  // are tuned one after the other (coordinate descent):
+  // 1. which FP32 4D groups run the register kernel (n <= r4_max_n), then its
+  //    block size (cells per block) and which x and which v direction goes first;
+  if (any4) {
+    const dg_batch_launch base = bcfg;
+    for (int rn : {1, 3, 4, 5, 6}) trial(dg_batch_launch{base.tile_dofs, base.threads, 128, base.order, rn});
+    const dg_batch_launch b1 = bcfg;
+    if (b1.r4_max_n > 1)
+      for (int t4 : {128, 256, 512})
+        for (int o = 0; o < 4; ++o)
+          trial(dg_batch_launch{b1.tile_dofs, b1.threads, t4, (b1.order & 4) | o, b1.r4_max_n});
+  }
+  // 2. the shared-memory kernel: tile size x block size, then the direction order
+  if (anysm || bcfg.r4_max_n < 6) {
+    const dg_batch_launch base = bcfg;
+    for (int tdofs : {1024, 2048, 4096, 8192})
+      for (int th : {128, 256, 512})
+        trial(dg_batch_launch{tdofs, th, base.threads4, base.order, base.r4_max_n});
+    const dg_batch_launch b2 = bcfg;
+    trial(dg_batch_launch{b2.tile_dofs, b2.threads, b2.threads4, b2.order ^ 4, b2.r4_max_n});
+  }
+  if (b->trials.empty()) trial(bcfg);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  dg_status st = dg_batch_set_launch(b, bt, bth);
+  dg_status st = dg_batch_set_launch_ex(b, &bcfg);
   if (best_ms) *best_ms = best;
   return st;
+}
+
+dg_status dg_batch_autotune_record(dg_batch b, dg_batch_trial* trials, int max_trials, int* count) {
+  if (b == nullptr || count == nullptr) return report(DG_ERR_INVALID_ARG, "NULL argument");
+  *count = static_cast<int>(b->trials.size());
+  if (trials)
+    for (int i = 0; i < std::min(max_trials, *count); ++i) trials[i] = b->trials[i];
+  return DG_OK;
 }
 
 }  // extern "C"

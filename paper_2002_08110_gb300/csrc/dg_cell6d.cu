@@ -358,7 +358,10 @@ __global__ void __launch_bounds__(64, 4) k_cell6d4(const KParams p) {
   unsigned item = s_item;
   if (item >= npencils) return;
   Mover<TIN> mv{sm6, &pipe};
-  auto cellp = [&](unsigned c) { return src + static_cast<size_t>(c) * 4096; };
+  auto cellp = [&](unsigned c) {
+    DG_BOUND(p.err, c, p.ncells);
+    return src + static_cast<size_t>(c) * 4096;
+  };
   auto setup = [&](unsigned c, float (&sp)[6], unsigned (&nbr)[6]) {
     const unsigned cv = c / ncx, cx = c - cv * ncx;
     const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * 64 + t) * 3;
@@ -1032,9 +1035,14 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
   if (item >= npencils) return;
   Mover2<TIN> mv{sm6, &pipe, &tmap};
   int slot = 0;
-  auto issue = [&](int b, unsigned c) { mv.issue(b, c, src, T_, t, h); };
+  auto issue = [&](int b, unsigned c) {
+    DG_BOUND(p.err, c, p.ncells);
+    mv.issue(b, c, src, T_, t, h);
+  };
   auto v3c = [&](const PencilInfo& pi, int i) {
-    return V3L + (pi.fwd ? static_cast<unsigned>(i) : static_cast<unsigned>(N3 - 1 - i));
+    unsigned c5 = V3L + (pi.fwd ? static_cast<unsigned>(i) : static_cast<unsigned>(N3 - 1 - i));
+    DG_BOUND(p.err, c5, p.ncell[5]);
+    return c5;
   };
   // speeds of the thread's nodes and the upwind neighbours of cell i of a pencil
   auto setup = [&](const PencilInfo& pi, int i, unsigned& cell, float (&sp)[6],
@@ -1087,6 +1095,10 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     }
     const bool has_next = next_item < npencils;
     const bool need_v3 = i == 0;    // the first cell's upwind v3 neighbour is not carried
+    DG_BOUND(p.err, cell, p.ncells);
+    DG_BOUND(p.err, nbr[3], p.ncells);
+    DG_BOUND(p.err, nbr[4], p.ncells);
+    DG_BOUND(p.err, nbr[5], p.ncells);
     // the next cell's upwind x1 and x2 neighbours (prefetched during phase V);
     // its full setup follows at the end of this iteration
     unsigned next = 0, nx0 = 0, nx1 = 0;

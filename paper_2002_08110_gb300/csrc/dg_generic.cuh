@@ -239,7 +239,11 @@ __global__ void __launch_bounds__(512) k_generic(const KParams p) {
         const int cj = static_cast<int>((cell / st) % nj);
         ci[2 + 2 * j] = cj == 0 ? cell + (nj - 1) * st : cell - st;
         ci[3 + 2 * j] = cj == nj - 1 ? cell - (nj - 1) * st : cell + st;
+        DG_BOUND(p.err, ci[2 + 2 * j], p.ncells);
+        DG_BOUND(p.err, ci[3 + 2 * j], p.ncells);
       }
+      DG_BOUND(p.err, ci[0], p.ncx);
+      DG_BOUND(p.err, ci[1], p.ncells / p.ncx);
     }
     __syncthreads();
 

@@ -8,6 +8,26 @@
 
 #include "../../include/dg.h"
 
+// Bounds-check build (compiled with -DDG_BOUNDS_CHECK, library
+// libdg_bounds.so): every computed cell, neighbour, tile and slab index is
+// checked against its range before it is used; a violation latches bit 2 (4)
+// of the device error word, which dg_check reports as DG_ERR_BOUNDS, and the
+// index is replaced by 0 so that nothing traps and nothing is read or
+// written out of range.  In the normal build the check compiles to nothing.
+#ifdef DG_BOUNDS_CHECK
+#define DG_BOUND(err, idx, n)                                                          \
+  do {                                                                                 \
+    if (static_cast<unsigned long long>(idx) >= static_cast<unsigned long long>(n)) { \
+      atomicOr((err), 4);                                                              \
+      (idx) = 0;                                                                       \
+    }                                                                                  \
+  } while (0)
+#else
+#define DG_BOUND(err, idx, n) \
+  do {                        \
+  } while (0)
+#endif
+
 namespace dg {
 
 constexpr int kMaxDim = 6;

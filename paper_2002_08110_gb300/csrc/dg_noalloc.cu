@@ -27,7 +27,9 @@ std::mutex g_mutex;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on device `dev` (which must be the
-// current device); looked up once per device.
+// current device); looked up once per device and kept for the life of the
+// process.  The address belongs to the device context that was current at
+// the lookup, so the cache is not valid across cudaDeviceReset.
 cudaError_t scratch_on(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (g_scratch_ptr[dev] == nullptr) {
@@ -115,7 +117,8 @@ __global__ void k_fold(const double* __restrict__ partial, int blocks, double* _
 }  // namespace
 
 extern "C" dg_status dg_integrals_noalloc(const double* u, long long n_cells, int dim, int degree,
-                                          double det_jacobian, double* out, void* stream) {
+                                          int basis, double det_jacobian, double* out,
+                                          void* stream) {
   char msg[256];
   if (u == nullptr || out == nullptr) return dg::report(DG_ERR_INVALID_ARG, "u and out must not be NULL");
   if (reinterpret_cast<uintptr_t>(u) % 16 != 0)
@@ -123,6 +126,14 @@ extern "C" dg_status dg_integrals_noalloc(const double* u, long long n_cells, in
   if (dim < 2 || dim > 6 || degree < 1 || degree > 5)
     return dg::report(DG_ERR_UNSUPPORTED, "dim must be in [2, 6] and degree in [1, 5]");
   if (n_cells < 1) return dg::report(DG_ERR_INVALID_ARG, "n_cells must be >= 1");
+  // the collocated bases integrate at their own nodes; the Lobatto-node,
+  // Gauss-quadrature element needs a change of basis (dg_integrals does it)
+  if (basis == DG_BASIS_GLL_GAUSS)
+    return dg::report(DG_ERR_UNSUPPORTED,
+                      "dg_integrals_noalloc covers the collocated bases only; use dg_integrals "
+                      "for DG_BASIS_GLL_GAUSS");
+  if (basis != DG_BASIS_GL && basis != DG_BASIS_GLL)
+    return dg::report(DG_ERR_INVALID_ARG, "unknown basis");
   if (!(det_jacobian > 0.0) || !std::isfinite(det_jacobian))
     return dg::report(DG_ERR_INVALID_ARG, "det_jacobian must be positive and finite");
   const int n = degree + 1;
@@ -149,7 +160,10 @@ extern "C" dg_status dg_integrals_noalloc(const double* u, long long n_cells, in
   }
   Weights wt{};
   double nodes[dg::kMaxN];
-  dg::gauss_legendre(n, nodes, wt.w);
+  if (basis == DG_BASIS_GL)
+    dg::gauss_legendre(n, nodes, wt.w);
+  else
+    dg::gauss_lobatto(n, nodes, wt.w);
   const int blocks = static_cast<int>((n_dofs + kChunk - 1) / kChunk);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // every partial slot read by k_fold is written by this call first, so the

@@ -23,7 +23,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_version_and_reference_nodes(lib):
-    assert lib.dg_version() == 3
+    assert lib.dg_version() == 4
     for k in range(6):
         x = np.zeros(k + 1)
         w = np.zeros(k + 1)

@@ -111,3 +111,52 @@ def test_batch_rejects_unsupported_members():
     with pytest.raises(DGError):
         DGBatch([dg])
     dg.close()
+
+
+def test_batch_launch_configurations_and_autotune_record():
+    """Every block size of the 4D register kernel (cells per block), every
+    direction order and every split of the 4D groups between the register and
+    the shared-memory kernel gives the single-problem result; the autotuner's
+    record lists what it timed and the configuration it kept is the fastest."""
+    from paper_2002_08110_gb300 import DG, DGBatch, DGError, reference_nodes
+    ws = _members(count=6, seed=7)
+    dgs = [DG(**W.dg_kwargs(w)) for w in ws]
+    u0 = _states(ws, lambda k: reference_nodes(k)[0])
+    dts = [0.5 * W.time_step(w)[0] for w in ws]
+    refs = []
+    for dg, u, dt in zip(dgs, u0, dts):
+        x = u.clone()
+        dg.rk_step(x, dt, nsteps=2, prec=1)
+        refs.append(x)
+    batch = DGBatch(dgs)
+    max_n = max(w.n for w in ws if w.d == 4)
+    for t4, order, r4 in [(128, 0, 4), (256, 1, 6), (512, 2, 4), (128, 3, 6), (256, 4, 1),
+                          (512, 7, 6)]:
+        if t4 == 512 and max_n > 4 and r4 >= max_n:
+            with pytest.raises(DGError):
+                batch.set_launch(4096, 256, threads4=t4, order=order, r4_max_n=r4)
+            continue
+        batch.set_launch(2048, 128, threads4=t4, order=order, r4_max_n=r4)
+        assert batch.get_launch() == {"tile_dofs": 2048, "threads": 128, "threads4": t4,
+                                      "order": order, "r4_max_n": r4}
+        us = [u.clone() for u in u0]
+        w0s = [torch.empty(w.n_dofs, device="cuda").float() for w in ws]
+        w1s = [torch.empty(w.n_dofs, device="cuda").float() for w in ws]
+        batch.rk_step(us, w0s, w1s, dts, nsteps=2, prec=1)
+        batch.check()
+        for u, ref in zip(us, refs):
+            assert torch.max(torch.abs(u - ref)) <= 1e-6 * torch.max(torch.abs(ref)), (t4, order, r4)
+    us = [u.clone() for u in u0]
+    w0s = [torch.empty(w.n_dofs, device="cuda").float() for w in ws]
+    w1s = [torch.empty(w.n_dofs, device="cuda").float() for w in ws]
+    best = batch.autotune(us, w0s, w1s, dts, prec=1)
+    rec = batch.autotune_record()
+    assert len(rec) >= 8
+    assert len({r["r4_max_n"] for r in rec}) >= 3
+    assert len({r["order"] for r in rec}) >= 2
+    assert abs(min(r["ms"] for r in rec) - best) <= 1e-9
+    kept = batch.get_launch()
+    assert any(all(r[k] == kept[k] for k in kept) and r["ms"] == best for r in rec)
+    batch.close()
+    for dg in dgs:
+        dg.close()
