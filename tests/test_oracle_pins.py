@@ -724,13 +724,28 @@ def _lagrange_1d_by_fit(nodes, x):
     return V, D
 
 
+def _rule_independent(n, basis):
+    """The n-point Gauss-Legendre ("gl") or Gauss-Lobatto ("gllc") rule from
+    scipy's Golub-Welsch roots (the Lobatto interior points are the
+    Gauss-Jacobi(1, 1) points) with weights from the moment equations, not
+    from the oracle's quadrature module."""
+    from scipy.special import roots_jacobi, roots_legendre
+    if basis == "gl":
+        x, w = roots_legendre(n)
+        return np.asarray(x), np.asarray(w)
+    x = np.concatenate([[-1.0], roots_jacobi(n - 2, 1.0, 1.0)[0] if n > 2 else [], [1.0]])
+    V = np.vander(x, n, increasing=True).T            # V[m, i] = x_i^m
+    mom = np.array([(1 - (-1) ** (m + 1)) / (m + 1) for m in range(n)])
+    return x, np.linalg.solve(V, mom)
+
+
 def _term_scale_dense(p, u):
     """|M^{-1}| sum over terms |T_t| |u| with every term of the weak form as a
     dense Kronecker matrix (cell terms per direction, outflow-face terms and
     upwind-neighbour face terms per face), built from independently fitted
     1D tables.  Collocation bases only (M diagonal)."""
     d, n = p.d, p.n
-    zeta, wq = (npleg.leggauss(n) if p.basis == "gl" else gauss_lobatto(n))
+    zeta, wq = _rule_independent(n, p.basis)
     B, Bd = _lagrange_1d_by_fit(zeta, zeta)
     lp, _ = _lagrange_1d_by_fit(zeta, np.array([1.0]))
     lm, _ = _lagrange_1d_by_fit(zeta, np.array([-1.0]))
