@@ -169,16 +169,8 @@ dg_status ensure_scratch(dg_ctx* h, int prec) {
   return DG_OK;
 }
 
-cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
-                        cudaStream_t s) {
-  if (cfg.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides && !h->curved) {
-    cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
-    if (e != cudaErrorNotSupported) return e;
-  }
-  if (cfg.variant == 2 && h->d == 4 && h->dx == 2 && !h->curved) {
-    cudaError_t e = launch_cell_4d(h->n, combo, p, cfg, s);
-    if (e != cudaErrorNotSupported) return e;
-  }
+cudaError_t launch_generic_any(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
+                               cudaStream_t s) {
   if (p.v3_n > 0) return cudaErrorInvalidValue;     // the generic kernels walk whole cells only
   switch (h->d) {
     case 2: return launch_cell_d2(h->n, combo, p, cfg, s);
@@ -188,6 +180,58 @@ cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg&
     case 6: return launch_cell_d6(h->n, combo, p, cfg, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
+                        cudaStream_t s) {
+  // the negated-field forward operator exists in the generic kernel only
+  if (p.negate) return launch_generic_any(h, combo, p, cfg, s);
+  if (cfg.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides && !h->curved) {
+    cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  if (cfg.variant == 2 && h->d == 4 && h->dx == 2 && !h->curved) {
+    cudaError_t e = launch_cell_4d(h->n, combo, p, cfg, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return launch_generic_any(h, combo, p, cfg, s);
+}
+
+// Does launch_cell run the generic kernel for this precision (no specialised
+// kernel covers the handle's dimensions, degree, field and launch variant)?
+bool generic_runs(const dg_ctx* h, int prec) {
+  if (prec == DG_PREC_FP64 || h->curved) return true;
+  const LaunchCfg& c = h->cfg[prec];
+  if (c.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides && h->ncells < (1LL << 31))
+    return false;
+  if (c.variant == 2 && h->d == 4 && h->dx == 2 && h->ncells < (1LL << 31)) return false;
+  return true;
+}
+
+// Node weights W_q = prod_i w_{q_i} of the handle's basis and their inverses
+// (device, 2 npc doubles), for the adjoint steps of the generic path.
+dg_status ensure_wnode(dg_ctx* h) {
+  if (h->wnode_d) return DG_OK;
+  std::vector<double> w(2 * static_cast<size_t>(h->npc));
+  for (int q = 0; q < h->npc; ++q) {
+    double f = 1.0;
+    int r = q;
+    for (int j = 0; j < h->d; ++j) {
+      f *= h->tables.t64.w[r % h->n];
+      r /= h->n;
+    }
+    w[q] = f;
+    w[h->npc + q] = 1.0 / f;
+  }
+  cudaError_t e = cudaMalloc(&h->wnode_d, w.size() * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->wnode_d, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(h->wnode_d);
+    h->wnode_d = nullptr;
+    return cuda_fail(e, "node weights");
+  }
+  return DG_OK;
 }
 
 // DG_BASIS_GLL_GAUSS: four FP64 temporaries of n_dofs values (two vectors
@@ -270,7 +314,8 @@ dg_status enqueue_stage(dg_handle h, const void* w_in, void* w_out, double* u, i
   p.dst = w_out;
   p.u = u;
   p.mode = 1;
-  p.adjoint = adjoint;
+  p.adjoint = adjoint == 1 ? 1 : 0;
+  p.negate = adjoint == 2 ? 1 : 0;     // 2: L(-a) on weight-scaled states (rk_step_core)
   p.last_stage = stage == 4;
   p.a_dt = stage < 4 ? kRkA[stage] * dt : kRkB[4] * dt;
   p.b_dt = kRkB[stage] * dt;
@@ -339,6 +384,7 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->err_d);
   cudaFree(h->work_d);
   cudaFree(h->scratch);
+  cudaFree(h->wnode_d);
   cudaFree(h->partial);
   cudaFree(h->field_flags_d);
   cudaFree(h->vp_rho);
@@ -1225,6 +1271,7 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
   if (nsteps == 0) return DG_OK;
   adjoint = adjoint ? 1 : 0;
   if ((st = ensure_scratch(h, prec)) != DG_OK) return st;
+  if (adjoint && (st = ensure_wnode(h)) != DG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (h->basis != DG_BASIS_GLL_GAUSS) return rk_step_core(h, u, w0, w1, dt, nsteps, prec, adjoint, s);
   // R(dt L) = V^{-1} R(dt L_GL) V: the steps run on the state at the Gauss points
@@ -1239,7 +1286,20 @@ dg_status dg_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, int 
 dg_status rk_step_core(dg_handle h, double* u, void* w0, void* w1, double dt, int nsteps, int prec,
                        int adjoint, cudaStream_t s) {
   dg_status st;
-  cudaError_t e = launch_convert(u, w0, prec == DG_PREC_FP32, h->n_dofs, s);
+  cudaError_t e;
+  if (adjoint == 1 && generic_runs(h, prec) && h->wnode_d != nullptr) {
+    // L^T = M L(-a) M^{-1} with M = |J| diag(W) on an affine mesh, so the
+    // adjoint steps R(dt L^T) = W R(dt L(-a)) W^{-1}: scale the state by the
+    // inverse node weights, step with the negated field (no per-value weights
+    // inside the generic kernel), scale back
+    if ((e = launch_scale_nodes(u, h->ncells, h->npc, h->wnode_d + h->npc, s)) != cudaSuccess)
+      return cuda_fail(e, "adjoint scaling");
+    if ((st = rk_step_core(h, u, w0, w1, dt, nsteps, prec, 2, s)) != DG_OK) return st;
+    if ((e = launch_scale_nodes(u, h->ncells, h->npc, h->wnode_d, s)) != cudaSuccess)
+      return cuda_fail(e, "adjoint scaling");
+    return DG_OK;
+  }
+  e = launch_convert(u, w0, prec == DG_PREC_FP32, h->n_dofs, s);
   if (e != cudaSuccess) return cuda_fail(e, "stage-vector initialisation");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return cuda_fail(e, "capture query");

@@ -151,7 +151,7 @@ __device__ __forceinline__ void sweep_dir(const KParams& p, const Tab1D<TC>& T, 
     // only, v directions on the x node only (phase-space structure)
     TC cj = J < p.dx ? static_cast<const TC*>(p.cx_tab)[(cv * nqv + qv) * p.dx + J]
                      : static_cast<const TC*>(p.cv_tab)[(cx * nqx + qx) * p.dv + (J - p.dx)];
-    if (p.adjoint) cj = -cj;
+    if (p.adjoint || p.negate) cj = -cj;
     if (cj == TC(0)) continue;
     const bool pos = cj > TC(0);
     TC uu[N];

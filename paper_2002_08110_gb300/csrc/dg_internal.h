@@ -100,6 +100,9 @@ struct KParams {
   unsigned* work;           // work-queue counter of the persistent kernels
   int mode;                 // 0 = apply, 1 = LSRK stage
   int adjoint;              // 1: L^T = M L(-a) M^{-1}
+  int negate;               // 1: L(-a), the forward operator of the negated field
+                            // (generic kernel only; the adjoint steps of the generic
+                            // path run it on states scaled by the node weights)
   int last_stage;           // stage mode: w_out = u_new
   double a_dt, b_dt;        // stage mode coefficients (a_s dt, b_s dt)
   int tab;                  // constant-table set of the 6D kernels (0 GL, 1 GLL)
@@ -194,6 +197,8 @@ cudaError_t launch_basis_change(const void* x, int x_is_float, void* y, int y_is
 cudaError_t launch_sub_to_f32(const double* a, const double* b, float* y, long long n, cudaStream_t s);
 cudaError_t launch_add_f32(const double* k, const float* y, double* z, long long n, cudaStream_t s);
 cudaError_t launch_axpy(double* x, double sc, const double* r, long long n, cudaStream_t s);
+// u[cell * npc + q] *= f[q] for every cell (dg_misc.cu).
+cudaError_t launch_scale_nodes(double* u, long long ncells, int npc, const double* f, cudaStream_t s);
 cudaError_t launch_charge_density(const void* f, int f_is_float, long long ncx, long long ncv,
                                   int npc, int nqx, int nqv, int dv, int n,
                                   const Tab1D<double>& t, double detJv, double* rho,
@@ -222,6 +227,7 @@ struct dg_ctx {
   double* geo_f64 = nullptr; float* geo_f32 = nullptr;
   double* ax64 = nullptr; float* ax32 = nullptr;
   double* jx_d = nullptr;   // |J_x| per x point (FP64) for the integrals
+  double* wnode_d = nullptr;  // node weights W_q = prod_i w_{q_i} and their inverses (2 npc)
   double* bc_tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // DG_BASIS_GLL_GAUSS temporaries
   double a_const[dg::kMaxDim] = {0};
   double speed_sum = 0.0;

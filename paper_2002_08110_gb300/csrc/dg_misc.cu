@@ -441,4 +441,19 @@ cudaError_t launch_axpy(double* x, double sc, const double* r, long long n, cuda
   return cudaGetLastError();
 }
 
+// Scales every cell's values by a per-node factor (the node weights of the
+// adjoint steps): blocks stride over cells, threads over the cell's nodes.
+__global__ void k_scale_nodes(double* __restrict__ u, long long ncells, int npc,
+                              const double* __restrict__ f) {
+  for (long long c = blockIdx.x; c < ncells; c += gridDim.x)
+    for (int q = threadIdx.x; q < npc; q += blockDim.x) u[c * npc + q] *= f[q];
+}
+
+cudaError_t launch_scale_nodes(double* u, long long ncells, int npc, const double* f, cudaStream_t s) {
+  const int threads = npc >= 256 ? 256 : ((npc + 31) / 32) * 32;
+  const long long grid = std::min<long long>(ncells, 152LL * 32);
+  k_scale_nodes<<<static_cast<unsigned>(std::max<long long>(1, grid)), threads, 0, s>>>(u, ncells, npc, f);
+  return cudaGetLastError();
+}
+
 }  // namespace dg
