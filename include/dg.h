@@ -494,7 +494,9 @@ typedef struct {
     int threads;     /* shared-memory kernel: threads per block; default 256 */
     int threads4;    /* 4D register kernel: threads per block, 128, 256 or 512
                         (n^2 per cell, so threads4 / n^2 cells per block and
-                        per tile; 512 only for n <= 4); default 128           */
+                        per tile; 512 only for n <= 4); default 128.  n = 6
+                        runs a pair-split kernel of its own (two threads per
+                        column and row, 3 cells per 224-thread block)        */
     int order;       /* direction order, bits: 1 = the second x direction
                         first, 2 = the second v direction first (4D register
                         kernel); 4 = all directions in reverse order (shared-

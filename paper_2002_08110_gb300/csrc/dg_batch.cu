@@ -59,7 +59,7 @@ struct BParams {
   int ntiles;
   int* counter;
   int* err;
-  int mode;        // 0: convert u -> w0, 1: stage
+  int mode;        // 1: stage (the only mode)
   int stage, parity;
   int nbt_off;     // byte offset of the per-cell neighbour table in shared memory
   double a, b;     // a_s (or b_4 at the last stage), b_s
@@ -94,14 +94,57 @@ __device__ __forceinline__ int nb_cell(const BInst& I, int cell, int j, int s, i
   return nb;
 }
 
+// The lines of direction J (compile-time, so the line stride N^J is a
+// constant) of a tile's cells, one line per thread and round.
+template <int D, int N, int J, typename TC, typename TW>
+__device__ __forceinline__ void bdir(const BInst& I, const TW* src, const TC* su, TC* sr, const int* nbt,
+                                     int nc) {
+  constexpr int NP = Pow<N, D>::v;
+  constexpr int NL = NP / N;
+  constexpr int sj = Pow<N, J>::v;
+  const Tab1D<TC>& T = btab<TC>(N);
+  const TC cj = speed<TC>(I, J);
+  if (cj == TC(0)) return;
+  const bool pos = cj > TC(0);
+  for (int it = threadIdx.x; it < nc * NL; it += blockDim.x) {
+    const int c = it / NL;
+    const int l = it - c * NL;
+    const int base = (l % sj) + (l / sj) * sj * N;
+    TC uu[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) uu[q] = su[c * NP + base + q * sj];
+    const int nb = nbt[c * 2 * kBatchMaxDim + 2 * J + (pos ? 0 : 1)];
+    const TW* ns = src + static_cast<size_t>(nb) * NP + base;
+    TC t = TC(0);
+#pragma unroll
+    for (int q = 0; q < N; ++q) t += (pos ? T.lp[q] : T.lm[q]) * ns[q * sj];
+    TC* r = sr + c * NP + base;
+    if (pos) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        TC acc = T.Lm[q] * t;
+#pragma unroll
+        for (int s = 0; s < N; ++s) acc += T.Gp[q * N + s] * uu[s];
+        r[q * sj] += cj * acc;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        TC acc = -T.Lp[q] * t;
+#pragma unroll
+        for (int s = 0; s < N; ++s) acc += T.Gn[q * N + s] * uu[s];
+        r[q * sj] += cj * acc;
+      }
+    }
+  }
+}
+
 // One tile of member I: cells [c0, c0 + nc), d = D, n = N, compute type TC,
 // stage vectors of type TW (TC == TW here).
 template <int D, int N, typename TC, typename TW>
 __device__ void process_tile(const BInst& I, const BParams& bp, int c0, int nc, TC* su, TC* sr,
                              int* nbt, int& bad) {
   constexpr int NP = Pow<N, D>::v;
-  constexpr int NL = NP / N;
-  const Tab1D<TC>& T = btab<TC>(N);
   const TW* src = static_cast<const TW*>(I.w[(bp.stage + bp.parity) & 1]);
   TW* dst = static_cast<TW*>(const_cast<void*>(I.w[(bp.stage + 1 + bp.parity) & 1]));
   const size_t base0 = static_cast<size_t>(c0) * NP;
@@ -117,47 +160,30 @@ __device__ void process_tile(const BInst& I, const BParams& bp, int c0, int nc, 
       nbt[c * 2 * kBatchMaxDim + 2 * j + 1] = nb_cell(I, c0 + c, j, 1, bp.err);
     }
   __syncthreads();
-#pragma unroll
-  for (int jj = 0; jj < D; ++jj) {
-    const int j = (bp.order & 4) ? D - 1 - jj : jj;
-    int sj = 1;
-    for (int m = 0; m < j; ++m) sj *= N;
-    const TC cj = speed<TC>(I, j);
-    if (cj != TC(0)) {
-      const bool pos = cj > TC(0);
-      for (int it = threadIdx.x; it < nc * NL; it += blockDim.x) {
-        const int c = it / NL;
-        const int l = it - c * NL;
-        const int base = (l % sj) + (l / sj) * sj * N;
-        TC uu[N];
-#pragma unroll
-        for (int q = 0; q < N; ++q) uu[q] = su[c * NP + base + q * sj];
-        const int nb = nbt[c * 2 * kBatchMaxDim + 2 * j + (pos ? 0 : 1)];
-        const TW* ns = src + static_cast<size_t>(nb) * NP + base;
-        TC t = TC(0);
-#pragma unroll
-        for (int q = 0; q < N; ++q) t += (pos ? T.lp[q] : T.lm[q]) * ns[q * sj];
-        TC* r = sr + c * NP + base;
-        if (pos) {
-#pragma unroll
-          for (int q = 0; q < N; ++q) {
-            TC acc = T.Lm[q] * t;
-#pragma unroll
-            for (int s = 0; s < N; ++s) acc += T.Gp[q * N + s] * uu[s];
-            r[q * sj] += cj * acc;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < N; ++q) {
-            TC acc = -T.Lp[q] * t;
-#pragma unroll
-            for (int s = 0; s < N; ++s) acc += T.Gn[q * N + s] * uu[s];
-            r[q * sj] += cj * acc;
-          }
-        }
-      }
+  // the directions in natural order, or reversed (order bit 2, FP32
+  // sweeps); each direction its own instantiation
+  if (sizeof(TC) == 4 && (bp.order & 4)) {
+    if constexpr (D > 3) {
+      bdir<D, N, (D > 3 ? 3 : 0), TC, TW>(I, src, su, sr, nbt, nc);
+      __syncthreads();
     }
+    bdir<D, N, 2, TC, TW>(I, src, su, sr, nbt, nc);
     __syncthreads();
+    bdir<D, N, 1, TC, TW>(I, src, su, sr, nbt, nc);
+    __syncthreads();
+    bdir<D, N, 0, TC, TW>(I, src, su, sr, nbt, nc);
+    __syncthreads();
+  } else {
+    bdir<D, N, 0, TC, TW>(I, src, su, sr, nbt, nc);
+    __syncthreads();
+    bdir<D, N, 1, TC, TW>(I, src, su, sr, nbt, nc);
+    __syncthreads();
+    bdir<D, N, 2, TC, TW>(I, src, su, sr, nbt, nc);
+    __syncthreads();
+    if constexpr (D > 3) {
+      bdir<D, N, (D > 3 ? 3 : 0), TC, TW>(I, src, su, sr, nbt, nc);
+      __syncthreads();
+    }
   }
   const double a_dt = bp.a * I.dt, b_dt = bp.b * I.dt;
   for (int i = threadIdx.x; i < nc * NP; i += blockDim.x) {
@@ -184,31 +210,28 @@ __global__ void __launch_bounds__(512) k_batch(const BParams bp) {
   extern __shared__ __align__(16) unsigned char bsm[];
   __shared__ int s_tile;
   int bad = 0;
+  if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
     __syncthreads();
     const int tix = s_tile;
     __syncthreads();
     if (tix >= bp.ntiles) break;
+    // the next tile is asked for now; its number is needed only at the end
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(bp.counter, 1);
     const Tile tl = bp.tiles[tix];
 #ifdef DG_BOUNDS_CHECK
     // a tile names a member and a run of its cells
     if (tl.inst < 0 || tl.inst >= bp.ninst || tl.cell0 < 0 || tl.ncells < 1 ||
         tl.cell0 + tl.ncells > bp.inst[tl.inst < 0 || tl.inst >= bp.ninst ? 0 : tl.inst].ncells) {
-      if (threadIdx.x == 0) atomicOr(bp.err, 4);
-      __syncthreads();
+      if (threadIdx.x == 0) {
+        atomicOr(bp.err, 4);
+        s_tile = next;
+      }
       continue;
     }
 #endif
     const BInst I = bp.inst[tl.inst];
-    if (bp.mode == 0) {
-      TW* w0 = static_cast<TW*>(const_cast<void*>(I.w[bp.parity & 1]));
-      const size_t b0 = static_cast<size_t>(tl.cell0) * I.npc;
-      const size_t cnt = static_cast<size_t>(tl.ncells) * I.npc;
-      for (size_t i = threadIdx.x; i < cnt; i += blockDim.x)
-        w0[b0 + i] = cvt<TW>(I.u[b0 + i]);
-      continue;
-    }
     TC* su = reinterpret_cast<TC*>(bsm);
     const int cap = tl.ncells * I.npc;
     TC* sr = su + cap;
@@ -226,6 +249,7 @@ __global__ void __launch_bounds__(512) k_batch(const BParams bp) {
       case 4 * 8 + 6: process_tile<4, 6, TC, TW>(I, bp, tl.cell0, tl.ncells, su, sr, nbt, bad); break;
       default: break;
     }
+    if (threadIdx.x == 0) s_tile = next;
   }
   if (bad) atomicOr(bp.err, 1);
 }
@@ -247,18 +271,24 @@ __global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
   const int c = threadIdx.x / S;
   const int k = threadIdx.x - c * S;
   float nanacc = 0.f;
+  if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
     __syncthreads();
     const int tix = s_tile;
     if (tix >= bp.ntiles) break;
+    // the next tile is asked for now; its number is needed only at the end
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(bp.counter, 1);
     const Tile tl = bp.tiles[tix];
 #ifdef DG_BOUNDS_CHECK
     // a tile names a member and a run of its cells
     if (tl.inst < 0 || tl.inst >= bp.ninst || tl.cell0 < 0 || tl.ncells < 1 ||
         tl.cell0 + tl.ncells > bp.inst[tl.inst < 0 || tl.inst >= bp.ninst ? 0 : tl.inst].ncells) {
-      if (threadIdx.x == 0) atomicOr(bp.err, 4);
-      __syncthreads();
+      __syncthreads();      // every thread has read s_tile
+      if (threadIdx.x == 0) {
+        atomicOr(bp.err, 4);
+        s_tile = next;
+      }
       continue;
     }
 #endif
@@ -366,8 +396,82 @@ __global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
       }
     }
     __syncthreads();        // su / sr and s_tile are reused by the next tile
+    if (threadIdx.x == 0) s_tile = next;
   }
   if (nanacc != 0.f) atomicOr(bp.err, 1);
+}
+
+// n = 6: the pair-split register kernel (dg_cell4d.cuh), 3 cells per tile
+// and per 224-thread block.
+constexpr int kCpb6 = 3, kThreads6 = 224;
+
+__global__ void __launch_bounds__(kThreads6, 2) k_batch4p(const BParams bp) {
+  extern __shared__ __align__(16) float bsm4p[];
+  float* const su = bsm4p;
+  float* const sr = bsm4p + kCpb6 * kPS * kPad6;
+  __shared__ int s_tile;
+  bool bad = false;
+  if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
+  for (;;) {
+    __syncthreads();
+    const int tix = s_tile;
+    if (tix >= bp.ntiles) break;
+    // the next tile is asked for now; its number is needed only at the end
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(bp.counter, 1);
+    const Tile tl = bp.tiles[tix];
+#ifdef DG_BOUNDS_CHECK
+    if (tl.inst < 0 || tl.inst >= bp.ninst || tl.cell0 < 0 || tl.ncells < 1 || tl.ncells > kCpb6 ||
+        tl.cell0 + tl.ncells > bp.inst[tl.inst < 0 || tl.inst >= bp.ninst ? 0 : tl.inst].ncells) {
+      __syncthreads();      // every thread has read s_tile
+      if (threadIdx.x == 0) {
+        atomicOr(bp.err, 4);
+        s_tile = next;
+      }
+      continue;
+    }
+#endif
+    const BInst& I = bp.inst[tl.inst];
+    int ncell[4];
+    unsigned cst[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ncell[j] = I.ncell[j];
+      cst[j] = static_cast<unsigned>(I.cstride[j]);
+    }
+    const float s0 = I.c32[0], s1 = I.c32[1], s2 = I.c32[2], s3 = I.c32[3];
+    auto speeds = [&](unsigned, const unsigned (&)[4], int, float& c0, float& c1, float& e0,
+                      float& e1) {
+      c0 = s0;
+      c1 = s1;
+      e0 = s2;
+      e1 = s3;
+    };
+    const float* src = static_cast<const float*>(I.w[(bp.stage + bp.parity) & 1]);
+    float* dst = static_cast<float*>(const_cast<void*>(I.w[(bp.stage + 1 + bp.parity) & 1]));
+    bad |= cell4p_block<float, float, 1, false, kCpb6>(
+        src, dst, I.u, static_cast<unsigned>(tl.cell0), tl.ncells, static_cast<unsigned>(I.ncells), ncell,
+        cst, static_cast<float>(bp.b * I.dt), static_cast<float>(bp.a * I.dt), bp.a * I.dt,
+        bp.last_stage != 0, speeds, c_bt32[6], su, sr, bp.err);
+    __syncthreads();        // su / sr and s_tile are reused by the next tile
+    if (threadIdx.x == 0) s_tile = next;
+  }
+  if (bad) atomicOr(bp.err, 1);
+}
+
+cudaError_t launch_batch4p(const BParams& bp, cudaStream_t s) {
+  const size_t smem = 2 * static_cast<size_t>(kCpb6) * kPS * kPad6 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_batch4p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch4p, kThreads6, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(bp.ntiles, std::max(1, sms * std::max(1, per_sm)));
+  k_batch4p<<<std::max(1, grid), kThreads6, smem, s>>>(bp);
+  return cudaGetLastError();
 }
 
 template <int N>
@@ -407,7 +511,7 @@ cudaError_t launch_batch4(int n, int threads, const BParams& bp, cudaStream_t s)
     case 3: return launch_batch4_n<3>(threads, bp, s);
     case 4: return launch_batch4_n<4>(threads, bp, s);
     case 5: return launch_batch4_n<5>(threads, bp, s);
-    case 6: return launch_batch4_n<6>(threads, bp, s);
+    case 6: return launch_batch4p(bp, s);     // the pair-split kernel (threads fixed)
     default: return cudaErrorNotSupported;
   }
 }
@@ -511,7 +615,7 @@ dg_status build_tiles(dg_batch b) {
     size_t max_cells_dofs = 0, max_cells = 0;
     const int npc = static_cast<int>(b->npc[g.members[0]]);
     const int per = std::max(1, b->tile_dofs / npc);
-    const int per4 = std::max(1, b->threads4 / (g.n * g.n));
+    const int per4 = g.n == 6 ? kCpb6 : std::max(1, b->threads4 / (g.n * g.n));
     for (int m : g.members) {
       const int nc = b->inst[m].ncells;
       for (int c = 0; c < nc; c += per) g.tiles_sm.push_back(Tile{m, c, std::min(per, nc - c)});
@@ -798,7 +902,7 @@ dg_status dg_batch_set_launch_ex(dg_batch b, const dg_batch_launch* cfg) {
   if (cfg->r4_max_n < 1 || cfg->r4_max_n > kMaxN)
     return report(DG_ERR_INVALID_ARG, "r4_max_n in [1, 6]");
   for (const auto& g : b->groups)
-    if (g.d == 4 && g.n <= cfg->r4_max_n &&
+    if (g.d == 4 && g.n <= cfg->r4_max_n && g.n < 6 &&
         (cfg->threads4 < g.n * g.n || (cfg->threads4 == 512 && g.n > 4)))
       return report(DG_ERR_INVALID_ARG,
                     "threads4 too small (or 512 with n > 4) for a 4D group of the register kernel");

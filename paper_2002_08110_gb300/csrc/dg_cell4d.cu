@@ -211,6 +211,57 @@ cudaError_t launch4(KParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// n = 6: the pair-split kernel (two threads per column and row, 18 values
+// each; 3 cells per 224-thread block).
+constexpr int kCpb6 = 3, kThreads6 = 224;
+
+template <typename TIN, typename TW, int MODE, bool ADJ>
+__global__ void __launch_bounds__(kThreads6, 2) k_cell4p(const KParams p) {
+  extern __shared__ __align__(16) float sm4p[];
+  float* const su = sm4p;
+  float* const sr = sm4p + kCpb6 * kPS * kPad6;
+  const unsigned ncells = static_cast<unsigned>(p.ncells);
+  const unsigned cell0 = blockIdx.x * static_cast<unsigned>(kCpb6);
+  const int nc = static_cast<int>(min(static_cast<unsigned>(kCpb6), ncells - cell0));
+  int ncell[4];
+  unsigned cst[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ncell[j] = p.ncell[j];
+    cst[j] = static_cast<unsigned>(p.cstride[j]);
+  }
+  // x speeds at v node k of the cell, v speeds at its x node k (tables)
+  auto speeds = [&](unsigned, const unsigned (&co)[4], int k, float& c0, float& c1, float& e0,
+                    float& e1) {
+    const unsigned cx = co[0] + static_cast<unsigned>(ncell[0]) * co[1];
+    const unsigned cv = co[2] + static_cast<unsigned>(ncell[2]) * co[3];
+    const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * kPS + k) * 2;
+    const float* ctv = static_cast<const float*>(p.cv_tab) + (static_cast<size_t>(cx) * kPS + k) * 2;
+    c0 = ADJ ? -ctx[0] : ctx[0];
+    c1 = ADJ ? -ctx[1] : ctx[1];
+    e0 = ADJ ? -ctv[0] : ctv[0];
+    e1 = ADJ ? -ctv[1] : ctv[1];
+  };
+  const bool bad = cell4p_block<TIN, TW, MODE, ADJ, kCpb6>(
+      static_cast<const TIN*>(p.src), static_cast<TW*>(p.dst), p.u, cell0, nc, ncells, ncell, cst,
+      static_cast<float>(p.b_dt), static_cast<float>(p.a_dt), p.a_dt, p.last_stage != 0, speeds, p.t32,
+      su, sr, p.err);
+  if (bad) atomicOr(p.err, 1);
+}
+
+template <typename TIN, typename TW>
+cudaError_t launch4p(KParams& p, cudaStream_t s) {
+  const size_t smem = 2 * static_cast<size_t>(kCpb6) * kPS * kPad6 * sizeof(float);
+  auto kern = p.adjoint ? (p.mode == 0 ? k_cell4p<TIN, TW, 0, true> : k_cell4p<TIN, TW, 1, true>)
+                        : (p.mode == 0 ? k_cell4p<TIN, TW, 0, false> : k_cell4p<TIN, TW, 1, false>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const long long grid = (p.ncells + kCpb6 - 1) / kCpb6;
+  kern<<<static_cast<unsigned>(grid), kThreads6, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <typename TIN, typename TW>
 cudaError_t launch4_n(int n, KParams& p, cudaStream_t s) {
   switch (n) {
@@ -218,7 +269,7 @@ cudaError_t launch4_n(int n, KParams& p, cudaStream_t s) {
     case 3: return launch4<3, TIN, TW>(p, s);
     case 4: return launch4<4, TIN, TW>(p, s);
     case 5: return launch4<5, TIN, TW>(p, s);
-    case 6: return launch4<6, TIN, TW>(p, s);
+    case 6: return launch4p<TIN, TW>(p, s);
     default: return cudaErrorNotSupported;
   }
 }

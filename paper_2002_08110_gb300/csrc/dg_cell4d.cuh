@@ -109,3 +109,253 @@ __device__ __forceinline__ float w2(const float* w, int i) {
 
 }  // namespace
 }  // namespace dg
+
+namespace dg {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Pair split for n = 6: two threads per column (phase X) and per row (phase
+// V), lanes 2k + h of a warp.  With n^2 = 36 values a column or a row is too
+// much for one thread's registers next to its neighbour's; thread h holds the
+// 18 values whose second digit is 3h + i (i = 0, 1, 2): v[i][a], a the first
+// digit.  Lines along the first digit are thread-local (3 per thread); lines
+// along the second digit are split between the two threads, which exchange
+// their three values of each line and add their partial traces by shuffles.
+constexpr int kP = 6;     // n
+constexpr int kPS = 36;   // n^2
+constexpr int kPad6 = 37; // padded column stride in shared memory
+
+// the lines along the first digit (3 per thread); POS: the upwind side
+template <bool POS>
+__device__ __forceinline__ void pdir_local(float (&r)[3][kP], const float (&u)[3][kP],
+                                           const float (&nb)[3][kP], float c, const Tab1D<float>& T) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < kP; ++q) t = fmaf(POS ? T.lp[q] : T.lm[q], nb[i][q], t);
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      float acc = (POS ? T.Lm[q] : -T.Lp[q]) * t;
+#pragma unroll
+      for (int s = 0; s < kP; ++s) acc = fmaf(POS ? T.Gp[q * kP + s] : T.Gn[q * kP + s], u[i][s], acc);
+      r[i][q] = fmaf(c, acc, r[i][q]);
+    }
+  }
+}
+
+// the 6 lines along the second digit, split between the pair (lane ^ 1): the
+// thread computes its own points q = 3h + i; every lane of the warp runs this
+// (the shuffles need all of them), with zero speed where there is no work
+__device__ __forceinline__ void pdir_split(float (&r)[3][kP], const float (&u)[3][kP],
+                                           const float (&nb)[3][kP], float c, int h,
+                                           const Tab1D<float>& T) {
+  const bool pos = c > 0.f;
+  const int own = 3 * h, par = 3 * (1 - h);
+  float Go[3][3], Gq[3][3], L[3], lo[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int q = own + i;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Go[i][j] = pos ? T.Gp[q * kP + own + j] : T.Gn[q * kP + own + j];
+      Gq[i][j] = pos ? T.Gp[q * kP + par + j] : T.Gn[q * kP + par + j];
+    }
+    L[i] = pos ? T.Lm[q] : -T.Lp[q];
+    lo[i] = pos ? T.lp[q] : T.lm[q];
+  }
+#pragma unroll
+  for (int a = 0; a < kP; ++a) {
+    float v[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] = __shfl_xor_sync(0xffffffffu, u[j][a], 1);
+    // the upwind neighbour's trace of line a: own half, then the partner's
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t = fmaf(lo[j], nb[j][a], t);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float acc = L[i] * t;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc = fmaf(Go[i][j], u[j][a], acc);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc = fmaf(Gq[i][j], v[j], acc);
+      r[i][a] = fmaf(c, acc, r[i][a]);
+    }
+  }
+}
+
+__device__ __forceinline__ void pdir_local_any(float (&r)[3][kP], const float (&u)[3][kP],
+                                               const float (&nb)[3][kP], float c, const Tab1D<float>& T) {
+  if (c > 0.f) pdir_local<true>(r, u, nb, c, T);
+  else if (c < 0.f) pdir_local<false>(r, u, nb, c, T);
+}
+
+// product of the 1D weights of the two digits of position m of a column/row
+__device__ __forceinline__ float w2p(const float* w, int m) { return w[m % kP] * w[m / kP]; }
+
+// One block's cells, n = 6, FP32 sweeps: cells [cell0, cell0 + nc), 2 n^2
+// threads per cell.  Geometry: ncell / cstride of the 4 cell coordinates
+// (x1, x2, v1, v2).  speeds(cell, co, k, c0, c1, e0, e1): the x speeds at v
+// node k and the v speeds at x node k (for ADJ already negated).  MODE 0:
+// dst = K; MODE 1: u += b dt K (FP64), dst = u_old + a dt K (or u_new at the
+// last stage).  ADJ: L^T = M L(-a) M^{-1} (input and neighbours scaled by
+// the inverse node weights, output by the weights).  su / sr: shared buffers
+// of CPB cells (kPS columns of kPad6 floats).  Returns the non-finite flag.
+template <typename TIN, typename TW, int MODE, bool ADJ, int CPB, typename Speeds>
+__device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __restrict__ dst,
+                                             double* __restrict__ uvec, unsigned cell0, int nc,
+                                             unsigned ncells, const int (&ncell)[4], const unsigned (&cst)[4],
+                                             float b_dt, float a_dt, double a_dt64, bool last_stage,
+                                             const Speeds& speeds, const Tab1D<float>& T, float* su,
+                                             float* sr, int* err) {
+  constexpr int S = kPS, NP = S * S, PAD = kPad6;
+  const int tid = threadIdx.x;
+  const int cslot = tid / (2 * S);
+  const int rem = tid - cslot * 2 * S;
+  const int k = rem >> 1, h = rem & 1;
+  const bool active = cslot < nc;
+  const int cs = cslot < CPB ? cslot : CPB - 1;     // smem slot (idle lanes read a valid one)
+  const unsigned cell = cell0 + static_cast<unsigned>(active ? cslot : 0);
+  unsigned co[4];
+  {
+    unsigned rm = cell;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      co[j] = rm % static_cast<unsigned>(ncell[j]);
+      rm /= static_cast<unsigned>(ncell[j]);
+    }
+  }
+  auto upwind = [&](int j, bool p) -> unsigned {
+    const unsigned st = cst[j], nj = static_cast<unsigned>(ncell[j]);
+    unsigned nb;
+    if (p) nb = co[j] == 0 ? cell + (nj - 1) * st : cell - st;
+    else nb = co[j] == nj - 1 ? cell - (nj - 1) * st : cell + st;
+    DG_BOUND(err, nb, ncells);
+    return nb;
+  };
+  float c0 = 0.f, c1 = 0.f, e0 = 0.f, e1 = 0.f;
+  if (active) speeds(cell, co, k, c0, c1, e0, e1);
+  // gather the block's cells (padded columns)
+  for (int i = tid; i < nc * NP; i += blockDim.x) {
+    const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
+    float v = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
+    if (ADJ) v *= w2p(T.winv, q) * w2p(T.winv, t);
+    su[(cc * S + t) * PAD + q] = v;
+  }
+  float u[3][kP], r[3][kP], nA[3][kP], nB[3][kP];
+  // the upwind neighbours' columns (own half: 18 contiguous values)
+  auto load_col = [&](float (&v)[3][kP], unsigned nbc) {
+    const TIN* colp = src + static_cast<size_t>(nbc) * NP + static_cast<size_t>(S) * k + 18 * h;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int a = 0; a < kP; ++a) {
+        float x = cvt<float>(__ldg(colp + kP * i + a));
+        if (ADJ) x *= w2p(T.winv, a + kP * (3 * h + i)) * w2p(T.winv, k);
+        v[i][a] = x;
+      }
+  };
+  auto load_row = [&](float (&v)[3][kP], unsigned nbc) {
+    const TIN* rowp = src + static_cast<size_t>(nbc) * NP + k;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int a = 0; a < kP; ++a) {
+        const int m = a + kP * (3 * h + i);
+        float x = cvt<float>(__ldg(rowp + static_cast<size_t>(S) * m));
+        if (ADJ) x *= w2p(T.winv, m) * w2p(T.winv, k);
+        v[i][a] = x;
+      }
+  };
+  auto zero = [](float (&v)[3][kP]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int a = 0; a < kP; ++a) v[i][a] = 0.f;
+  };
+  zero(nA);
+  zero(nB);
+  if (active) {
+    if (c0 != 0.f) load_col(nA, upwind(0, c0 > 0.f));
+    if (c1 != 0.f) load_col(nB, upwind(1, c1 > 0.f));
+  }
+  __syncthreads();
+  // ---- phase X: column k, directions x1 (local), x2 (split)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < kP; ++a) {
+      u[i][a] = su[(cs * S + k) * PAD + a + kP * (3 * h + i)];
+      r[i][a] = 0.f;
+    }
+  pdir_local_any(r, u, nA, c0, T);
+  pdir_split(r, u, nB, c1, h, T);
+  // lanes without a cell (they ran the split direction for the shuffles
+  // only) must not write: their slot is clamped onto a real cell's
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int a = 0; a < kP; ++a) sr[(cs * S + k) * PAD + a + kP * (3 * h + i)] = r[i][a];
+  }
+  zero(nA);
+  zero(nB);
+  if (active) {
+    if (e0 != 0.f) load_row(nA, upwind(2, e0 > 0.f));
+    if (e1 != 0.f) load_row(nB, upwind(3, e1 > 0.f));
+  }
+  __syncthreads();
+  // ---- phase V: row k, directions v1 (local), v2 (split)
+  const size_t g0 = static_cast<size_t>(cell) * NP + k;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int a = 0; a < kP; ++a) {
+      const int m = a + kP * (3 * h + i);
+      u[i][a] = su[(cs * S + m) * PAD + k];
+      r[i][a] = sr[(cs * S + m) * PAD + k];
+    }
+  pdir_local_any(r, u, nA, e0, T);
+  pdir_split(r, u, nB, e1, h, T);
+  if (ADJ) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int a = 0; a < kP; ++a) r[i][a] *= w2p(T.w, a + kP * (3 * h + i)) * w2p(T.w, k);
+  }
+  float nanacc = 0.f;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double ua[kP];
+      if constexpr (MODE == 1) {
+#pragma unroll
+        for (int a = 0; a < kP; ++a) ua[a] = __ldcs(uvec + g0 + static_cast<size_t>(S) * (a + kP * (3 * h + i)));
+      }
+#pragma unroll
+      for (int a = 0; a < kP; ++a) {
+        const size_t g = g0 + static_cast<size_t>(S) * (a + kP * (3 * h + i));
+        const float K = r[i][a];
+        nanacc = fmaf(K, 0.f, nanacc);
+        if constexpr (MODE == 0) {
+          __stcs(dst + g, cvt<TW>(K));
+        } else {
+          const double un = ua[a] + f32_to_f64_finite(b_dt * K);
+          __stcs(uvec + g, un);
+          if constexpr (sizeof(TW) == 4)
+            __stcs(dst + g, last_stage ? f64_to_f32(un) : fmaf(a_dt, K, f64_to_f32(ua[a])));
+          else
+            __stcs(dst + g, last_stage ? un : ua[a] + a_dt64 * f32_to_f64(K));
+        }
+      }
+    }
+  }
+  (void)err;
+  (void)ncells;
+  return nanacc != 0.f;
+}
+
+}  // namespace
+}  // namespace dg
