@@ -176,7 +176,12 @@ typedef struct {
                                  cell (default).  4D with dim_x = dim_v = 2, FP32
                                  sweeps: 2 = specialised, n^2 threads per cell, cell
                                  in registers (default; the delta-f stage and
-                                 curved meshes use the generic kernel)       */
+                                 curved meshes use the generic kernel).  5D with
+                                 dim_x = 2, dim_v = 3, k = 3, FP32 sweeps: 2 =
+                                 specialised, 64 threads per cell in three
+                                 register phases (default; the transpose, the
+                                 delta-f stage and curved meshes use the generic
+                                 kernel)                                     */
 } dg_launch;
 
 /* Library version (DG_ABI_VERSION). */

@@ -184,7 +184,11 @@ cudaError_t launch_generic_any(const dg_ctx* h, int combo, KParams& p, const Lau
 
 cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg& cfg,
                         cudaStream_t s) {
-  // the negated-field forward operator exists in the generic kernel only
+  if (cfg.variant == 2 && h->d == 5 && h->dx == 2 && !h->curved) {
+    cudaError_t e = launch_cell_5d(h->n, combo, p, cfg, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  // the negated-field forward operator: the generic and the 5D kernels only
   if (p.negate) return launch_generic_any(h, combo, p, cfg, s);
   if (cfg.variant >= 1 && h->d == 6 && h->n == 4 && h->uniform_sides && !h->curved) {
     cudaError_t e = launch_cell_6d4(combo, p, cfg, s);
@@ -197,8 +201,10 @@ cudaError_t launch_cell(const dg_ctx* h, int combo, KParams& p, const LaunchCfg&
   return launch_generic_any(h, combo, p, cfg, s);
 }
 
-// Does launch_cell run the generic kernel for this precision (no specialised
-// kernel covers the handle's dimensions, degree, field and launch variant)?
+// Do the adjoint steps for this precision run as forward steps of the
+// negated field on weight-scaled states?  Yes where the kernel that runs has
+// no transpose of its own: the generic kernel and the 5D kernel (the 6D and
+// 4D kernels apply the node weights inside).
 bool generic_runs(const dg_ctx* h, int prec) {
   if (prec == DG_PREC_FP64 || h->curved) return true;
   const LaunchCfg& c = h->cfg[prec];
@@ -353,6 +359,7 @@ void default_cfg(dg_ctx* h) {
     if (h->npc >= 1024) c.threads = 512;
     if (h->d == 6 && h->n == 4 && prec != DG_PREC_FP64) c.variant = 2;
     if (h->d == 4 && h->dx == 2 && prec != DG_PREC_FP64) c.variant = 2;
+    if (h->d == 5 && h->dx == 2 && h->n == 4 && prec != DG_PREC_FP64) c.variant = 2;
   }
 }
 
@@ -1483,7 +1490,8 @@ dg_status dg_autotune(dg_handle h, const void* src, void* dst, int prec, void* s
   for (int variant = 0; variant < 3; ++variant) {
     const bool spec6 = h->d == 6 && h->n == 4 && prec != DG_PREC_FP64;
     const bool spec4 = h->d == 4 && h->dx == 2 && prec != DG_PREC_FP64 && !h->curved;
-    if (variant >= 1 && !spec6 && !(variant == 2 && spec4)) continue;
+    const bool spec5 = h->d == 5 && h->dx == 2 && h->n == 4 && prec != DG_PREC_FP64 && !h->curved;
+    if (variant >= 1 && !spec6 && !(variant == 2 && (spec4 || spec5))) continue;
     for (int rev = 0; rev < 2; ++rev)
       for (int t : threads_c)
         for (int c : cpbs) {

@@ -154,6 +154,10 @@ int generic_grid_blocks(int d, int n, long long ncells, int cells_per_block, int
 // Specialised 6D, n = 4, FP32-sweep kernel (dg_cell6d.cu).  Returns
 // cudaErrorNotSupported if the configuration is not covered.
 cudaError_t launch_cell_6d4(int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
+// Specialised 5D (dim_x = 2, dim_v = 3), n = 4 FP32-sweep kernel (dg_cell5d.cu):
+// forward operator (also of the negated field), apply and stage;
+// cudaErrorNotSupported if the configuration is not covered.
+cudaError_t launch_cell_5d(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
 // Specialised 4D (dim_x = dim_v = 2) FP32-sweep kernel, n = 2..6 (dg_cell4d.cu);
 // cudaErrorNotSupported if the configuration is not covered.
 cudaError_t launch_cell_4d(int n, int combo, KParams& p, const LaunchCfg& cfg, cudaStream_t s);
