@@ -54,7 +54,7 @@ def flop_entry(dofs, ms, d, n, stage):
             "frac": tflops / FP32_PEAK_TFLOPS,
             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
-KERNEL_SOURCES = ["dg_cell6d.cu", "dg_generic.cuh", "dg_internal.h"]
+KERNEL_SOURCES = ["dg_cell6d.cu", "dg_generic.cuh", "dg_internal.h", "dg_tma.cuh"]
 
 
 def parse():
@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--fp64-reps", type=int, default=2)
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 2D, 4D, batched and adjoint configurations")
+    ap.add_argument("--configs", default=None,
+                    help="comma-separated subset of the other configurations (6d_fp32_vs_fp64, "
+                         "6d_gll, 6d_curved, 2d, 4d, 4d_k5, batched, adjoint); default: all")
     ap.add_argument("--step-kind", default="stage",
                     choices=["stage", "apply_fp32", "apply_fp32_fp64io", "apply_fp64"],
                     help="what one timed step is (default: the fused LSRK stage)")
@@ -316,13 +319,16 @@ def _timed(torch, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_configs(torch, hbm_peak):
+def measure_configs(torch, hbm_peak, only=None):
     """Throughput of the other synthetic workloads, GDoF/s per LSRK stage
     (each stage = one operator application fused with the state update)."""
     import workloads as W
     from paper_2002_08110_gb300 import DG, DGBatch, PREC_FP32, PREC_FP64, reference_nodes
     from paper_2002_08110_gb300.autograd import misfit_gradient
     out = {}
+
+    def want(name):
+        return only is None or name in only
 
     def make(w):
         zeta, _ = reference_nodes(w.k)
@@ -340,187 +346,212 @@ def measure_configs(torch, hbm_peak):
     # (its 50 steps); the temporal error of the run, estimated from a second
     # run at half the step (Richardson: (16/15) ||u_dt - u_dt/2|| for a
     # fourth-order scheme), says what "the same final-time accuracy" means
-    w = W.config_6d()
-    dg, zeta = make(w)
-    dt, nacc = W.time_step(w)
-    u0 = W.separable_state(w, zeta, xp=torch, device="cuda")
-    k64 = dg.apply(u0, prec=PREC_FP64)
-    k32 = dg.apply(u0.float(), prec=PREC_FP32).double()
-    rel_apply = float(torch.linalg.vector_norm(k32 - k64) / torch.linalg.vector_norm(k64))
-    del k32
-    u64 = u0.clone()
-    ms64 = _timed(torch, lambda: dg.rk_step(u64, dt, nsteps=nacc, prec=PREC_FP64), 1)
-    u32 = u0.clone()
-    ms32 = _timed(torch, lambda: dg.rk_step(u32, dt, nsteps=nacc, prec=PREC_FP32), 1)
-    u32h = u0.clone()
-    dg.rk_step(u32h, dt / 2, nsteps=2 * nacc, prec=PREC_FP32)
-    dg.check()
-    nrm = lambda x: float(torch.linalg.vector_norm(x))
-    n64 = nrm(u64)
-    time_err = 16.0 / 15.0 * nrm(u32 - u32h) / n64
-    del u32h
-    # delta-f form around the Maxwellian equilibrium: FP32 sweeps on u - u_eq
-    u_eq = W.separable_state(W.equilibrium_6d(w), zeta, xp=torch, device="cuda")
-    dg.set_reference(u_eq)
-    kdf = dg.apply_df(u0)
-    rel_apply_df = float(torch.linalg.vector_norm(kdf - k64) / torch.linalg.vector_norm(k64))
-    del kdf, u_eq
-    udf = u0.clone()
-    dg.rk_step_df(udf, dt, nsteps=1)
-    udf.copy_(u0)
-    msdf = _timed(torch, lambda: dg.rk_step_df(udf, dt, nsteps=nacc), 1)
-    dg.check()
-    m0, l0, _ = dg.integrals(u0)
+    if want("6d_fp32_vs_fp64"):
+        w = W.config_6d()
+        dg, zeta = make(w)
+        dt, nacc = W.time_step(w)
+        u0 = W.separable_state(w, zeta, xp=torch, device="cuda")
+        k64 = dg.apply(u0, prec=PREC_FP64)
+        k32 = dg.apply(u0.float(), prec=PREC_FP32).double()
+        rel_apply = float(torch.linalg.vector_norm(k32 - k64) / torch.linalg.vector_norm(k64))
+        del k32
+        u64 = u0.clone()
+        ms64 = _timed(torch, lambda: dg.rk_step(u64, dt, nsteps=nacc, prec=PREC_FP64), 1)
+        u32 = u0.clone()
+        ms32 = _timed(torch, lambda: dg.rk_step(u32, dt, nsteps=nacc, prec=PREC_FP32), 1)
+        u32h = u0.clone()
+        dg.rk_step(u32h, dt / 2, nsteps=2 * nacc, prec=PREC_FP32)
+        dg.check()
+        nrm = lambda x: float(torch.linalg.vector_norm(x))
+        n64 = nrm(u64)
+        time_err = 16.0 / 15.0 * nrm(u32 - u32h) / n64
+        del u32h
+        # delta-f form around the Maxwellian equilibrium: FP32 sweeps on u - u_eq
+        u_eq = W.separable_state(W.equilibrium_6d(w), zeta, xp=torch, device="cuda")
+        dg.set_reference(u_eq)
+        kdf = dg.apply_df(u0)
+        rel_apply_df = float(torch.linalg.vector_norm(kdf - k64) / torch.linalg.vector_norm(k64))
+        del kdf, u_eq
+        udf = u0.clone()
+        dg.rk_step_df(udf, dt, nsteps=1)
+        udf.copy_(u0)
+        msdf = _timed(torch, lambda: dg.rk_step_df(udf, dt, nsteps=nacc), 1)
+        dg.check()
+        m0, l0, _ = dg.integrals(u0)
 
-    def drift(x):
-        m, l2, _ = dg.integrals(x)
-        return {"mass_drift": (m - m0) / m0, "l2_change": (l2 - l0) / l0}
-    out["6d_fp32_vs_fp64"] = {
-        "workload": w.name, "steps": nacc, "final_time": dt * nacc,
-        "apply_rel_l2_diff_fp32": rel_apply, "apply_rel_l2_diff_deltaf": rel_apply_df,
-        "state_change_rel_l2": nrm(u64 - u0) / nrm(u0),
-        "temporal_error_estimate_rel_l2": time_err,
-        "fp64": {"ms_per_step": ms64 / nacc, **drift(u64)},
-        "fp32_sweeps_fp64_state": {"ms_per_step": ms32 / nacc, **drift(u32),
-                                   "state_rel_l2_diff_vs_fp64": nrm(u32 - u64) / n64},
-        "deltaf_fp32_sweeps": {"ms_per_step": msdf / nacc, **drift(udf),
-                               "state_rel_l2_diff_vs_fp64": nrm(udf - u64) / n64},
-        "note": "K of the FP64 path matches the FP64 oracle to 1e-12 (tests); the plain relative "
-                "difference of K is large for smooth data (K << its terms); see tests for the "
-                "term-scale error.  The final-time differences against FP64 are to be read "
-                "against the temporal error estimate of the run"}
-    dg.close()
-    del u0, u64, u32, k64, udf
-    torch.cuda.empty_cache()
+        def drift(x):
+            m, l2, _ = dg.integrals(x)
+            return {"mass_drift": (m - m0) / m0, "l2_change": (l2 - l0) / l0}
+        out["6d_fp32_vs_fp64"] = {
+            "workload": w.name, "steps": nacc, "final_time": dt * nacc,
+            "apply_rel_l2_diff_fp32": rel_apply, "apply_rel_l2_diff_deltaf": rel_apply_df,
+            "state_change_rel_l2": nrm(u64 - u0) / nrm(u0),
+            "temporal_error_estimate_rel_l2": time_err,
+            "fp64": {"ms_per_step": ms64 / nacc, **drift(u64)},
+            "fp32_sweeps_fp64_state": {"ms_per_step": ms32 / nacc, **drift(u32),
+                                       "state_rel_l2_diff_vs_fp64": nrm(u32 - u64) / n64},
+            "deltaf_fp32_sweeps": {"ms_per_step": msdf / nacc, **drift(udf),
+                                   "state_rel_l2_diff_vs_fp64": nrm(udf - u64) / n64},
+            "note": "K of the FP64 path matches the FP64 oracle to 1e-12 (tests); the plain relative "
+                    "difference of K is large for smooth data (K << its terms); see tests for the "
+                    "term-scale error.  The final-time differences against FP64 are to be read "
+                    "against the temporal error estimate of the run"}
+        dg.close()
+        del u0, u64, u32, k64, udf
+        torch.cuda.empty_cache()
 
     # 6D in the Gauss-Lobatto bases: the collocation variant (FP32 stage; its
     # v neighbours arrive as face layers) and the paper's Lobatto-node,
     # Gauss-quadrature element (steps between two changes of basis)
-    from paper_2002_08110_gb300 import BASIS_GLL, BASIS_GLL_GAUSS, basis_nodes
-    w = W.config_6d()
-    dt, _ = W.time_step(w)
-    for name, basis in (("6d_gll_collocation", BASIS_GLL), ("6d_gll_gauss", BASIS_GLL_GAUSS)):
-        nodes, qpts, _ = basis_nodes(basis, w.k)
-        dg = DG(e_nodes=W.e_table(w, qpts), basis=basis, **W.dg_kwargs(w))
-        u = W.separable_state(w, nodes, xp=torch, device="cuda")
-        if basis == BASIS_GLL:
-            a, b = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda")
-            for i in range(3):
-                dg.rk_stage(a, b, u, i, dt, prec=PREC_FP32)
-                a, b = b, a
-            reps = 20
-            ms = _timed(torch, lambda: dg.rk_stage(a, b, u, 1, dt, prec=PREC_FP32), reps)
-            dg.check()
-            gbs = 24 * dg.n_dofs / (ms * 1e-3) / 1e9
-            out[name] = {"workload": w.name + "_gll_collocation", "dofs": dg.n_dofs,
-                         "ms_per_stage": ms, "GDoF/s_per_stage": dg.n_dofs / (ms * 1e-3) / 1e9,
-                         "frac_hbm": gbs / hbm_peak, "bytes_per_dof": 24,
-                         "uniform_sides": int(dg.info.uniform_sides)}
-            del a, b
-        else:
-            nst = 5
-            dg.rk_step(u, dt, nsteps=1, prec=PREC_FP32)
-            ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=nst, prec=PREC_FP32), 1)
-            dg.check()
-            out[name] = {"workload": w.name + "_gll_gauss", "dofs": dg.n_dofs, "steps_per_call": nst,
-                         "ms_per_step": ms / nst,
-                         "GDoF/s_per_stage": dg.n_dofs / (ms / nst / 5 * 1e-3) / 1e9,
-                         "note": "each call changes the FP64 state to the Gauss points and back "
-                                 "around its steps (two tensor-product passes)"}
-        dg.close()
-        del u
-        torch.cuda.empty_cache()
+    if want("6d_gll"):
+        from paper_2002_08110_gb300 import BASIS_GLL, BASIS_GLL_GAUSS, basis_nodes
+        w = W.config_6d()
+        dt, _ = W.time_step(w)
+        for name, basis in (("6d_gll_collocation", BASIS_GLL), ("6d_gll_gauss", BASIS_GLL_GAUSS)):
+            nodes, qpts, _ = basis_nodes(basis, w.k)
+            dg = DG(e_nodes=W.e_table(w, qpts), basis=basis, **W.dg_kwargs(w))
+            u = W.separable_state(w, nodes, xp=torch, device="cuda")
+            if basis == BASIS_GLL:
+                a, b = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda")
+                for i in range(3):
+                    dg.rk_stage(a, b, u, i, dt, prec=PREC_FP32)
+                    a, b = b, a
+                reps = 20
+                ms = _timed(torch, lambda: dg.rk_stage(a, b, u, 1, dt, prec=PREC_FP32), reps)
+                dg.check()
+                gbs = 24 * dg.n_dofs / (ms * 1e-3) / 1e9
+                out[name] = {"workload": w.name + "_gll_collocation", "dofs": dg.n_dofs,
+                             "ms_per_stage": ms, "GDoF/s_per_stage": dg.n_dofs / (ms * 1e-3) / 1e9,
+                             "frac_hbm": gbs / hbm_peak, "bytes_per_dof": 24,
+                             "uniform_sides": int(dg.info.uniform_sides)}
+                del a, b
+            else:
+                nst = 5
+                dg.rk_step(u, dt, nsteps=1, prec=PREC_FP32)
+                ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=nst, prec=PREC_FP32), 1)
+                dg.check()
+                out[name] = {"workload": w.name + "_gll_gauss", "dofs": dg.n_dofs, "steps_per_call": nst,
+                             "ms_per_step": ms / nst,
+                             "GDoF/s_per_stage": dg.n_dofs / (ms / nst / 5 * 1e-3) / 1e9,
+                             "note": "each call changes the FP64 state to the Gauss points and back "
+                                     "around its steps (two tensor-product passes)"}
+            dg.close()
+            del u
+            torch.cuda.empty_cache()
 
     # 6D on a curved x-mesh (a Jacobian per quadrature point, deformation
     # 0.1 in every x direction): FP32 stage in the generic kernel
-    zeta, _ = reference_nodes(w.k)
-    dg = DG(e_nodes=W.e_table(w, zeta), deform=(0.1, 0.1, 0.1), **W.dg_kwargs(w))
-    u = W.separable_state(w, zeta, xp=torch, device="cuda")
-    a, b = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda")
-    dg.rk_stage(a, b, u, 0, dt, prec=PREC_FP32)
-    ms = _timed(torch, lambda: dg.rk_stage(a, b, u, 1, dt, prec=PREC_FP32), 5)
-    dg.check()
-    out["6d_curved"] = {"workload": w.name + "_curved0.1", "dofs": dg.n_dofs, "ms_per_stage": ms,
-                        "GDoF/s_per_stage": dg.n_dofs / (ms * 1e-3) / 1e9,
-                        "frac_hbm": 24 * dg.n_dofs / (ms * 1e-3) / 1e9 / hbm_peak,
-                        "kernel": "generic (the specialised 6D kernels are affine-only)"}
-    dg.close()
-    del u, a, b
-    torch.cuda.empty_cache()
+    if want("6d_curved"):
+        w = W.config_6d()
+        dt, _ = W.time_step(w)
+        zeta, _ = reference_nodes(w.k)
+        dg = DG(e_nodes=W.e_table(w, zeta), deform=(0.1, 0.1, 0.1), **W.dg_kwargs(w))
+        u = W.separable_state(w, zeta, xp=torch, device="cuda")
+        a, b = u.float(), torch.empty(dg.n_dofs, dtype=torch.float32, device="cuda")
+        dg.rk_stage(a, b, u, 0, dt, prec=PREC_FP32)
+        ms = _timed(torch, lambda: dg.rk_stage(a, b, u, 1, dt, prec=PREC_FP32), 5)
+        dg.check()
+        out["6d_curved"] = {"workload": w.name + "_curved0.1", "dofs": dg.n_dofs, "ms_per_stage": ms,
+                            "GDoF/s_per_stage": dg.n_dofs / (ms * 1e-3) / 1e9,
+                            "frac_hbm": 24 * dg.n_dofs / (ms * 1e-3) / 1e9 / hbm_peak,
+                            "kernel": "generic (the specialised 6D kernels are affine-only)"}
+        dg.close()
+        del u, a, b
+        torch.cuda.empty_cache()
 
     # 2D: one period (T = 2, 240 steps), FP64
-    w = W.config_2d()
-    dg, zeta = make(w)
-    dt, steps = W.time_step(w)
-    u = W.separable_state(w, zeta, xp=torch, device="cuda")
-    ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=PREC_FP64), 1)
-    dg.check()
-    out["2d"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
-                 **stage_entry(dg, ms / steps, PREC_FP64)}
-    dg.close()
+    if want("2d"):
+        w = W.config_2d()
+        dg, zeta = make(w)
+        dt, steps = W.time_step(w)
+        u = W.separable_state(w, zeta, xp=torch, device="cuda")
+        ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=PREC_FP64), 1)
+        dg.check()
+        out["2d"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                     **stage_entry(dg, ms / steps, PREC_FP64)}
+        dg.close()
 
     # 4D sheared phase space: 200 steps, FP64 and FP32 sweeps / FP64 state
-    w = W.config_4d()
-    dg, zeta = make(w)
-    dt, steps = W.time_step(w)
-    u0 = torch.tensor(W.initial_state(w, zeta), device="cuda")
-    for prec, name in ((PREC_FP64, "4d_fp64"), (PREC_FP32, "4d_fp32_fp64state")):
-        u = u0.clone()
-        dg.rk_step(u, dt, nsteps=1, prec=prec)
-        ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=prec), 1)
+    if want("4d"):
+        w = W.config_4d()
+        dg, zeta = make(w)
+        dt, steps = W.time_step(w)
+        u0 = torch.tensor(W.initial_state(w, zeta), device="cuda")
+        for prec, name in ((PREC_FP64, "4d_fp64"), (PREC_FP32, "4d_fp32_fp64state")):
+            u = u0.clone()
+            dg.rk_step(u, dt, nsteps=1, prec=prec)
+            ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=prec), 1)
+            dg.check()
+            out[name] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                         **stage_entry(dg, ms / steps, prec)}
+        dg.close()
+        del u0, u
+
+    # 4D sheared phase space at degree 5 (n = 6 points per direction): 200
+    # FP32-sweep steps with the FP64 state
+    if want("4d_k5"):
+        w = W.config_4d(k=5)
+        dg, zeta = make(w)
+        dt, steps = W.time_step(w)
+        u = torch.tensor(W.initial_state(w, zeta), device="cuda")
+        dg.rk_step(u, dt, nsteps=1, prec=PREC_FP32)
+        ms = _timed(torch, lambda: dg.rk_step(u, dt, nsteps=steps, prec=PREC_FP32), 1)
         dg.check()
-        out[name] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
-                     **stage_entry(dg, ms / steps, prec)}
-    dg.close()
-    del u0, u
+        out["4d_k5_fp32_fp64state"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                                       **stage_entry(dg, ms / steps, PREC_FP32)}
+        dg.close()
+        del u
 
     # batched: 64 instances, one persistent launch per stage, autotuned
-    ws = W.batched_instances()
-    dgs = [DG(**W.dg_kwargs(w)) for w in ws]
-    batch = DGBatch(dgs)
-    us = [W.separable_state(w, reference_nodes(w.k)[0], xp=torch, device="cuda") for w in ws]
-    w0s = [torch.empty(w.n_dofs, device="cuda", dtype=torch.float32) for w in ws]
-    w1s = [torch.empty(w.n_dofs, device="cuda", dtype=torch.float32) for w in ws]
-    dts = [W.time_step(w)[0] for w in ws]
-    best = batch.autotune(us, w0s, w1s, dts, prec=PREC_FP32)
-    reps = 4
-    ms = _timed(torch, lambda: batch.rk_step(us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32), reps)
-    batch.check()
-    st = ms / 5
-    out["batched"] = {"workload": "64 instances, d in {3,4}, k in {2..5}, 8..24 cells/dir",
-                      "dofs": batch.n_dofs, "tiles": batch.tiles, "ms_per_step": ms,
-                      "GDoF/s_per_stage": batch.n_dofs / (st * 1e-3) / 1e9,
-                      "frac_hbm": 24 * batch.n_dofs / (st * 1e-3) / 1e9 / hbm_peak,
-                      "autotuned_ms_per_step": best}
-    batch.close()
-    for dg in dgs:
-        dg.close()
-    del us, w0s, w1s
+    if want("batched"):
+        ws = W.batched_instances()
+        dgs = [DG(**W.dg_kwargs(w)) for w in ws]
+        batch = DGBatch(dgs)
+        us = [W.separable_state(w, reference_nodes(w.k)[0], xp=torch, device="cuda") for w in ws]
+        w0s = [torch.empty(w.n_dofs, device="cuda", dtype=torch.float32) for w in ws]
+        w1s = [torch.empty(w.n_dofs, device="cuda", dtype=torch.float32) for w in ws]
+        dts = [W.time_step(w)[0] for w in ws]
+        best = batch.autotune(us, w0s, w1s, dts, prec=PREC_FP32)
+        reps = 4
+        ms = _timed(torch, lambda: batch.rk_step(us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32), reps)
+        batch.check()
+        st = ms / 5
+        out["batched"] = {"workload": "64 instances, d in {3,4}, k in {2..5}, 8..24 cells/dir",
+                          "dofs": batch.n_dofs, "tiles": batch.tiles, "ms_per_step": ms,
+                          "GDoF/s_per_stage": batch.n_dofs / (st * 1e-3) / 1e9,
+                          "frac_hbm": 24 * batch.n_dofs / (st * 1e-3) / 1e9 / hbm_peak,
+                          "autotuned_ms_per_step": best}
+        batch.close()
+        for dg in dgs:
+            dg.close()
+        del us, w0s, w1s
 
     # adjoint: gradient of the final-time misfit over 200 steps, checkpoints every 20
-    w = W.config_adjoint()
-    dg, zeta = make(w)
-    dt, steps = W.time_step(w)
-    u0 = torch.tensor(W.separable_state(w, zeta), device="cuda")
-    tgt = u0 + torch.tensor(W.noise(w), device="cuda")
-    dg.rk_step(tgt, dt, nsteps=steps, prec=PREC_FP32)
-    every = w.extra["checkpoint_every"]
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # one untimed pass: graph captures and the checkpoints' memory
-    misfit_gradient(u0, tgt, dg, dt, steps, prec=PREC_FP32, checkpoint_every=every)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    J, g = misfit_gradient(u0, tgt, dg, dt, steps, prec=PREC_FP32, checkpoint_every=every)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    # forward (200) + recomputation (200) + adjoint (200) steps
-    out["adjoint"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
-                      "checkpoint_every": every, "ms_total": ms, "misfit": J,
-                      "grad_norm": float(torch.linalg.vector_norm(g)),
-                      "GDoF/s_per_stage": 3 * steps * 5 * dg.n_dofs / (ms * 1e-3) / 1e9}
-    dg.close()
+    if want("adjoint"):
+        w = W.config_adjoint()
+        dg, zeta = make(w)
+        dt, steps = W.time_step(w)
+        u0 = torch.tensor(W.separable_state(w, zeta), device="cuda")
+        tgt = u0 + torch.tensor(W.noise(w), device="cuda")
+        dg.rk_step(tgt, dt, nsteps=steps, prec=PREC_FP32)
+        every = w.extra["checkpoint_every"]
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # one untimed pass: graph captures and the checkpoints' memory
+        misfit_gradient(u0, tgt, dg, dt, steps, prec=PREC_FP32, checkpoint_every=every)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        J, g = misfit_gradient(u0, tgt, dg, dt, steps, prec=PREC_FP32, checkpoint_every=every)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        # forward (200) + recomputation (200) + adjoint (200) steps
+        out["adjoint"] = {"workload": w.name, "dofs": dg.n_dofs, "steps": steps,
+                          "checkpoint_every": every, "ms_total": ms, "misfit": J,
+                          "grad_norm": float(torch.linalg.vector_norm(g)),
+                          "GDoF/s_per_stage": 3 * steps * 5 * dg.n_dofs / (ms * 1e-3) / 1e9}
+        dg.close()
+
     return out
 
 
@@ -675,7 +706,8 @@ def main():
     if not args.no_configs:
         del u0, u, w0, w1
         torch.cuda.empty_cache()
-        others = measure_configs(torch, hbm_peak)
+        others = measure_configs(torch, hbm_peak,
+                                 None if args.configs is None else set(args.configs.split(",")))
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:

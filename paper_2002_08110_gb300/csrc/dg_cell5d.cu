@@ -21,8 +21,12 @@
 // (the 5D workload's E_3 does).  Phase C ends with the scatter or the fused
 // LSRK stage update.  negate: the operator of the negated field (the adjoint
 // steps run it on states scaled by the node weights).
+#include <algorithm>
+#include <cstring>
+
 #include "dg_convert.cuh"
 #include "dg_internal.h"
+#include "dg_tma.cuh"
 
 namespace dg {
 namespace {
@@ -39,32 +43,30 @@ constexpr int kCell5Smem = 20 * 64 + 16 * 4;   // floats per cell buffer
 // One direction over the thread's 4 lines of 4 values: v[l][p] (line l,
 // point p), nb the upwind neighbour's values at the same positions, c the
 // speed of every line (per thread: the lines share their node outside the
-// direction).  r += c (G u + L t).
-__device__ __forceinline__ void dir5(float (&r)[4][4], const float (&u)[4][4], const float (&nb)[4][4],
-                                     float c, const Tab1D<float>& T) {
-  if (c == 0.f) return;
-  const bool pos = c > 0.f;
-  float G[16], L[4], l[4];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) G[i] = pos ? T.Gp[i] : T.Gn[i];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    L[q] = pos ? T.Lm[q] : -T.Lp[q];
-    l[q] = pos ? T.lp[q] : T.lm[q];
-  }
+// direction).  r += c (G u + L t).  The upwind side is a template argument,
+// so the 1D tables are read as constant operands (no registers, no selects);
+// dir5 branches on the thread's sign.
+template <bool POS>
+__device__ __forceinline__ void dir5s(float (&r)[4][4], const float (&u)[4][4], const float (&nb)[4][4],
+                                      float c, const Tab1D<float>& T) {
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     float t = 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) t = fmaf(l[q], nb[a][q], t);
+    for (int q = 0; q < 4; ++q) t = fmaf(POS ? T.lp[q] : T.lm[q], nb[a][q], t);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float acc = L[q] * t;
+      float acc = (POS ? T.Lm[q] : -T.Lp[q]) * t;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) acc = fmaf(G[q * 4 + s], u[a][s], acc);
+      for (int s = 0; s < 4; ++s) acc = fmaf(POS ? T.Gp[q * 4 + s] : T.Gn[q * 4 + s], u[a][s], acc);
       r[a][q] = fmaf(c, acc, r[a][q]);
     }
   }
+}
+__device__ __forceinline__ void dir5(float (&r)[4][4], const float (&u)[4][4], const float (&nb)[4][4],
+                                     float c, const Tab1D<float>& T) {
+  if (c > 0.f) dir5s<true>(r, u, nb, c, T);
+  else if (c < 0.f) dir5s<false>(r, u, nb, c, T);
 }
 
 // the same values seen along the other local digit: w[b][a] = v[a][b]
@@ -278,6 +280,423 @@ __global__ void __launch_bounds__(kT5, 4) k_cell5d(const KParams p) {
   if (nanacc != 0.f) atomicOr(p.err, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent variant for FP32 input.  One block of 64 threads walks the cells
+// blockIdx.x, blockIdx.x + gridDim.x, ... with the phases above, and every
+// cell it reads -- the cell itself and one upwind neighbour per direction --
+// arrives in shared memory by a tensor copy (cp.async.bulk.tensor, issued by
+// thread 0, completion counted on the buffer's mbarrier) instead of by the
+// threads' own loads, so that the copies of the next cell are in flight while
+// the current one is computed:
+//   the next cell itself: at the start of the current cell (two own-cell
+//   buffers alternate); its x1, x2, v1 and v2 neighbours: after phase B of the
+//   current cell; its v3 neighbour: after phase C.
+// A copied cell is the 2D box (16 floats, 64 rows) of the view (16, 64 ncells)
+// of the vector with the 64-byte swizzle: element (x, m) sits at
+//   16 m + 4 ((x >> 2) ^ ((m >> 1) & 3)) + (x & 3),
+// so that the 16-byte row reads of phase A are free of bank conflicts.
+// Where the speeds of a direction change sign inside a cell, the side with
+// more of the cell's nodes is copied and the threads of the other side read
+// their neighbour's values from global memory.  Which side is copied is
+// decided for the next cell by warp votes over its speeds.
+// Waits are bounded: after the limit the block latches DG_ERR_TIMEOUT's flag,
+// leaves the walk at the end of the cell, waits (bounded) for the copies it
+// has in flight and returns.
+constexpr int kT5p = 64;                  // threads per block, one cell at a time
+constexpr int kBuf5 = 7;                  // own cell x 2, upwind neighbours x 5
+constexpr int kO5 = 0, kN5 = 2;           // buffer indices: own cells, neighbours
+
+struct Cell5 {                            // block-uniform description of a cell
+  unsigned cell;
+  unsigned co[5];                         // coordinates (x1, x2, v1, v2, v3)
+  unsigned nb[5];                         // copied upwind neighbour per direction
+  int side[5];                            // its side: 0 (speed > 0), 1 (< 0), -1 none
+};
+
+// the four rows of x block m (u[x2][x1]) from a swizzled cell buffer
+__device__ __forceinline__ void rows5(float (&u)[4][4], const float* buf, int m) {
+  const int s = (m >> 1) & 3;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float4 v = *reinterpret_cast<const float4*>(buf + 16 * m + 4 * (b ^ s));
+    u[b][0] = v.x;
+    u[b][1] = v.y;
+    u[b][2] = v.z;
+    u[b][3] = v.w;
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) float sm_raw[];
+  // swizzled buffers need 512-byte alignment (one KB of slack is allocated)
+  float* const sb = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u) / 4;
+  float* const br = sb + kBuf5 * kS5;     // the residual between the phases (off5 layout)
+  __shared__ unsigned long long bar[kBuf5];
+  __shared__ Cell5 s_c[2];
+  __shared__ int s_cnt[2][5][2];          // per warp and direction: nodes with speed > 0, < 0
+  const int t = threadIdx.x;
+  const unsigned ncells = static_cast<unsigned>(p.ncells);
+  const float* __restrict__ src = static_cast<const float*>(p.src);
+  const Tab1D<float>& T = p.t32;
+  const float sgn = p.negate ? -1.f : 1.f;
+  const unsigned long long pol = l2_evict_last();
+  const unsigned stride = gridDim.x;
+  unsigned cell = blockIdx.x;
+  if (cell >= ncells) return;
+  int ok = 1, bad = 0;
+  unsigned ph = 0, pend = 0;              // mbarrier parities; copies not yet waited for (thread 0)
+
+  auto coords = [&](unsigned cl, Cell5& c) {
+    unsigned rem = cl;
+    c.cell = cl;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const unsigned nj = static_cast<unsigned>(p.ncell[j]);
+      c.co[j] = rem % nj;
+      rem /= nj;
+    }
+  };
+  auto upwind = [&](const Cell5& c, int j, int side) -> unsigned {
+    const unsigned st = static_cast<unsigned>(p.cstride[j]);
+    const unsigned nj = static_cast<unsigned>(p.ncell[j]);
+    unsigned nb;
+    if (side == 0) nb = c.co[j] == 0 ? c.cell + (nj - 1) * st : c.cell - st;
+    else nb = c.co[j] == nj - 1 ? c.cell - (nj - 1) * st : c.cell + st;
+    DG_BOUND(p.err, nb, ncells);
+    return nb;
+  };
+  // the thread's speeds in a cell: x1, x2 at v node t; v1, v2, v3 at x node t & 15
+  auto speeds = [&](const Cell5& c, float (&sp)[5]) {
+    const unsigned cx = c.co[0] + static_cast<unsigned>(p.ncell[0]) * c.co[1];
+    const unsigned cv = c.co[2] + static_cast<unsigned>(p.ncell[2]) * (c.co[3] + static_cast<unsigned>(p.ncell[3]) * c.co[4]);
+    const float* ctx = static_cast<const float*>(p.cx_tab) + (static_cast<size_t>(cv) * 64 + t) * 2;
+    const float* ctv = static_cast<const float*>(p.cv_tab) + (static_cast<size_t>(cx) * 16 + (t & 15)) * 3;
+    sp[0] = sgn * ctx[0];
+    sp[1] = sgn * ctx[1];
+    sp[2] = sgn * ctv[0];
+    sp[3] = sgn * ctv[1];
+    sp[4] = sgn * ctv[2];
+  };
+  auto vote = [&](const float (&sp)[5]) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int np = __popc(__ballot_sync(0xffffffffu, sp[j] > 0.f));
+      const int nn = __popc(__ballot_sync(0xffffffffu, sp[j] < 0.f));
+      if ((t & 31) == 0) {
+        s_cnt[t >> 5][j][0] = np;
+        s_cnt[t >> 5][j][1] = nn;
+      }
+    }
+  };
+  // thread 0: the copied side and neighbour of every direction
+  auto sides = [&](Cell5& c) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int np = s_cnt[0][j][0] + s_cnt[1][j][0], nn = s_cnt[0][j][1] + s_cnt[1][j][1];
+      const int sd = np == 0 && nn == 0 ? -1 : (np >= nn ? 0 : 1);
+      c.side[j] = sd;
+      c.nb[j] = sd < 0 ? c.cell : upwind(c, j, sd);
+    }
+  };
+  auto stage = [&](int b, unsigned cl) {  // thread 0
+    DG_BOUND(p.err, cl, ncells);
+    mbar_expect_tx(&bar[b], kS5 * 4);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(sb + b * kS5)),
+        "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(0), "r"(static_cast<int>(cl * 64u)),
+        "r"(smem_u32(&bar[b])), "l"(pol)
+        : "memory");
+    pend |= 1u << b;
+  };
+  auto wait = [&](int b) {
+    if (mbar_wait_bounded(&bar[b], (ph >> b) & 1u)) {
+      ph ^= 1u << b;
+      pend &= ~(1u << b);
+    } else {
+      ok = 0;
+      atomicOr(p.err, 2);
+    }
+  };
+  auto prefetch_u = [&](unsigned cl) {
+    if (MODE == 1 && t < 8) prefetch_l2(p.u + static_cast<size_t>(cl) * kS5 + 128 * t, 1024);
+  };
+
+  // ---- the first cell: coordinates, votes, sides, copies
+  if (t == 0) {
+    for (int b = 0; b < kBuf5; ++b) mbar_init(&bar[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    coords(cell, s_c[0]);
+  }
+  __syncthreads();
+  float sp[5];
+  speeds(s_c[0], sp);
+  vote(sp);
+  prefetch_u(cell);
+  __syncthreads();
+  if (t == 0) {
+    sides(s_c[0]);
+    stage(kO5, cell);
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+      if (s_c[0].side[j] >= 0) stage(kN5 + j, s_c[0].nb[j]);
+  }
+  __syncthreads();
+
+  int cur = 0;
+  for (;;) {
+    const Cell5& C = s_c[cur];
+    const unsigned next = cell + stride;
+    const bool has_next = next < ncells;
+    float* const bo = sb + (kO5 + cur) * kS5;
+    // the next cell: its coordinates, its own values in flight
+    if (has_next && t == 0) {
+      coords(next, s_c[cur ^ 1]);
+      stage(kO5 + (cur ^ 1), next);
+    }
+    if (has_next) prefetch_u(next);
+    float u[4][4], r[4][4], nA[4][4], nB[4][4];
+
+    // ---- phase A: thread t = v node m, lines along x1 and x2
+    {
+      const int m = t;
+      wait(kO5 + cur);
+      rows5(u, bo, m);
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) r[b][a] = 0.f;
+      if (C.side[0] >= 0) wait(kN5 + 0);
+      if (C.side[1] >= 0) wait(kN5 + 1);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        float (&n)[4][4] = j == 0 ? nA : nB;
+        if (sp[j] != 0.f) {
+          const int sd = sp[j] > 0.f ? 0 : 1;
+          if (sd == C.side[j]) {
+            rows5(n, sb + (kN5 + j) * kS5, m);
+          } else {
+            const float4* g = reinterpret_cast<const float4*>(src + static_cast<size_t>(upwind(C, j, sd)) * kS5 + 16 * m);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float4 v = __ldg(g + b);
+              n[b][0] = v.x;
+              n[b][1] = v.y;
+              n[b][2] = v.z;
+              n[b][3] = v.w;
+            }
+          }
+        }
+      }
+      dir5(r, u, nA, sp[0], T);                  // x1: lines b (= x2), points a
+      float ut[4][4], nt[4][4], rt[4][4];
+      transpose4(ut, u);
+      transpose4(nt, nB);
+      transpose4(rt, r);
+      dir5(rt, ut, nt, sp[1], T);                // x2: lines a (= x1), points b
+      transpose4(r, rt);
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        *reinterpret_cast<float4*>(br + off5(4 * b, m)) = make_float4(r[b][0], r[b][1], r[b][2], r[b][3]);
+    }
+    fence_async_smem();
+    __syncthreads();                             // x1, x2 buffers free; the phase A residual visible
+
+    // the next cell's speeds (loads in flight during phase B, votes after it)
+    float spn[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (has_next) speeds(s_c[cur ^ 1], spn);
+
+    // ---- phase B: thread (x node xk, v3 j): the v1-v2 plane, u[v2][v1]
+    const int xk = t & 15;
+    {
+      const int j = t >> 4;
+      int xb[4];                                 // swizzled offsets of element (xk, a + 4 b + 16 j)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) xb[s] = 256 * j + 4 * ((xk >> 2) ^ s) + (xk & 3);
+      if (C.side[2] >= 0) wait(kN5 + 2);
+      if (C.side[3] >= 0) wait(kN5 + 3);
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int mm = a + 4 * b + 16 * j;
+          u[b][a] = bo[xb[(a >> 1) + 2 * (b & 1)] + 16 * (a + 4 * b)];
+          r[b][a] = br[off5(xk, mm)];
+        }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        float (&n)[4][4] = jj == 0 ? nA : nB;
+        const int d = 2 + jj;
+        if (sp[d] != 0.f) {
+          const int sd = sp[d] > 0.f ? 0 : 1;
+          if (sd == C.side[d]) {
+            const float* nb = sb + (kN5 + d) * kS5;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int a = 0; a < 4; ++a) n[b][a] = nb[xb[(a >> 1) + 2 * (b & 1)] + 16 * (a + 4 * b)];
+          } else {
+            const float* g = src + static_cast<size_t>(upwind(C, d, sd)) * kS5 + xk;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int a = 0; a < 4; ++a) n[b][a] = __ldg(g + 16 * (a + 4 * b + 16 * j));
+          }
+        }
+      }
+      dir5(r, u, nA, sp[2], T);                  // v1: lines b (= v2), points a
+      float ut[4][4], nt[4][4], rt[4][4];
+      transpose4(ut, u);
+      transpose4(nt, nB);
+      transpose4(rt, r);
+      dir5(rt, ut, nt, sp[3], T);                // v2: lines a (= v1), points b
+      transpose4(r, rt);
+      if (has_next) vote(spn);
+      fence_async_smem();
+      __syncthreads();                           // v1, v2 buffers free; residual read; votes in
+      if (t == 0 && has_next) {
+        Cell5& N = s_c[cur ^ 1];
+        sides(N);
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+          if (N.side[d] >= 0) stage(kN5 + d, N.nb[d]);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) br[off5(xk, a + 4 * b + 16 * j)] = r[b][a];
+    }
+    __syncthreads();
+
+    // ---- phase C: thread (x node xk, v1 a3): four v3 lines (one per v2), u[v2][v3]
+    const int a3 = t >> 4;
+    {
+      int xc[2];                                 // swizzled offsets of element (xk, a3 + 4 b), b & 1 = 0, 1
+#pragma unroll
+      for (int q = 0; q < 2; ++q) xc[q] = 16 * a3 + 4 * ((xk >> 2) ^ ((a3 >> 1) + 2 * q)) + (xk & 3);
+      if (C.side[4] >= 0) wait(kN5 + 4);
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          u[b][jj] = bo[xc[b & 1] + 16 * (4 * b + 16 * jj)];
+          r[b][jj] = br[off5(xk, a3 + 4 * b + 16 * jj)];
+        }
+      if (sp[4] != 0.f) {
+        const int sd = sp[4] > 0.f ? 0 : 1;
+        if (sd == C.side[4]) {
+          const float* nb = sb + (kN5 + 4) * kS5;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) nA[b][jj] = nb[xc[b & 1] + 16 * (4 * b + 16 * jj)];
+        } else {
+          const float* g = src + static_cast<size_t>(upwind(C, 4, sd)) * kS5 + xk;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) nA[b][jj] = __ldg(g + 16 * (a3 + 4 * b + 16 * jj));
+        }
+      }
+      dir5(r, u, nA, sp[4], T);                  // v3: lines b (= v2), points jj
+    }
+
+    // ---- scatter / fused LSRK stage update (consecutive threads: consecutive x nodes)
+    {
+      float* __restrict__ dst = static_cast<float*>(p.dst);
+      const size_t g0 = static_cast<size_t>(cell) * kS5 + xk;
+      float nanacc = 0.f;
+      if constexpr (MODE == 0) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const float K = r[b][jj];
+            nanacc = fmaf(K, 0.f, nanacc);
+            __stcs(dst + g0 + 16 * (a3 + 4 * b + 16 * jj), K);
+          }
+      } else {
+        // all 16 FP64 state values requested at once (one L2 round trip)
+        const float bf = static_cast<float>(p.b_dt), af = static_cast<float>(p.a_dt);
+        double ua[4][4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) ua[b][jj] = __ldcs(p.u + g0 + 16 * (a3 + 4 * b + 16 * jj));
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const size_t g = g0 + 16 * (a3 + 4 * b + 16 * jj);
+            const float K = r[b][jj];
+            nanacc = fmaf(K, 0.f, nanacc);
+            const double un = ua[b][jj] + f32_to_f64_finite(bf * K);
+            __stcs(p.u + g, un);
+            __stcs(dst + g, p.last_stage ? f64_to_f32(un) : fmaf(af, K, f64_to_f32(ua[b][jj])));
+          }
+      }
+      bad |= nanacc != 0.f;
+    }
+    fence_async_smem();
+    ok = __syncthreads_and(ok);                  // v3 buffer and own buffer free
+    if (!ok || !has_next) break;
+    if (t == 0) {
+      const Cell5& N = s_c[cur ^ 1];
+      if (N.side[4] >= 0) stage(kN5 + 4, N.nb[4]);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) sp[j] = spn[j];
+    cell = next;
+    cur ^= 1;
+  }
+  // copies still in flight (only after a failed wait): wait for them, bounded
+  if (t == 0 && pend != 0u) {
+    for (int b = 0; b < kBuf5; ++b)
+      if ((pend >> b) & 1u) mbar_wait_bounded(&bar[b], (ph >> b) & 1u);
+  }
+  if (bad) atomicOr(p.err, 1);
+}
+
+// 2D view (16 floats, 64 ncells rows) of an FP32 vector, box 16 x 64 (one
+// cell), 64-byte swizzle.
+cudaError_t encode_cell5_map(CUtensorMap* tm, const void* src, long long ncells) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {16, static_cast<cuuint64_t>(ncells) * 64};
+  const cuuint64_t strides[1] = {64};
+  const cuuint32_t box[2] = {16, 64};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(src), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorNotSupported;
+}
+
+cudaError_t launch5p(KParams& p, cudaStream_t s) {
+  // tensor-copy rows are 32-bit signed coordinates; 16-byte aligned vector
+  if (p.ncells * 64 >= (1LL << 31) || (reinterpret_cast<uintptr_t>(p.src) & 15u) != 0)
+    return cudaErrorNotSupported;
+  alignas(64) CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  cudaError_t e;
+  if ((e = encode_cell5_map(&tm, p.src, p.ncells)) != cudaSuccess) return e;
+  const void* kern = p.mode == 0 ? reinterpret_cast<const void*>(k_cell5p<0>)
+                                 : reinterpret_cast<const void*>(k_cell5p<1>);
+  const size_t smem = 1024 + (static_cast<size_t>(kBuf5) * kS5 + kCell5Smem) * sizeof(float);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT5p, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const long long grid = std::min<long long>(p.ncells, static_cast<long long>(sms) * per_sm);
+  (p.mode == 0 ? k_cell5p<0> : k_cell5p<1>)<<<static_cast<unsigned>(grid), kT5p, smem, s>>>(p, tm);
+  return cudaGetLastError();
+}
+
 template <typename TIN, typename TW>
 cudaError_t launch5(KParams& p, cudaStream_t s) {
   auto kern = p.mode == 0 ? k_cell5d<TIN, TW, 0> : k_cell5d<TIN, TW, 1>;
@@ -294,7 +713,11 @@ cudaError_t launch_cell_5d(int n, int combo, KParams& p, const LaunchCfg& cfg, c
   // scaled states), the delta-f stage, curved meshes, partial pencils
   if (p.adjoint || p.kref != nullptr || p.geo_c != nullptr || p.v3_n > 0) return cudaErrorNotSupported;
   if (p.ncells >= (1LL << 31) / kS5) return cudaErrorNotSupported;   // 32-bit cell indices
-  if (combo == kFFF) return launch5<float, float>(p, s);
+  if (combo == kFFF) {
+    const cudaError_t e = launch5p(p, s);
+    if (e != cudaErrorNotSupported) return e;
+    return launch5<float, float>(p, s);
+  }
   if (combo == kFDD) return launch5<double, double>(p, s);
   return cudaErrorNotSupported;
 }

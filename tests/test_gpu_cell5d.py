@@ -1,6 +1,7 @@
-"""GPU parity of the specialised 5D kernel (dim_x = 2, dim_v = 3, k = 3, FP32
+"""GPU parity of the specialised 5D kernels (dim_x = 2, dim_v = 3, k = 3, FP32
 sweeps; three register phases: the x block of a v node, the v1-v2 plane of
-an x node, the v3 lines) against the FP64 oracle, element by element against
+an x node, the v3 lines; FP32 input: the persistent kernel whose cells
+arrive by tensor copies) against the FP64 oracle, element by element against
 the term scale, and against the generic kernel.  Ragged meshes over several
 blocks with one- and two-cell directions; the phase-space field changes sign
 inside cells (the upwind side is chosen per thread); sheared x-mesh.  The
@@ -53,6 +54,26 @@ def test_apply_5d_kernel(cells, kind, prec):
         out = dg.apply(x, prec=prec).double().cpu().numpy()
         dg.check()
         assert_term_scale(out, ref, scale, TOL32, what=f"5D variant {v}")
+    dg.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_apply_5d_zero_speed_directions(prec):
+    """Directions whose speed is zero everywhere (x2 and v2 here) need no
+    neighbour: the persistent kernel copies none for them and waits for none."""
+    from oracle.dg import ConstantField, Problem
+    from paper_2002_08110_gb300 import DG
+    a = np.array([0.3, 0.0, -0.7, 0.0, 0.2])
+    cells = (2, 3, 2, 1, 3)
+    args = (2, 3, 3, cells[:2], cells[2:], [0.0] * 2, [1.0] * 2, [-1.0] * 3, [1.5] * 3)
+    p = Problem(*args, ConstantField(a))
+    dg = DG(*args, field_kind=0, a_const=a)
+    u = np.random.default_rng(3).standard_normal(p.n_dofs)
+    x = torch.tensor(u, device="cuda", dtype=torch.float32 if prec == 1 else torch.float64)
+    xin = x.double().cpu().numpy()
+    out = dg.apply(x, prec=prec).double().cpu().numpy()
+    dg.check()
+    assert_term_scale(out, p.apply(xin), p.apply_abs(xin), TOL32, what="5D, zero-speed directions")
     dg.close()
 
 

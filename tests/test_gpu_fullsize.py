@@ -228,6 +228,31 @@ def test_4d_fullsize_stage_fp32_sampled():
     dg.close()
 
 
+def test_5d_fullsize_stage_fp32_sampled():
+    """The persistent 5D kernel at the 5D workload's full size (73,728 cells,
+    each block walks ~80 of them with the next cell's copies in flight; E_3
+    changes sign inside a third of the x cells, where the minority side reads
+    its neighbour from global memory): a fused FP32-sweep stage on all 2^5
+    corner cells and 40 random ones."""
+    from paper_2002_08110_gb300 import DG, PREC_FP32, reference_nodes
+    w = W.config_adjoint()
+    zeta, _ = reference_nodes(w.k)
+    dg = DG(e_nodes=W.e_table(w, zeta), **W.dg_kwargs(w))
+    assert dg.get_launch(PREC_FP32)["variant"] == 2
+    p = oracle_for(w)
+    u = torch.tensor(W.initial_state(w, zeta), device="cuda")
+    w_in = u.float()
+    w_out = torch.empty_like(w_in)
+    uu = u.clone()
+    dt, _ = W.time_step(w)
+    stage = 2
+    dg.rk_stage(w_in, w_out, uu, stage, dt, prec=PREC_FP32)
+    dg.check()
+    cells = _sample_cells(p, 40, seed=7)
+    _check_stage_cells(p, u, uu, w_out, DeviceVector(w_in), cells, stage, dt)
+    dg.close()
+
+
 def test_5d_adjoint_fullsize_sampled():
     from paper_2002_08110_gb300 import DG, PREC_FP32, reference_nodes
     w = W.config_adjoint()
