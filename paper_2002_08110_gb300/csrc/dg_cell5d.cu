@@ -282,35 +282,37 @@ __global__ void __launch_bounds__(kT5, 4) k_cell5d(const KParams p) {
 
 // ---------------------------------------------------------------------------
 // Persistent variant for FP32 input.  One block of 64 threads walks the cells
-// blockIdx.x, blockIdx.x + gridDim.x, ... with the phases above, and every
-// cell it reads -- the cell itself and one upwind neighbour per direction --
-// arrives in shared memory by a tensor copy (cp.async.bulk.tensor, issued by
-// thread 0, completion counted on the buffer's mbarrier) instead of by the
-// threads' own loads, so that the copies of the next cell are in flight while
-// the current one is computed:
-//   the next cell itself: at the start of the current cell (two own-cell
-//   buffers alternate); its x1, x2, v1 and v2 neighbours: after phase B of the
-//   current cell; its v3 neighbour: after phase C.
+// blockIdx.x, blockIdx.x + gridDim.x, ... with the phases above.  The cell
+// itself and its upwind neighbours along x1, x2, v1 and v2 arrive in shared
+// memory by tensor copies (cp.async.bulk.tensor, issued by thread 0,
+// completion counted on the buffer's mbarrier) instead of by the threads' own
+// loads, so that the copies of the next cell are in flight while the current
+// one is computed: the next cell itself at the start of the current cell (two
+// own-cell buffers alternate), its four neighbours after phase B of the
+// current cell.  The v3 neighbour's values of phase C are loaded by each
+// thread (its own upwind side) at the start of phase B, into registers: one
+// buffer less lets seven blocks share an SM instead of six (measured 538 ->
+// 512 us per stage on the 5D workload).
 // A copied cell is the 2D box (16 floats, 64 rows) of the view (16, 64 ncells)
 // of the vector with the 64-byte swizzle: element (x, m) sits at
 //   16 m + 4 ((x >> 2) ^ ((m >> 1) & 3)) + (x & 3),
 // so that the 16-byte row reads of phase A are free of bank conflicts.
-// Where the speeds of a direction change sign inside a cell, the side with
-// more of the cell's nodes is copied and the threads of the other side read
-// their neighbour's values from global memory.  Which side is copied is
+// Where the speeds of a copied direction change sign inside a cell, the side
+// with more of the cell's nodes is copied and the threads of the other side
+// read their neighbour's values from global memory.  Which side is copied is
 // decided for the next cell by warp votes over its speeds.
 // Waits are bounded: after the limit the block latches DG_ERR_TIMEOUT's flag,
 // leaves the walk at the end of the cell, waits (bounded) for the copies it
 // has in flight and returns.
 constexpr int kT5p = 64;                  // threads per block, one cell at a time
-constexpr int kBuf5 = 7;                  // own cell x 2, upwind neighbours x 5
+constexpr int kBuf5 = 6;                  // own cell x 2, upwind neighbours along x1, x2, v1, v2
 constexpr int kO5 = 0, kN5 = 2;           // buffer indices: own cells, neighbours
 
 struct Cell5 {                            // block-uniform description of a cell
   unsigned cell;
   unsigned co[5];                         // coordinates (x1, x2, v1, v2, v3)
-  unsigned nb[5];                         // copied upwind neighbour per direction
-  int side[5];                            // its side: 0 (speed > 0), 1 (< 0), -1 none
+  unsigned nb[4];                         // copied upwind neighbour per direction (x1..v2)
+  int side[4];                            // its side: 0 (speed > 0), 1 (< 0), -1 none
 };
 
 // the four rows of x block m (u[x2][x1]) from a swizzled cell buffer
@@ -327,14 +329,14 @@ __device__ __forceinline__ void rows5(float (&u)[4][4], const float* buf, int m)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(kT5p, 7) k_cell5p(const KParams p, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) float sm_raw[];
   // swizzled buffers need 512-byte alignment (one KB of slack is allocated)
   float* const sb = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u) / 4;
   float* const br = sb + kBuf5 * kS5;     // the residual between the phases (off5 layout)
   __shared__ unsigned long long bar[kBuf5];
   __shared__ Cell5 s_c[2];
-  __shared__ int s_cnt[2][5][2];          // per warp and direction: nodes with speed > 0, < 0
+  __shared__ int s_cnt[2][4][2];          // per warp and copied direction: nodes with speed > 0, < 0
   const int t = threadIdx.x;
   const unsigned ncells = static_cast<unsigned>(p.ncells);
   const float* __restrict__ src = static_cast<const float*>(p.src);
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
   };
   auto vote = [&](const float (&sp)[5]) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
+    for (int j = 0; j < 4; ++j) {
       const int np = __popc(__ballot_sync(0xffffffffu, sp[j] > 0.f));
       const int nn = __popc(__ballot_sync(0xffffffffu, sp[j] < 0.f));
       if ((t & 31) == 0) {
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
   // thread 0: the copied side and neighbour of every direction
   auto sides = [&](Cell5& c) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
+    for (int j = 0; j < 4; ++j) {
       const int np = s_cnt[0][j][0] + s_cnt[1][j][0], nn = s_cnt[0][j][1] + s_cnt[1][j][1];
       const int sd = np == 0 && nn == 0 ? -1 : (np >= nn ? 0 : 1);
       c.side[j] = sd;
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
     sides(s_c[0]);
     stage(kO5, cell);
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
+    for (int j = 0; j < 4; ++j)
       if (s_c[0].side[j] >= 0) stage(kN5 + j, s_c[0].nb[j]);
   }
   __syncthreads();
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
       stage(kO5 + (cur ^ 1), next);
     }
     if (has_next) prefetch_u(next);
-    float u[4][4], r[4][4], nA[4][4], nB[4][4];
+    float u[4][4], r[4][4], nA[4][4], nB[4][4], nC[4][4];
 
     // ---- phase A: thread t = v node m, lines along x1 and x2
     {
@@ -514,6 +516,15 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
       int xb[4];                                 // swizzled offsets of element (xk, a + 4 b + 16 j)
 #pragma unroll
       for (int s = 0; s < 4; ++s) xb[s] = 256 * j + 4 * ((xk >> 2) ^ s) + (xk & 3);
+      // the upwind v3 neighbour's values of phase C (this thread, a3 = j), per
+      // thread side, requested now and used after phase B
+      if (sp[4] != 0.f) {
+        const float* g = src + static_cast<size_t>(upwind(C, 4, sp[4] > 0.f ? 0 : 1)) * kS5 + xk;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) nC[b][jj] = __ldg(g + 16 * (j + 4 * b + 16 * jj));
+      }
       if (C.side[2] >= 0) wait(kN5 + 2);
       if (C.side[3] >= 0) wait(kN5 + 3);
 #pragma unroll
@@ -575,7 +586,6 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
       int xc[2];                                 // swizzled offsets of element (xk, a3 + 4 b), b & 1 = 0, 1
 #pragma unroll
       for (int q = 0; q < 2; ++q) xc[q] = 16 * a3 + 4 * ((xk >> 2) ^ ((a3 >> 1) + 2 * q)) + (xk & 3);
-      if (C.side[4] >= 0) wait(kN5 + 4);
 #pragma unroll
       for (int b = 0; b < 4; ++b)
 #pragma unroll
@@ -583,23 +593,7 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
           u[b][jj] = bo[xc[b & 1] + 16 * (4 * b + 16 * jj)];
           r[b][jj] = br[off5(xk, a3 + 4 * b + 16 * jj)];
         }
-      if (sp[4] != 0.f) {
-        const int sd = sp[4] > 0.f ? 0 : 1;
-        if (sd == C.side[4]) {
-          const float* nb = sb + (kN5 + 4) * kS5;
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) nA[b][jj] = nb[xc[b & 1] + 16 * (4 * b + 16 * jj)];
-        } else {
-          const float* g = src + static_cast<size_t>(upwind(C, 4, sd)) * kS5 + xk;
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) nA[b][jj] = __ldg(g + 16 * (a3 + 4 * b + 16 * jj));
-        }
-      }
-      dir5(r, u, nA, sp[4], T);                  // v3: lines b (= v2), points jj
+      dir5(r, u, nC, sp[4], T);                  // v3: lines b (= v2), points jj
     }
 
     // ---- scatter / fused LSRK stage update (consecutive threads: consecutive x nodes)
@@ -639,12 +633,8 @@ __global__ void __launch_bounds__(kT5p, 6) k_cell5p(const KParams p, const __gri
       bad |= nanacc != 0.f;
     }
     fence_async_smem();
-    ok = __syncthreads_and(ok);                  // v3 buffer and own buffer free
+    ok = __syncthreads_and(ok);                  // the own buffer free
     if (!ok || !has_next) break;
-    if (t == 0) {
-      const Cell5& N = s_c[cur ^ 1];
-      if (N.side[4] >= 0) stage(kN5 + 4, N.nb[4]);
-    }
 #pragma unroll
     for (int j = 0; j < 5; ++j) sp[j] = spn[j];
     cell = next;

@@ -231,9 +231,9 @@ def test_4d_fullsize_stage_fp32_sampled():
 def test_5d_fullsize_stage_fp32_sampled():
     """The persistent 5D kernel at the 5D workload's full size (73,728 cells,
     each block walks ~80 of them with the next cell's copies in flight; E_3
-    changes sign inside a third of the x cells, where the minority side reads
-    its neighbour from global memory): a fused FP32-sweep stage on all 2^5
-    corner cells and 40 random ones."""
+    changes sign inside a third of the x cells, and its v3 neighbours are read
+    per thread): a fused FP32-sweep stage on all 2^5 corner cells and 40
+    random ones."""
     from paper_2002_08110_gb300 import DG, PREC_FP32, reference_nodes
     w = W.config_adjoint()
     zeta, _ = reference_nodes(w.k)
