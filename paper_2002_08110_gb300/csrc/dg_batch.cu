@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_batch4p(const BParams bp) {
   extern __shared__ __align__(16) float bsm4p[];
   float* const su = bsm4p;
   float* const sr = bsm4p + kCpb6 * kPS * kPad6;
+  float* const sn = bsm4p + 2 * kCpb6 * kPS * kPad6;   // staged neighbour values, 72 per thread
   __shared__ int s_tile;
   bool bad = false;
   if (threadIdx.x == 0) s_tile = atomicAdd(bp.counter, 1);
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_batch4p(const BParams bp) {
     bad |= cell4p_block<float, float, 1, false, kCpb6>(
         src, dst, I.u, static_cast<unsigned>(tl.cell0), tl.ncells, static_cast<unsigned>(I.ncells), ncell,
         cst, static_cast<float>(bp.b * I.dt), static_cast<float>(bp.a * I.dt), bp.a * I.dt,
-        bp.last_stage != 0, speeds, c_bt32[6], su, sr, bp.err);
+        bp.last_stage != 0, speeds, c_bt32[6], su, sr, sn, bp.err);
     __syncthreads();        // su / sr and s_tile are reused by the next tile
     if (threadIdx.x == 0) s_tile = next;
   }
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_batch4p(const BParams bp) {
 }
 
 cudaError_t launch_batch4p(const BParams& bp, cudaStream_t s) {
-  const size_t smem = 2 * static_cast<size_t>(kCpb6) * kPS * kPad6 * sizeof(float);
+  const size_t smem = (2 * static_cast<size_t>(kCpb6) * kPS * kPad6 + 72 * kThreads6) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_batch4p, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

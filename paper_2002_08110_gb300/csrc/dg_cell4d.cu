@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_cell4p(const KParams p) {
   extern __shared__ __align__(16) float sm4p[];
   float* const su = sm4p;
   float* const sr = sm4p + kCpb6 * kPS * kPad6;
+  float* const sn = sm4p + 2 * kCpb6 * kPS * kPad6;   // staged neighbour values, 72 per thread
   const unsigned ncells = static_cast<unsigned>(p.ncells);
   const unsigned cell0 = blockIdx.x * static_cast<unsigned>(kCpb6);
   const int nc = static_cast<int>(min(static_cast<unsigned>(kCpb6), ncells - cell0));
@@ -245,13 +246,13 @@ __global__ void __launch_bounds__(kThreads6, 2) k_cell4p(const KParams p) {
   const bool bad = cell4p_block<TIN, TW, MODE, ADJ, kCpb6>(
       static_cast<const TIN*>(p.src), static_cast<TW*>(p.dst), p.u, cell0, nc, ncells, ncell, cst,
       static_cast<float>(p.b_dt), static_cast<float>(p.a_dt), p.a_dt, p.last_stage != 0, speeds, p.t32,
-      su, sr, p.err);
+      su, sr, sn, p.err);
   if (bad) atomicOr(p.err, 1);
 }
 
 template <typename TIN, typename TW>
 cudaError_t launch4p(KParams& p, cudaStream_t s) {
-  const size_t smem = 2 * static_cast<size_t>(kCpb6) * kPS * kPad6 * sizeof(float);
+  const size_t smem = (2 * static_cast<size_t>(kCpb6) * kPS * kPad6 + 72 * kThreads6) * sizeof(float);
   auto kern = p.adjoint ? (p.mode == 0 ? k_cell4p<TIN, TW, 0, true> : k_cell4p<TIN, TW, 1, true>)
                         : (p.mode == 0 ? k_cell4p<TIN, TW, 0, false> : k_cell4p<TIN, TW, 1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -8,9 +8,23 @@
 
 #include "dg_convert.cuh"
 #include "dg_internal.h"
+#include "dg_tma.cuh"
 
 namespace dg {
 namespace {
+
+// Asynchronous 4-byte copy global -> shared (completion tracked per thread
+// in commit groups); the thread sees the value after cp_async_wait, the
+// others after that and a block barrier.
+__device__ __forceinline__ void cp_async4(float* smem, const float* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's commit groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <int N>
 struct Cell4 {
@@ -209,7 +223,7 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
                                              unsigned ncells, const int (&ncell)[4], const unsigned (&cst)[4],
                                              float b_dt, float a_dt, double a_dt64, bool last_stage,
                                              const Speeds& speeds, const Tab1D<float>& T, float* su,
-                                             float* sr, int* err) {
+                                             float* sr, float* sn, int* err) {
   constexpr int S = kPS, NP = S * S, PAD = kPad6;
   const int tid = threadIdx.x;
   const int cslot = tid / (2 * S);
@@ -237,51 +251,95 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
   };
   float c0 = 0.f, c1 = 0.f, e0 = 0.f, e1 = 0.f;
   if (active) speeds(cell, co, k, c0, c1, e0, e1);
-  // gather the block's cells (padded columns)
-  for (int i = tid; i < nc * NP; i += blockDim.x) {
-    const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
-    float v = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
-    if (ADJ) v *= w2p(T.winv, q) * w2p(T.winv, t);
-    su[(cc * S + t) * PAD + q] = v;
-  }
   float u[3][kP], r[3][kP], nA[3][kP], nB[3][kP];
-  // the upwind neighbours' columns (own half: 18 contiguous values)
-  auto load_col = [&](float (&v)[3][kP], unsigned nbc) {
-    const TIN* colp = src + static_cast<size_t>(nbc) * NP + static_cast<size_t>(S) * k + 18 * h;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int a = 0; a < kP; ++a) {
-        float x = cvt<float>(__ldg(colp + kP * i + a));
-        if (ADJ) x *= w2p(T.winv, a + kP * (3 * h + i)) * w2p(T.winv, k);
-        v[i][a] = x;
-      }
-  };
-  auto load_row = [&](float (&v)[3][kP], unsigned nbc) {
-    const TIN* rowp = src + static_cast<size_t>(nbc) * NP + k;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int a = 0; a < kP; ++a) {
-        const int m = a + kP * (3 * h + i);
-        float x = cvt<float>(__ldg(rowp + static_cast<size_t>(S) * m));
-        if (ADJ) x *= w2p(T.winv, m) * w2p(T.winv, k);
-        v[i][a] = x;
-      }
-  };
   auto zero = [](float (&v)[3][kP]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int a = 0; a < kP; ++a) v[i][a] = 0.f;
   };
-  zero(nA);
-  zero(nB);
-  if (active) {
-    if (c0 != 0.f) load_col(nA, upwind(0, c0 > 0.f));
-    if (c1 != 0.f) load_col(nB, upwind(1, c1 > 0.f));
+  // offsets of the thread's 18 values in a neighbour: its column k (own half,
+  // contiguous) for phase X, its row k for phase V; and the adjoint's factor
+  // M^{-1} of either (the same product of node weights)
+  auto col_off = [&](int i, int a) { return static_cast<size_t>(S) * k + 18 * h + kP * i + a; };
+  auto row_off = [&](int i, int a) { return static_cast<size_t>(k) + static_cast<size_t>(S) * (a + kP * (3 * h + i)); };
+  auto winv = [&](int i, int a) { return w2p(T.winv, a + kP * (3 * h + i)) * w2p(T.winv, k); };
+  const int nt = static_cast<int>(blockDim.x);
+  if constexpr (sizeof(TIN) == 4) {
+    // FP32 input: every value the block reads arrives by asynchronous copies
+    // into shared memory (no registers held while in flight), issued at once
+    // in two groups -- the cells and their x neighbours' columns, then the v
+    // neighbours' rows -- so that phase X waits only for the first and the
+    // second lands during it; the FP64 state of the epilogue is asked of L2
+    // ahead.  sn holds the thread's neighbour values at sn[v * nt + tid].
+    if (MODE == 1 && tid == 0)
+      prefetch_l2(uvec + static_cast<size_t>(cell0) * NP, static_cast<unsigned>(nc) * NP * 8u);
+    for (int i = tid; i < nc * NP; i += nt) {
+      const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
+      cp_async4(su + (cc * S + t) * PAD + q, src + static_cast<size_t>(cell0) * NP + i);
+    }
+    auto stage_nb = [&](int v0, unsigned nbc, bool rows) {
+      const TIN* g = src + static_cast<size_t>(nbc) * NP;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < kP; ++a)
+          cp_async4(sn + (v0 + kP * i + a) * nt + tid, g + (rows ? row_off(i, a) : col_off(i, a)));
+    };
+    if (active) {
+      if (c0 != 0.f) stage_nb(0, upwind(0, c0 > 0.f), false);
+      if (c1 != 0.f) stage_nb(18, upwind(1, c1 > 0.f), false);
+    }
+    cp_async_commit();
+    if (active) {
+      if (e0 != 0.f) stage_nb(36, upwind(2, e0 > 0.f), true);
+      if (e1 != 0.f) stage_nb(54, upwind(3, e1 > 0.f), true);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    if (ADJ) {
+      for (int i = tid; i < nc * NP; i += nt) {
+        const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
+        su[(cc * S + t) * PAD + q] *= w2p(T.winv, q) * w2p(T.winv, t);
+      }
+    }
+  } else {
+    // gather the block's cells (padded columns)
+    for (int i = tid; i < nc * NP; i += nt) {
+      const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
+      float v = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
+      if (ADJ) v *= w2p(T.winv, q) * w2p(T.winv, t);
+      su[(cc * S + t) * PAD + q] = v;
+    }
+  }
+  // the thread's neighbour values of a direction: from the staging slots
+  // v0.. (FP32 input) or loaded now (FP64 input); zero where the speed is zero
+  auto nbvals = [&](float (&v)[3][kP], int v0, float c, int j, bool rows) {
+    zero(v);
+    if (!active || c == 0.f) return;
+    if constexpr (sizeof(TIN) == 4) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < kP; ++a) v[i][a] = sn[(v0 + kP * i + a) * nt + tid] * (ADJ ? winv(i, a) : 1.f);
+    } else {
+      const TIN* g = src + static_cast<size_t>(upwind(j, c > 0.f)) * NP;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < kP; ++a)
+          v[i][a] = cvt<float>(__ldg(g + (rows ? row_off(i, a) : col_off(i, a)))) * (ADJ ? winv(i, a) : 1.f);
+    }
+  };
+  if constexpr (sizeof(TIN) != 4) {
+    nbvals(nA, 0, c0, 0, false);
+    nbvals(nB, 18, c1, 1, false);
   }
   __syncthreads();
+  if constexpr (sizeof(TIN) == 4) {
+    nbvals(nA, 0, c0, 0, false);
+    nbvals(nB, 18, c1, 1, false);
+  }
   // ---- phase X: column k, directions x1 (local), x2 (split)
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -300,13 +358,17 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
 #pragma unroll
       for (int a = 0; a < kP; ++a) sr[(cs * S + k) * PAD + a + kP * (3 * h + i)] = r[i][a];
   }
-  zero(nA);
-  zero(nB);
-  if (active) {
-    if (e0 != 0.f) load_row(nA, upwind(2, e0 > 0.f));
-    if (e1 != 0.f) load_row(nB, upwind(3, e1 > 0.f));
+  if constexpr (sizeof(TIN) == 4) {
+    cp_async_wait<0>();
+  } else {
+    nbvals(nA, 36, e0, 2, true);
+    nbvals(nB, 54, e1, 3, true);
   }
   __syncthreads();
+  if constexpr (sizeof(TIN) == 4) {
+    nbvals(nA, 36, e0, 2, true);
+    nbvals(nB, 54, e1, 3, true);
+  }
   // ---- phase V: row k, directions v1 (local), v2 (split)
   const size_t g0 = static_cast<size_t>(cell) * NP + k;
 #pragma unroll
@@ -327,13 +389,16 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
   }
   float nanacc = 0.f;
   if (active) {
+    // the FP64 state: all 18 values requested at once (one round trip)
+    double ua[3][kP];
+    if constexpr (MODE == 1) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < kP; ++a) ua[i][a] = __ldcs(uvec + g0 + static_cast<size_t>(S) * (a + kP * (3 * h + i)));
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      double ua[kP];
-      if constexpr (MODE == 1) {
-#pragma unroll
-        for (int a = 0; a < kP; ++a) ua[a] = __ldcs(uvec + g0 + static_cast<size_t>(S) * (a + kP * (3 * h + i)));
-      }
 #pragma unroll
       for (int a = 0; a < kP; ++a) {
         const size_t g = g0 + static_cast<size_t>(S) * (a + kP * (3 * h + i));
@@ -342,12 +407,12 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
         if constexpr (MODE == 0) {
           __stcs(dst + g, cvt<TW>(K));
         } else {
-          const double un = ua[a] + f32_to_f64_finite(b_dt * K);
+          const double un = ua[i][a] + f32_to_f64_finite(b_dt * K);
           __stcs(uvec + g, un);
           if constexpr (sizeof(TW) == 4)
-            __stcs(dst + g, last_stage ? f64_to_f32(un) : fmaf(a_dt, K, f64_to_f32(ua[a])));
+            __stcs(dst + g, last_stage ? f64_to_f32(un) : fmaf(a_dt, K, f64_to_f32(ua[i][a])));
           else
-            __stcs(dst + g, last_stage ? un : ua[a] + a_dt64 * f32_to_f64(K));
+            __stcs(dst + g, last_stage ? un : ua[i][a] + a_dt64 * f32_to_f64(K));
         }
       }
     }
