@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
   extern __shared__ __align__(16) unsigned char bsm4[];
   float* const su = reinterpret_cast<float*>(bsm4);
   float* const sr = su + BUF;
+  float* const sn = sr + BUF;     // the thread's phase V neighbour rows: sn[v * THREADS + tid]
   __shared__ int s_tile;
   const Tab1D<float>& T = c_bt32[N];
   const int c = threadIdx.x / S;
@@ -319,15 +320,40 @@ __global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
       return nb;
     };
     const float c0 = I.c32[0], c1 = I.c32[1], e0 = I.c32[2], e1 = I.c32[3];
+    // the tile's FP64 state is asked of L2 now (whole 16-byte units inside it)
+    if (threadIdx.x == 0) {
+      const uintptr_t b0 = reinterpret_cast<uintptr_t>(I.u + static_cast<size_t>(cell0) * NP);
+      const uintptr_t lo = (b0 + 15) & ~static_cast<uintptr_t>(15);
+      const uintptr_t hi = (b0 + static_cast<size_t>(nc) * NP * sizeof(double)) & ~static_cast<uintptr_t>(15);
+      if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), static_cast<unsigned>(hi - lo));
+    }
+    // asynchronous copies: the tile's cells (group 1), then the thread's two
+    // v neighbour rows (group 2, they land during phase X); the x
+    // neighbours' columns come into registers meanwhile
     for (int i = threadIdx.x; i < nc * NP; i += THREADS) {
       const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
-      su[(cc * S + t) * PAD + q] = src[static_cast<size_t>(cell0) * NP + i];
+      cp_async4(su + (cc * S + t) * PAD + q, src + static_cast<size_t>(cell0) * NP + i);
     }
+    cp_async_commit();
+    if (active) {
+      if (e0 != 0.f) {
+        const float* row = src + static_cast<size_t>(upwind(2, e0 > 0.f)) * NP + k;
+#pragma unroll
+        for (int m = 0; m < S; ++m) cp_async4(sn + m * THREADS + threadIdx.x, row + S * m);
+      }
+      if (e1 != 0.f) {
+        const float* row = src + static_cast<size_t>(upwind(3, e1 > 0.f)) * NP + k;
+#pragma unroll
+        for (int m = 0; m < S; ++m) cp_async4(sn + (S + m) * THREADS + threadIdx.x, row + S * m);
+      }
+    }
+    cp_async_commit();
     float u[S], r[S], nbA[S], nbB[S];
     if (active) {
       if (c0 != 0.f) load_col<N>(nbA, src, upwind(0, c0 > 0.f), k);
       if (c1 != 0.f) load_col<N>(nbB, src, upwind(1, c1 > 0.f), k);
     }
+    cp_async_wait<1>();
     __syncthreads();
     // phase X: column k, directions x1, x2 (order by bit 0)
     if (active) {
@@ -345,9 +371,8 @@ __global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
       }
 #pragma unroll
       for (int q = 0; q < S; ++q) sr[(c * S + k) * PAD + q] = r[q];
-      if (e0 != 0.f) load_row<N>(nbA, src, upwind(2, e0 > 0.f), k);
-      if (e1 != 0.f) load_row<N>(nbB, src, upwind(3, e1 > 0.f), k);
     }
+    cp_async_wait<0>();
     __syncthreads();
     if (active) {
       // phase V: row k, directions v1, v2 (order by bit 1)
@@ -360,6 +385,8 @@ __global__ void __launch_bounds__(THREADS) k_batch4(const BParams bp) {
       for (int m = 0; m < S; ++m) {
         u[m] = su[(c * S + m) * PAD + k];
         r[m] = sr[(c * S + m) * PAD + k];
+        nbA[m] = sn[m * THREADS + threadIdx.x];
+        nbB[m] = sn[(S + m) * THREADS + threadIdx.x];
       }
       if (bp.order & 2) {
         if (e1 != 0.f) dir4<N, N>(r, u, nbB, e1, T);
@@ -475,10 +502,13 @@ cudaError_t launch_batch4p(const BParams& bp, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// the cell and residual buffers, and the staged v neighbour rows (2 n^2 floats
+// per thread)
 template <int N>
 size_t batch4_smem(int threads) {
   const int S = N * N;
-  return 2 * static_cast<size_t>(threads / S) * S * (S + 1) * sizeof(float);
+  return (2 * static_cast<size_t>(threads / S) * S * (S + 1) + 2 * static_cast<size_t>(S) * threads) *
+         sizeof(float);
 }
 
 template <int N, int THREADS>
