@@ -508,7 +508,7 @@ typedef struct {
                         memory kernel).  Results differ only by rounding.     */
     int r4_max_n;    /* FP32 d = 4 groups with n = degree + 1 <= r4_max_n run
                         the 4D register kernel, the others the shared-memory
-                        kernel (1: none); default 4                           */
+                        kernel (1: none); default 6                           */
 } dg_batch_launch;
 /* One configuration timed by dg_batch_autotune and its time per step (ms). */
 typedef struct {

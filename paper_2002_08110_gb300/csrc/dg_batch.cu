@@ -563,7 +563,7 @@ struct dg_batch_ctx {
   int threads = 256;              // shared-memory kernel: threads per block
   int threads4 = 128;             // 4D register kernel: threads per block (n^2 per cell)
   int order = 0;                  // direction order bits (BParams::order)
-  int r4_max_n = 4;               // FP32 4D groups with n <= this run the register kernel
+  int r4_max_n = 6;               // FP32 4D groups with n <= this run the register kernels
   // members grouped by (d, n); each group's tiles for the two kernels
   struct Group {
     int d = 0, n = 0;

@@ -19,6 +19,9 @@ namespace {
 __device__ __forceinline__ void cp_async4(float* smem, const float* g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
 }
+__device__ __forceinline__ void cp_async8(float2* smem, const float* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // waits until at most N of this thread's commit groups are still in flight
 template <int N>
@@ -265,35 +268,44 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
   auto row_off = [&](int i, int a) { return static_cast<size_t>(k) + static_cast<size_t>(S) * (a + kP * (3 * h + i)); };
   auto winv = [&](int i, int a) { return w2p(T.winv, a + kP * (3 * h + i)) * w2p(T.winv, k); };
   const int nt = static_cast<int>(blockDim.x);
+  float2* const sn2 = reinterpret_cast<float2*>(sn);   // 8-byte aligned by the callers
   if constexpr (sizeof(TIN) == 4) {
     // FP32 input: every value the block reads arrives by asynchronous copies
     // into shared memory (no registers held while in flight), issued at once
     // in two groups -- the cells and their x neighbours' columns, then the v
     // neighbours' rows -- so that phase X waits only for the first and the
     // second lands during it; the FP64 state of the epilogue is asked of L2
-    // ahead.  sn holds the thread's neighbour values at sn[v * nt + tid].
+    // ahead.  sn holds the thread's neighbour values: the two columns as 18
+    // pairs (8-byte copies of contiguous values) at sn2[p * nt + tid], the two
+    // rows at sn[(36 + v) * nt + tid].
     if (MODE == 1 && tid == 0)
       prefetch_l2(uvec + static_cast<size_t>(cell0) * NP, static_cast<unsigned>(nc) * NP * 8u);
     for (int i = tid; i < nc * NP; i += nt) {
       const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
       cp_async4(su + (cc * S + t) * PAD + q, src + static_cast<size_t>(cell0) * NP + i);
     }
-    auto stage_nb = [&](int v0, unsigned nbc, bool rows) {
+    auto stage_col = [&](int p0, unsigned nbc) {
       const TIN* g = src + static_cast<size_t>(nbc) * NP;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int a = 0; a < kP; ++a)
-          cp_async4(sn + (v0 + kP * i + a) * nt + tid, g + (rows ? row_off(i, a) : col_off(i, a)));
+        for (int ap = 0; ap < kP / 2; ++ap) cp_async8(sn2 + (p0 + 3 * i + ap) * nt + tid, g + col_off(i, 2 * ap));
+    };
+    auto stage_row = [&](int v0, unsigned nbc) {
+      const TIN* g = src + static_cast<size_t>(nbc) * NP;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < kP; ++a) cp_async4(sn + (v0 + kP * i + a) * nt + tid, g + row_off(i, a));
     };
     if (active) {
-      if (c0 != 0.f) stage_nb(0, upwind(0, c0 > 0.f), false);
-      if (c1 != 0.f) stage_nb(18, upwind(1, c1 > 0.f), false);
+      if (c0 != 0.f) stage_col(0, upwind(0, c0 > 0.f));
+      if (c1 != 0.f) stage_col(9, upwind(1, c1 > 0.f));
     }
     cp_async_commit();
     if (active) {
-      if (e0 != 0.f) stage_nb(36, upwind(2, e0 > 0.f), true);
-      if (e1 != 0.f) stage_nb(54, upwind(3, e1 > 0.f), true);
+      if (e0 != 0.f) stage_row(36, upwind(2, e0 > 0.f));
+      if (e1 != 0.f) stage_row(54, upwind(3, e1 > 0.f));
     }
     cp_async_commit();
     cp_async_wait<1>();
@@ -318,10 +330,21 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
     zero(v);
     if (!active || c == 0.f) return;
     if constexpr (sizeof(TIN) == 4) {
+      if (!rows) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int a = 0; a < kP; ++a) v[i][a] = sn[(v0 + kP * i + a) * nt + tid] * (ADJ ? winv(i, a) : 1.f);
+          for (int ap = 0; ap < kP / 2; ++ap) {
+            const float2 x = sn2[(v0 / 2 + 3 * i + ap) * nt + tid];
+            v[i][2 * ap] = x.x * (ADJ ? winv(i, 2 * ap) : 1.f);
+            v[i][2 * ap + 1] = x.y * (ADJ ? winv(i, 2 * ap + 1) : 1.f);
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int a = 0; a < kP; ++a) v[i][a] = sn[(v0 + kP * i + a) * nt + tid] * (ADJ ? winv(i, a) : 1.f);
+      }
     } else {
       const TIN* g = src + static_cast<size_t>(upwind(j, c > 0.f)) * NP;
 #pragma unroll
