@@ -522,14 +522,16 @@ dg_status dg_batch_set_launch(dg_batch b, int tile_dofs, int threads);
  * dropped). */
 dg_status dg_batch_set_launch_ex(dg_batch b, const dg_batch_launch* cfg);
 dg_status dg_batch_get_launch(dg_batch b, dg_batch_launch* cfg);
-/* Autotuner of the batched launch: times one LSRK step (after one untimed
+/* Autotuner of the batched launch: times two LSRK steps (after one untimed
  * step) for each candidate on the caller's vectors (which are advanced by
- * those steps) and keeps the fastest; best_ms (may be NULL) receives its time
+ * those steps); best_ms (may be NULL) receives the kept configuration's time
  * per step.  The groups are separate launches whose times add, so it tunes
  * by coordinate descent: which 4D groups run the register kernel, then its
  * block size and direction order, then the shared-memory kernel's tile size
  * and block size, then its direction order; parameters that no group of the
- * batch uses are not varied. */
+ * batch uses are not varied.  The three fastest candidates and the starting
+ * configuration are then timed again over four steps and the fastest of
+ * those is kept. */
 dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void* const* w1,
                             const double* dt, int prec, void* stream, double* best_ms);
 /* The configurations the last dg_batch_autotune timed, in the order tried:

@@ -982,25 +982,30 @@ dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void*
   b->trials.clear();
   double best = 1e300;
   dg_batch_launch bcfg{b->tile_dofs, b->threads, b->threads4, b->order, b->r4_max_n};
+  const dg_batch_launch start = bcfg;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   // time two steps per candidate (after one untimed step that captures its
   // graphs) on the caller's buffers: their contents are advanced, as the
   // header states
-  auto trial = [&](const dg_batch_launch& c) {
-    if (dg_batch_set_launch_ex(b, &c) != DG_OK) return;
-    if (dg_batch_rk_step(b, u, w0, w1, dt, 1, prec, stream) != DG_OK) return;  // warm-up / capture
+  auto timed = [&](const dg_batch_launch& c, int steps) -> double {
+    if (dg_batch_set_launch_ex(b, &c) != DG_OK) return -1.0;
+    if (dg_batch_rk_step(b, u, w0, w1, dt, 1, prec, stream) != DG_OK) return -1.0;  // warm-up / capture
     cudaEventRecord(e0, s);
-    if (dg_batch_rk_step(b, u, w0, w1, dt, 2, prec, stream) != DG_OK) return;
+    if (dg_batch_rk_step(b, u, w0, w1, dt, steps, prec, stream) != DG_OK) return -1.0;
     cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) return;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    b->trials.push_back(
-        dg_batch_trial{c.tile_dofs, c.threads, c.threads4, c.order, c.r4_max_n, 0.5 * ms});
-    if (ms / 2 < best) {
-      best = ms / 2;
+    return static_cast<double>(ms) / steps;
+  };
+  auto trial = [&](const dg_batch_launch& c) {
+    const double ms = timed(c, 2);
+    if (ms < 0.0) return;
+    b->trials.push_back(dg_batch_trial{c.tile_dofs, c.threads, c.threads4, c.order, c.r4_max_n, ms});
+    if (ms < best) {
+      best = ms;
       bcfg = c;
     }
   };
@@ -1027,6 +1032,38 @@ dg_status dg_batch_autotune(dg_batch b, double* const* u, void* const* w0, void*
     trial(dg_batch_launch{b2.tile_dofs, b2.threads, b2.threads4, b2.order ^ 4, b2.r4_max_n});
   }
   if (b->trials.empty()) trial(bcfg);
+  // the minimum over many two-step trials favours a lucky one: the three
+  // fastest distinct configurations and the starting one are timed again
+  // over four steps, and the fastest of those is kept (these timings are
+  // recorded as trials too)
+  {
+    std::vector<dg_batch_trial> order(b->trials);
+    std::stable_sort(order.begin(), order.end(),
+                     [](const dg_batch_trial& x, const dg_batch_trial& y) { return x.ms < y.ms; });
+    auto same = [](const dg_batch_launch& x, const dg_batch_launch& y) {
+      return x.tile_dofs == y.tile_dofs && x.threads == y.threads && x.threads4 == y.threads4 &&
+             x.order == y.order && x.r4_max_n == y.r4_max_n;
+    };
+    std::vector<dg_batch_launch> finals{start};
+    for (const auto& t : order) {
+      if (finals.size() >= 4) break;
+      const dg_batch_launch c{t.tile_dofs, t.threads, t.threads4, t.order, t.r4_max_n};
+      bool dup = false;
+      for (const auto& f : finals) dup = dup || same(f, c);
+      if (!dup) finals.push_back(c);
+    }
+    double fbest = 1e300;
+    for (const auto& c : finals) {
+      const double ms = timed(c, 4);
+      if (ms < 0.0) continue;
+      b->trials.push_back(dg_batch_trial{c.tile_dofs, c.threads, c.threads4, c.order, c.r4_max_n, ms});
+      if (ms < fbest) {
+        fbest = ms;
+        bcfg = c;
+      }
+    }
+    if (fbest < 1e300) best = fbest;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   dg_status st = dg_batch_set_launch_ex(b, &bcfg);

@@ -156,9 +156,12 @@ def test_batch_launch_configurations_and_autotune_record():
     assert len(rec) >= 8
     assert len({r["r4_max_n"] for r in rec}) >= 3
     assert len({r["order"] for r in rec}) >= 2
-    assert abs(min(r["ms"] for r in rec) - best) <= 1e-9
+    # the search's fastest candidates are timed again at the end of the
+    # record; the kept configuration is the fastest of those re-timings
     kept = batch.get_launch()
+    assert best > 0
     assert any(all(r[k] == kept[k] for k in kept) and r["ms"] == best for r in rec)
+    assert all(r["ms"] >= best for r in rec[-2:])
     batch.close()
     for dg in dgs:
         dg.close()
