@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_batch4p(const BParams bp) {
     };
     const float* src = static_cast<const float*>(I.w[(bp.stage + bp.parity) & 1]);
     float* dst = static_cast<float*>(const_cast<void*>(I.w[(bp.stage + 1 + bp.parity) & 1]));
-    bad |= cell4p_block<float, float, 1, false, kCpb6>(
+    bad |= cell4p_block<float, float, 1, false, kCpb6, kThreads6>(
         src, dst, I.u, static_cast<unsigned>(tl.cell0), tl.ncells, static_cast<unsigned>(I.ncells), ncell,
         cst, static_cast<float>(bp.b * I.dt), static_cast<float>(bp.a * I.dt), bp.a * I.dt,
         bp.last_stage != 0, speeds, c_bt32[6], su, sr, sn, bp.err);

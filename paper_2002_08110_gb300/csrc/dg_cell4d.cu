@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_cell4p(const KParams p) {
     e0 = ADJ ? -ctv[0] : ctv[0];
     e1 = ADJ ? -ctv[1] : ctv[1];
   };
-  const bool bad = cell4p_block<TIN, TW, MODE, ADJ, kCpb6>(
+  const bool bad = cell4p_block<TIN, TW, MODE, ADJ, kCpb6, kThreads6>(
       static_cast<const TIN*>(p.src), static_cast<TW*>(p.dst), p.u, cell0, nc, ncells, ncell, cst,
       static_cast<float>(p.b_dt), static_cast<float>(p.a_dt), p.a_dt, p.last_stage != 0, speeds, p.t32,
       su, sr, sn, p.err);

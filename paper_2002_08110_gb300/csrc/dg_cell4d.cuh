@@ -22,6 +22,9 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* g) {
 __device__ __forceinline__ void cp_async8(float2* smem, const float* g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
 }
+__device__ __forceinline__ void cp_async16(float* smem, const float* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // waits until at most N of this thread's commit groups are still in flight
 template <int N>
@@ -140,7 +143,7 @@ namespace {
 // their three values of each line and add their partial traces by shuffles.
 constexpr int kP = 6;     // n
 constexpr int kPS = 36;   // n^2
-constexpr int kPad6 = 37; // padded column stride in shared memory
+constexpr int kPad6 = 36; // column stride in shared memory (unpadded: a cell's global layout)
 
 // the lines along the first digit (3 per thread); POS: the upwind side
 template <bool POS>
@@ -220,7 +223,7 @@ __device__ __forceinline__ float w2p(const float* w, int m) { return w[m % kP] *
 // last stage).  ADJ: L^T = M L(-a) M^{-1} (input and neighbours scaled by
 // the inverse node weights, output by the weights).  su / sr: shared buffers
 // of CPB cells (kPS columns of kPad6 floats).  Returns the non-finite flag.
-template <typename TIN, typename TW, int MODE, bool ADJ, int CPB, typename Speeds>
+template <typename TIN, typename TW, int MODE, bool ADJ, int CPB, int NT, typename Speeds>
 __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __restrict__ dst,
                                              double* __restrict__ uvec, unsigned cell0, int nc,
                                              unsigned ncells, const int (&ncell)[4], const unsigned (&cst)[4],
@@ -267,7 +270,7 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
   auto col_off = [&](int i, int a) { return static_cast<size_t>(S) * k + 18 * h + kP * i + a; };
   auto row_off = [&](int i, int a) { return static_cast<size_t>(k) + static_cast<size_t>(S) * (a + kP * (3 * h + i)); };
   auto winv = [&](int i, int a) { return w2p(T.winv, a + kP * (3 * h + i)) * w2p(T.winv, k); };
-  const int nt = static_cast<int>(blockDim.x);
+  constexpr int nt = NT;
   float2* const sn2 = reinterpret_cast<float2*>(sn);   // 8-byte aligned by the callers
   if constexpr (sizeof(TIN) == 4) {
     // FP32 input: every value the block reads arrives by asynchronous copies
@@ -280,9 +283,13 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
     // rows at sn[(36 + v) * nt + tid].
     if (MODE == 1 && tid == 0)
       prefetch_l2(uvec + static_cast<size_t>(cell0) * NP, static_cast<unsigned>(nc) * NP * 8u);
-    for (int i = tid; i < nc * NP; i += nt) {
-      const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
-      cp_async4(su + (cc * S + t) * PAD + q, src + static_cast<size_t>(cell0) * NP + i);
+    // the block's cells keep their global layout (columns of 36 values):
+    // 16-byte copies where the vector is 16-byte aligned (a cell is 5184 bytes)
+    const float* gc = src + static_cast<size_t>(cell0) * NP;
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+      for (int i = tid; i < nc * (NP / 4); i += nt) cp_async16(su + 4 * i, gc + 4 * i);
+    } else {
+      for (int i = tid; i < nc * NP; i += nt) cp_async4(su + i, gc + i);
     }
     auto stage_col = [&](int p0, unsigned nbc) {
       const TIN* g = src + static_cast<size_t>(nbc) * NP;
@@ -310,9 +317,17 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
     cp_async_commit();
     cp_async_wait<1>();
     if (ADJ) {
-      for (int i = tid; i < nc * NP; i += nt) {
-        const int cc = i / NP, r0 = i - cc * NP, t = r0 / S, q = r0 - t * S;
-        su[(cc * S + t) * PAD + q] *= w2p(T.winv, q) * w2p(T.winv, t);
+      // each thread scales the values it copied itself (its copies are complete)
+      auto scale = [&](int e) {
+        const int r0 = e % NP, t = r0 / S, q = r0 - t * S;
+        su[e] *= w2p(T.winv, q) * w2p(T.winv, t);
+      };
+      if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        for (int i = tid; i < nc * (NP / 4); i += nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) scale(4 * i + e);
+      } else {
+        for (int i = tid; i < nc * NP; i += nt) scale(i);
       }
     }
   } else {
@@ -364,22 +379,29 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
     nbvals(nB, 18, c1, 1, false);
   }
   // ---- phase X: column k, directions x1 (local), x2 (split)
+  {
+    // the thread's 18 values of column k: contiguous, 8-byte aligned
+    const float2* col = reinterpret_cast<const float2*>(su + (cs * S + k) * PAD + 18 * h);
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < kP; ++a) {
-      u[i][a] = su[(cs * S + k) * PAD + a + kP * (3 * h + i)];
-      r[i][a] = 0.f;
+    for (int j = 0; j < 9; ++j) {
+      const float2 x = col[j];
+      u[(2 * j) / kP][(2 * j) % kP] = x.x;
+      u[(2 * j) / kP][(2 * j) % kP + 1] = x.y;
     }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int a = 0; a < kP; ++a) r[i][a] = 0.f;
+  }
   pdir_local_any(r, u, nA, c0, T);
   pdir_split(r, u, nB, c1, h, T);
   // lanes without a cell (they ran the split direction for the shuffles
   // only) must not write: their slot is clamped onto a real cell's
   if (active) {
+    float2* col = reinterpret_cast<float2*>(sr + (cs * S + k) * PAD + 18 * h);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int a = 0; a < kP; ++a) sr[(cs * S + k) * PAD + a + kP * (3 * h + i)] = r[i][a];
+    for (int j = 0; j < 9; ++j)
+      col[j] = make_float2(r[(2 * j) / kP][(2 * j) % kP], r[(2 * j) / kP][(2 * j) % kP + 1]);
   }
   if constexpr (sizeof(TIN) == 4) {
     cp_async_wait<0>();
