@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_batch4p(const BParams bp) {
 }
 
 cudaError_t launch_batch4p(const BParams& bp, cudaStream_t s) {
-  const size_t smem = (2 * static_cast<size_t>(kCpb6) * kPS * kPad6 + 72 * kThreads6) * sizeof(float);
+  const size_t smem = (2 * static_cast<size_t>(kCpb6) * kPS * kPad6 + 72 * kThreads6 + kSplitTab) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_batch4p, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads6, 2) k_cell4p(const KParams p) {
 
 template <typename TIN, typename TW>
 cudaError_t launch4p(KParams& p, cudaStream_t s) {
-  const size_t smem = (2 * static_cast<size_t>(kCpb6) * kPS * kPad6 + 72 * kThreads6) * sizeof(float);
+  const size_t smem = (2 * static_cast<size_t>(kCpb6) * kPS * kPad6 + 72 * kThreads6 + kSplitTab) * sizeof(float);
   auto kern = p.adjoint ? (p.mode == 0 ? k_cell4p<TIN, TW, 0, true> : k_cell4p<TIN, TW, 1, true>)
                         : (p.mode == 0 ? k_cell4p<TIN, TW, 0, false> : k_cell4p<TIN, TW, 1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -164,25 +164,52 @@ __device__ __forceinline__ void pdir_local(float (&r)[3][kP], const float (&u)[3
   }
 }
 
+// Coefficients of the split direction for each upwind side and half h, in
+// shared memory so that a thread reads its set with six 16-byte loads
+// (indexed by its own side and h) instead of computed constant-memory loads:
+// entry (side s, h) at tab[24 (2 s + h) ...]: Go[i][j] = G[q][3h + j] (9),
+// Gq[i][j] = G[q][3 (1 - h) + j] (9), L[i] (3), the trace weights lo[j] of the
+// thread's own points (3), q = 3h + i; s = 0: Gp, Lm, lp; s = 1: Gn, -Lp, lm.
+constexpr int kSplitTab = 96;
+__device__ __forceinline__ void split_tab_build(float* tab, const Tab1D<float>& T, int tid) {
+  if (tid >= kSplitTab) return;
+  const int v = tid / 24, e = tid - 24 * (tid / 24);
+  const bool pos = (v >> 1) == 0;
+  const int h = v & 1, own = 3 * h, par = 3 * (1 - h);
+  float x;
+  if (e < 9) {
+    const int q = own + e / 3, j = e % 3;
+    x = pos ? T.Gp[q * kP + own + j] : T.Gn[q * kP + own + j];
+  } else if (e < 18) {
+    const int q = own + (e - 9) / 3, j = (e - 9) % 3;
+    x = pos ? T.Gp[q * kP + par + j] : T.Gn[q * kP + par + j];
+  } else if (e < 21) {
+    const int q = own + e - 18;
+    x = pos ? T.Lm[q] : -T.Lp[q];
+  } else {
+    const int q = own + e - 21;
+    x = pos ? T.lp[q] : T.lm[q];
+  }
+  tab[tid] = x;
+}
+
 // the 6 lines along the second digit, split between the pair (lane ^ 1): the
 // thread computes its own points q = 3h + i; every lane of the warp runs this
 // (the shuffles need all of them), with zero speed where there is no work
 __device__ __forceinline__ void pdir_split(float (&r)[3][kP], const float (&u)[3][kP],
                                            const float (&nb)[3][kP], float c, int h,
-                                           const Tab1D<float>& T) {
-  const bool pos = c > 0.f;
-  const int own = 3 * h, par = 3 * (1 - h);
-  float Go[3][3], Gq[3][3], L[3], lo[3];
+                                           const float* tab) {
+  float cf[24];
+  {
+    const float4* t4 = reinterpret_cast<const float4*>(tab + 24 * (2 * (c > 0.f ? 0 : 1) + h));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int q = own + i;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      Go[i][j] = pos ? T.Gp[q * kP + own + j] : T.Gn[q * kP + own + j];
-      Gq[i][j] = pos ? T.Gp[q * kP + par + j] : T.Gn[q * kP + par + j];
+    for (int i = 0; i < 6; ++i) {
+      const float4 x = t4[i];
+      cf[4 * i] = x.x;
+      cf[4 * i + 1] = x.y;
+      cf[4 * i + 2] = x.z;
+      cf[4 * i + 3] = x.w;
     }
-    L[i] = pos ? T.Lm[q] : -T.Lp[q];
-    lo[i] = pos ? T.lp[q] : T.lm[q];
   }
 #pragma unroll
   for (int a = 0; a < kP; ++a) {
@@ -192,15 +219,15 @@ __device__ __forceinline__ void pdir_split(float (&r)[3][kP], const float (&u)[3
     // the upwind neighbour's trace of line a: own half, then the partner's
     float t = 0.f;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) t = fmaf(lo[j], nb[j][a], t);
+    for (int j = 0; j < 3; ++j) t = fmaf(cf[21 + j], nb[j][a], t);
     t += __shfl_xor_sync(0xffffffffu, t, 1);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      float acc = L[i] * t;
+      float acc = cf[18 + i] * t;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) acc = fmaf(Go[i][j], u[j][a], acc);
+      for (int j = 0; j < 3; ++j) acc = fmaf(cf[3 * i + j], u[j][a], acc);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) acc = fmaf(Gq[i][j], v[j], acc);
+      for (int j = 0; j < 3; ++j) acc = fmaf(cf[9 + 3 * i + j], v[j], acc);
       r[i][a] = fmaf(c, acc, r[i][a]);
     }
   }
@@ -222,7 +249,10 @@ __device__ __forceinline__ float w2p(const float* w, int m) { return w[m % kP] *
 // dst = K; MODE 1: u += b dt K (FP64), dst = u_old + a dt K (or u_new at the
 // last stage).  ADJ: L^T = M L(-a) M^{-1} (input and neighbours scaled by
 // the inverse node weights, output by the weights).  su / sr: shared buffers
-// of CPB cells (kPS columns of kPad6 floats).  Returns the non-finite flag.
+// of CPB cells (kPS columns of kPad6 floats); sn: 72 floats per thread of the
+// block (the staged neighbour values, FP32 input) followed by the kSplitTab
+// floats of the split direction's coefficients (16-byte aligned).  Returns
+// the non-finite flag.
 template <typename TIN, typename TW, int MODE, bool ADJ, int CPB, int NT, typename Speeds>
 __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __restrict__ dst,
                                              double* __restrict__ uvec, unsigned cell0, int nc,
@@ -271,6 +301,9 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
   auto row_off = [&](int i, int a) { return static_cast<size_t>(k) + static_cast<size_t>(S) * (a + kP * (3 * h + i)); };
   auto winv = [&](int i, int a) { return w2p(T.winv, a + kP * (3 * h + i)) * w2p(T.winv, k); };
   constexpr int nt = NT;
+  // the split direction's coefficient table, after the staged values
+  float* const stab = sn + 72 * NT;
+  split_tab_build(stab, T, tid);
   float2* const sn2 = reinterpret_cast<float2*>(sn);   // 8-byte aligned by the callers
   if constexpr (sizeof(TIN) == 4) {
     // FP32 input: every value the block reads arrives by asynchronous copies
@@ -394,7 +427,7 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
       for (int a = 0; a < kP; ++a) r[i][a] = 0.f;
   }
   pdir_local_any(r, u, nA, c0, T);
-  pdir_split(r, u, nB, c1, h, T);
+  pdir_split(r, u, nB, c1, h, stab);
   // lanes without a cell (they ran the split direction for the shuffles
   // only) must not write: their slot is clamped onto a real cell's
   if (active) {
@@ -425,7 +458,7 @@ __device__ __forceinline__ bool cell4p_block(const TIN* __restrict__ src, TW* __
       r[i][a] = sr[(cs * S + m) * PAD + k];
     }
   pdir_local_any(r, u, nA, e0, T);
-  pdir_split(r, u, nB, e1, h, T);
+  pdir_split(r, u, nB, e1, h, stab);
   if (ADJ) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
