@@ -31,7 +31,10 @@ namespace {
 // Every global read is issued as early as its address is known, so that a
 // thread has several in flight: the upwind neighbours' columns before the
 // barrier that completes the gather, their rows before the exchange, the
-// FP64 state in chunks of 8 ahead of its use.
+// FP64 state in chunks of 8 ahead of its use.  With FP32 input the gather
+// and the neighbours' rows are asynchronous copies into shared memory issued
+// together at the start (the rows land during phase X; sn holds the
+// thread's two rows at sn[m * THREADS + tid]).
 template <int N, typename TIN, typename TW, int MODE, bool ADJ>
 __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(const KParams p) {
   using C = Cell4<N>;
@@ -40,6 +43,8 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
   extern __shared__ __align__(16) float sm4[];
   float* const su = sm4;
   float* const sr = sm4 + C::BUF;
+  float* const sn = sr + C::BUF;
+  constexpr bool kAsync = sizeof(TIN) == 4;
   const TIN* __restrict__ src = static_cast<const TIN*>(p.src);
   const Tab1D<float>& T = p.t32;
   const unsigned ncells = static_cast<unsigned>(p.ncells);
@@ -83,17 +88,50 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
   }
 
   // gather the block's cells, each column padded to S + 1 floats
+  if constexpr (kAsync) {
 #pragma unroll 4
-  for (int i = threadIdx.x; i < nc * NP; i += C::THREADS) {
-    const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
-    float v = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
-    if (ADJ) v *= w2<N>(T.winv, q) * w2<N>(T.winv, t);
-    su[(cc * S + t) * PAD + q] = v;
+    for (int i = threadIdx.x; i < nc * NP; i += C::THREADS) {
+      const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
+      cp_async4(su + (cc * S + t) * PAD + q, reinterpret_cast<const float*>(src) + static_cast<size_t>(cell0) * NP + i);
+    }
+    cp_async_commit();
+    if (active) {
+      const float* s32 = reinterpret_cast<const float*>(src);
+      if (e0 != 0.f) {
+        const float* row = s32 + static_cast<size_t>(upwind(2, e0 > 0.f)) * NP + k;
+#pragma unroll
+        for (int m = 0; m < S; ++m) cp_async4(sn + m * C::THREADS + threadIdx.x, row + S * m);
+      }
+      if (e1 != 0.f) {
+        const float* row = s32 + static_cast<size_t>(upwind(3, e1 > 0.f)) * NP + k;
+#pragma unroll
+        for (int m = 0; m < S; ++m) cp_async4(sn + (S + m) * C::THREADS + threadIdx.x, row + S * m);
+      }
+    }
+    cp_async_commit();
+  } else {
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nc * NP; i += C::THREADS) {
+      const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
+      float v = cvt<float>(src[static_cast<size_t>(cell0) * NP + i]);
+      if (ADJ) v *= w2<N>(T.winv, q) * w2<N>(T.winv, t);
+      su[(cc * S + t) * PAD + q] = v;
+    }
   }
   float u[S], r[S], nbA[S], nbB[S];
   if (active) {
     if (c0 != 0.f) load_col<N>(nbA, src, upwind(0, c0 > 0.f), k);
     if (c1 != 0.f) load_col<N>(nbB, src, upwind(1, c1 > 0.f), k);
+  }
+  if constexpr (kAsync) {
+    cp_async_wait<1>();
+    if (ADJ) {                           // each thread scales the values it copied
+#pragma unroll 4
+      for (int i = threadIdx.x; i < nc * NP; i += C::THREADS) {
+        const int cc = i / NP, rem = i - cc * NP, t = rem / S, q = rem - t * S;
+        su[(cc * S + t) * PAD + q] *= w2<N>(T.winv, q) * w2<N>(T.winv, t);
+      }
+    }
   }
   __syncthreads();
 
@@ -117,11 +155,21 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
     if (c1 != 0.f) dir4<N, N>(r, u, nbB, c1, T);
 #pragma unroll
     for (int q = 0; q < S; ++q) sr[(c * S + k) * PAD + q] = r[q];
-    if (e0 != 0.f) load_row<N>(nbA, src, upwind(2, e0 > 0.f), k);
-    if (e1 != 0.f) load_row<N>(nbB, src, upwind(3, e1 > 0.f), k);
+    if constexpr (!kAsync) {
+      if (e0 != 0.f) load_row<N>(nbA, src, upwind(2, e0 > 0.f), k);
+      if (e1 != 0.f) load_row<N>(nbB, src, upwind(3, e1 > 0.f), k);
+    }
   }
+  if constexpr (kAsync) cp_async_wait<0>();
   __syncthreads();
   if (!active) return;
+  if constexpr (kAsync) {
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+      nbA[m] = sn[m * C::THREADS + threadIdx.x];
+      nbB[m] = sn[(S + m) * C::THREADS + threadIdx.x];
+    }
+  }
 
   // ---- phase V: row k, directions v1, v2
   const size_t g0 = static_cast<size_t>(cell) * NP + k;
@@ -200,7 +248,8 @@ __global__ void __launch_bounds__(Cell4<N>::THREADS, Cell4<N>::MINB) k_cell4d(co
 template <int N, typename TIN, typename TW>
 cudaError_t launch4(KParams& p, cudaStream_t s) {
   using C = Cell4<N>;
-  const size_t smem = 2 * static_cast<size_t>(C::BUF) * sizeof(float);
+  // cell and residual buffers; FP32 input: the staged neighbour rows
+  const size_t smem = (2 * static_cast<size_t>(C::BUF) + (sizeof(TIN) == 4 ? 2 * C::S * C::THREADS : 0)) * sizeof(float);
   auto kern = p.adjoint ? (p.mode == 0 ? k_cell4d<N, TIN, TW, 0, true> : k_cell4d<N, TIN, TW, 1, true>)
                         : (p.mode == 0 ? k_cell4d<N, TIN, TW, 0, false> : k_cell4d<N, TIN, TW, 1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
