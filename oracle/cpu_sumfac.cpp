@@ -26,6 +26,7 @@
 //
 // C entry points (ctypes, oracle/sumfac.py):
 //   sf_create(...) -> plan, sf_destroy(plan), sf_apply(plan, src, dst),
+//   sf_apply_abs(plan, src, dst) (the term scale),
 //   sf_rk_stage(plan, w_in, w_out, u, a_dt, b_dt, last, cell_lo, cell_hi),
 //   sf_threads().
 #include <cmath>
@@ -245,7 +246,13 @@ void sf_destroy(sf_plan* p) { delete p; }
 namespace {
 
 // K = M^{-1} A(src) on one cell (b: scratch of n^d doubles; K written to out).
+// ABS: the same sums with the absolute value of every factor and term (the
+// term scale M^{-1} |A| |src| that bounds the rounding error of an
+// evaluation in reduced precision); the upwind choice stays with the sign of
+// the speed.
+template <bool ABS>
 void cell_operator(const sf_plan* p, const double* src, long long cell, double* b, double* out) {
+  auto f = [](double x) { return ABS ? std::fabs(x) : x; };
   const int n = p->n, d = p->d, dx = p->dx, npc = p->npc;
   const double* u = src + cell * npc;
   for (int q = 0; q < npc; ++q) b[q] = 0.0;
@@ -271,6 +278,7 @@ void cell_operator(const sf_plan* p, const double* src, long long cell, double* 
         double c;
         if (j < dx) c = p->cx[(static_cast<size_t>(cv) * p->nqv + base / p->nqx) * dx + j];
         else c = p->cv[(static_cast<size_t>(cx) * p->nqx + base % p->nqx) * p->dv + (j - dx)];
+        const double ca = f(c);
         double wperp = p->detJ;
         {
           int q = base;
@@ -282,24 +290,26 @@ void cell_operator(const sf_plan* p, const double* src, long long cell, double* 
         // cell term
         for (int q = 0; q < n; ++q) {
           double acc = 0.0;
-          for (int pp = 0; pp < n; ++pp) acc += p->Dw[q][pp] * c * u[base + pp * s];
+          for (int pp = 0; pp < n; ++pp) acc += f(p->Dw[q][pp]) * ca * f(u[base + pp * s]);
           b[base + q * s] += wperp * acc;
         }
         // upwind traces on the two faces
         double tp = 0.0, tm = 0.0;
         if (c > 0) {
           for (int pp = 0; pp < n; ++pp) {
-            tp += p->lp[pp] * u[base + pp * s];     // own trace leaves through +1
-            tm += p->lp[pp] * um[base + pp * s];    // the lower neighbour's +1 trace enters
+            tp += f(p->lp[pp]) * f(u[base + pp * s]);     // own trace leaves through +1
+            tm += f(p->lp[pp]) * f(um[base + pp * s]);    // the lower neighbour's +1 trace enters
           }
         } else {
           for (int pp = 0; pp < n; ++pp) {
-            tp += p->lm[pp] * up[base + pp * s];    // the upper neighbour's -1 trace enters
-            tm += p->lm[pp] * u[base + pp * s];     // own trace leaves through -1
+            tp += f(p->lm[pp]) * f(up[base + pp * s]);    // the upper neighbour's -1 trace enters
+            tm += f(p->lm[pp]) * f(u[base + pp * s]);     // own trace leaves through -1
           }
         }
-        const double fp = c * tp, fm = c * tm;
-        for (int q = 0; q < n; ++q) b[base + q * s] += wperp * (-p->lp[q] * fp + p->lm[q] * fm);
+        const double fp = ca * tp, fm = ca * tm;
+        for (int q = 0; q < n; ++q)
+          b[base + q * s] += ABS ? wperp * (f(p->lp[q]) * fp + f(p->lm[q]) * fm)
+                                 : wperp * (-p->lp[q] * fp + p->lm[q] * fm);
       }
   }
   // inverse of the diagonal mass matrix W_q |J|
@@ -325,7 +335,19 @@ int sf_apply(const sf_plan* p, const double* src, double* dst) {
   {
     std::vector<double> b(p->npc);
 #pragma omp for schedule(static)
-    for (long long e = 0; e < p->ncells; ++e) cell_operator(p, src, e, b.data(), dst + e * p->npc);
+    for (long long e = 0; e < p->ncells; ++e) cell_operator<false>(p, src, e, b.data(), dst + e * p->npc);
+  }
+  return 0;
+}
+
+// dst = M^{-1} |A| |src|, the term scale of every value (see cell_operator).
+int sf_apply_abs(const sf_plan* p, const double* src, double* dst) {
+  if (!p || !src || !dst) return 1;
+#pragma omp parallel
+  {
+    std::vector<double> b(p->npc);
+#pragma omp for schedule(static)
+    for (long long e = 0; e < p->ncells; ++e) cell_operator<true>(p, src, e, b.data(), dst + e * p->npc);
   }
   return 0;
 }
@@ -343,7 +365,7 @@ int sf_rk_stage(const sf_plan* p, const double* w_in, double* w_out, double* u, 
     std::vector<double> b(p->npc), K(p->npc);
 #pragma omp for schedule(static)
     for (long long e = cell_lo; e < cell_hi; ++e) {
-      cell_operator(p, w_in, e, b.data(), K.data());
+      cell_operator<false>(p, w_in, e, b.data(), K.data());
       double* ue = u + e * p->npc;
       double* we = w_out + e * p->npc;
       for (int q = 0; q < p->npc; ++q) {

@@ -56,6 +56,8 @@ def load():
         lib.sf_destroy.argtypes = [vp]
         lib.sf_apply.restype = ctypes.c_int
         lib.sf_apply.argtypes = [vp, vp, vp]
+        lib.sf_apply_abs.restype = ctypes.c_int
+        lib.sf_apply_abs.argtypes = [vp, vp, vp]
         lib.sf_rk_stage.restype = ctypes.c_int
         lib.sf_rk_stage.argtypes = [vp, vp, vp, vp, d, d, ctypes.c_int, ctypes.c_longlong,
                                     ctypes.c_longlong]
@@ -110,6 +112,15 @@ class SumFac:
         assert src.shape == (self.n_dofs,)
         dst = np.empty_like(src) if dst is None else dst
         assert self.lib.sf_apply(self.plan, src.ctypes.data, dst.ctypes.data) == 0
+        return dst
+
+    def apply_abs(self, src, dst=None):
+        """The term scale M^{-1} |A| |src| (every factor and term in absolute
+        value, upwind choices unchanged), as ``dg.Problem.apply_abs``."""
+        src = np.ascontiguousarray(src, dtype=np.float64)
+        assert src.shape == (self.n_dofs,)
+        dst = np.empty_like(src) if dst is None else dst
+        assert self.lib.sf_apply_abs(self.plan, src.ctypes.data, dst.ctypes.data) == 0
         return dst
 
     def rk_stage(self, w_in, w_out, u, a_dt, b_dt, last=False, cells=None):

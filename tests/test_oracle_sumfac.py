@@ -3,8 +3,9 @@ against the oracle's axis-wise and dense Kronecker routes on small meshes:
 the same operator to round-off (1e-13 of the term scale, element by
 element), in every dimension split and degree, with constant and
 phase-space fields, sheared x-meshes and one- and two-cell directions; and
-the fused LSRK stage.  It is the timed CPU baseline at full size, so it is
-pinned here against the plain definition first."""
+the fused LSRK stage; its term scale against ``Problem.apply_abs``.  It is
+the timed CPU baseline and the full-size parity reference, so it is pinned
+here against the plain definition first."""
 import numpy as np
 import pytest
 
@@ -54,7 +55,12 @@ def test_sumfac_equals_oracle(case, kind):
     got = sf.apply(u)
     ref = p.apply(u)
     assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
-    assert_term_scale(got, ref, p.apply_abs(u), 1e-13, what="sum factorisation vs oracle")
+    scale = p.apply_abs(u)
+    assert_term_scale(got, ref, scale, 1e-13, what="sum factorisation vs oracle")
+    # the term scale (the tolerance of the full-size GPU parity tests)
+    got_abs = sf.apply_abs(u)
+    assert np.all(got_abs >= 0)
+    assert np.max(np.abs(got_abs - scale) / np.maximum(scale, 1e-300)) <= 1e-13
     if p.dofs_per_cell <= 64:
         dense = p.apply_dense(u)
         assert np.linalg.norm(got - dense) <= 1e-13 * np.linalg.norm(dense)
