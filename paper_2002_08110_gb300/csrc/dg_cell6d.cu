@@ -684,6 +684,7 @@ __device__ __forceinline__ void nb_traces_p(float (&tr)[16], const float* nbv, c
 // The 16 split lines along the middle digit: the thread owns rows q = h and
 // h + 2 and receives the partner's two values of each line by shuffles.  The
 // rows depend on h, so their entries (scaled by c) are loaded into registers.
+template <bool PACK>
 __device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32],
                                             const float (&tr)[16], float c, int tb, float tscale, int h) {
   const int side = tb + (signbit(c) ? 1 : 0);
@@ -697,6 +698,30 @@ __device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32]
     G[b][2] = c * c_G[side][q * 4 + 1 - h];
     G[b][3] = c * c_G[side][q * 4 + 3 - h];
     Ln[b] = c * c_Ln[side][q];
+  }
+  if constexpr (PACK) {
+    // lines l and l + 1 (first digit a even and odd) hold adjacent values: they
+    // go through the packed FP32 FMA together (per lane the same fmaf sequence)
+#pragma unroll
+    for (int l = 0; l < 16; l += 2) {
+      const float2 u0 = make_float2(u[pk<1>(l, 0)], u[pk<1>(l + 1, 0)]);
+      const float2 u1 = make_float2(u[pk<1>(l, 1)], u[pk<1>(l + 1, 1)]);
+      const float2 v0 = make_float2(__shfl_xor_sync(kFull, u0.x, 8), __shfl_xor_sync(kFull, u0.y, 8));
+      const float2 v1 = make_float2(__shfl_xor_sync(kFull, u1.x, 8), __shfl_xor_sync(kFull, u1.y, 8));
+      const float2 t = make_float2(tscale * tr[l], tscale * tr[l + 1]);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int k = pk<1>(l, b);
+        float2 acc = __ffma2_rn(make_float2(Ln[b], Ln[b]), t, make_float2(r[k], r[k + 1]));
+        acc = __ffma2_rn(make_float2(G[b][0], G[b][0]), u0, acc);
+        acc = __ffma2_rn(make_float2(G[b][1], G[b][1]), u1, acc);
+        acc = __ffma2_rn(make_float2(G[b][2], G[b][2]), v0, acc);
+        acc = __ffma2_rn(make_float2(G[b][3], G[b][3]), v1, acc);
+        r[k] = acc.x;
+        r[k + 1] = acc.y;
+      }
+    }
+    return;
   }
 #pragma unroll
   for (int l = 0; l < 16; ++l) {
@@ -716,11 +741,14 @@ __device__ __forceinline__ void lines_split(float (&r)[32], const float (&u)[32]
   }
 }
 
-template <int J>
+// PACK: the packed FP32 FMA for the pairs of lines that hold adjacent values
+// (the operator application; the stage kernel keeps the scalar form, which
+// needs fewer registers next to its FP64 state)
+template <int J, bool PACK = false>
 __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], const float (&tr)[16],
                                         float c, int tb, float tscale, int h) {
   if constexpr (J == 1) {
-    lines_split(r, u, tr, c, tb, tscale, h);
+    lines_split<PACK>(r, u, tr, c, tb, tscale, h);
   } else {
     // the 8 local lines along J = 0 or 2
     const int side = tb + (signbit(c) ? 1 : 0);
@@ -729,15 +757,36 @@ __device__ __forceinline__ void lines_p(float (&r)[32], const float (&u)[32], co
     for (int i = 0; i < 4; ++i) Ln[i] = c * c_Ln[side][i];
 #pragma unroll
     for (int i = 0; i < 16; ++i) G[i] = c * c_G[side][i];
+    if constexpr (J == 2 && PACK) {
+      // lines (a, b) and (a + 1, b) hold adjacent values: packed FP32 FMA
+      // over the pair (per lane the same fmaf sequence as below)
 #pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      const float t = tscale * tr[l];
+      for (int l = 0; l < 8; l += 2) {
+        const float2 t = make_float2(tscale * tr[l], tscale * tr[l + 1]);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float acc = fmaf(Ln[q], t, r[pk<J>(l, q)]);
+        for (int q = 0; q < 4; ++q) {
+          const int kq = pk<J>(l, q);
+          float2 acc = __ffma2_rn(make_float2(Ln[q], Ln[q]), t, make_float2(r[kq], r[kq + 1]));
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) acc = fmaf(G[q * 4 + pp], u[pk<J>(l, pp)], acc);
-        r[pk<J>(l, q)] = acc;
+          for (int pp = 0; pp < 4; ++pp) {
+            const int kp = pk<J>(l, pp);
+            acc = __ffma2_rn(make_float2(G[q * 4 + pp], G[q * 4 + pp]), make_float2(u[kp], u[kp + 1]), acc);
+          }
+          r[kq] = acc.x;
+          r[kq + 1] = acc.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        const float t = tscale * tr[l];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float acc = fmaf(Ln[q], t, r[pk<J>(l, q)]);
+#pragma unroll
+          for (int pp = 0; pp < 4; ++pp) acc = fmaf(G[q * 4 + pp], u[pk<J>(l, pp)], acc);
+          r[pk<J>(l, q)] = acc;
+        }
       }
     }
   }
@@ -758,13 +807,13 @@ __device__ __forceinline__ void own_traces_p(float (&to)[8], const float (&u)[32
   }
 }
 
-template <int J, bool ROWS, bool ADJ>
+template <int J, bool ROWS, bool ADJ, bool PACK>
 __device__ __forceinline__ void direction_p(float (&r)[32], const float (&u)[32], const float* nbv,
                                             const int (&o)[4], float c, int tb, float wthread, int h,
                                             const Tab1D<float>& T) {
   float tr[16];
   nb_traces_p<J, ROWS, ADJ>(tr, nbv, o, c, tb, h, T);
-  lines_p<J>(r, u, tr, c, tb, ADJ ? wthread : 1.f, h);
+  lines_p<J, PACK>(r, u, tr, c, tb, ADJ ? wthread : 1.f, h);
 }
 
 // Tensor copy of one cell into a swizzled buffer: two boxes of 32 x 1 x 64
@@ -1076,12 +1125,12 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
       for (int k = 0; k < 32; ++k) u[k] *= winv_t * wprod_p(T.winv, k, h);
     }
     ok &= mv.wait(P, p.err);
-    direction_p<0, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[0], tb, winv_t, h, T);
+    direction_p<0, true, ADJ, MODE == 0>(r, u, sm6 + P * kCellF, o, sp[0], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     issue(P, nbr[2]);                            // x3
     ok &= mv.wait(Q, p.err);
-    direction_p<1, true, ADJ>(r, u, sm6 + Q * kCellF, o, sp[1], tb, winv_t, h, T);
+    direction_p<1, true, ADJ, MODE == 0>(r, u, sm6 + Q * kCellF, o, sp[1], tb, winv_t, h, T);
     fence_async_smem();
     __syncthreads();
     if constexpr (FACE)
@@ -1089,7 +1138,7 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     else
       issue(Q, nbr[3]);                          // v1
     ok &= mv.wait(P, p.err);
-    direction_p<2, true, ADJ>(r, u, sm6 + P * kCellF, o, sp[2], tb, winv_t, h, T);
+    direction_p<2, true, ADJ, MODE == 0>(r, u, sm6 + P * kCellF, o, sp[2], tb, winv_t, h, T);
     __syncthreads();                             // P is free: it takes the phase X result
     {
       float* rb = sm6 + P * kCellF;
@@ -1121,9 +1170,9 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     if constexpr (FACE) {
       float tr[16];
       face_traces<0, ADJ>(tr, sm6 + Q * kCellF, t, h, signbit(sp[3]) ? 0 : 3, T);
-      lines_p<0>(r, u, tr, sp[3], tb, ADJ ? winv_t : 1.f, h);
+      lines_p<0, MODE == 0>(r, u, tr, sp[3], tb, ADJ ? winv_t : 1.f, h);
     } else {
-      direction_p<0, false, ADJ>(r, u, sm6 + Q * kCellF, o, sp[3], tb, winv_t, h, T);
+      direction_p<0, false, ADJ, MODE == 0>(r, u, sm6 + Q * kCellF, o, sp[3], tb, winv_t, h, T);
     }
     fence_async_smem();
     __syncthreads();
@@ -1144,9 +1193,9 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     if constexpr (FACE) {
       float tr[16];
       face_traces<1, ADJ>(tr, sm6 + P * kCellF, t, h, signbit(sp[4]) ? 0 : 3, T);
-      lines_p<1>(r, u, tr, sp[4], tb, ADJ ? winv_t : 1.f, h);
+      lines_p<1, MODE == 0>(r, u, tr, sp[4], tb, ADJ ? winv_t : 1.f, h);
     } else {
-      direction_p<1, false, ADJ>(r, u, sm6 + P * kCellF, o, sp[4], tb, winv_t, h, T);
+      direction_p<1, false, ADJ, MODE == 0>(r, u, sm6 + P * kCellF, o, sp[4], tb, winv_t, h, T);
     }
     fence_async_smem();
     __syncthreads();
@@ -1176,7 +1225,7 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
     // ---- last direction fused with step 5: scatter / LSRK stage update
     const size_t g0 = static_cast<size_t>(cell) * 4096 + t + 256 * h;
     if constexpr (MODE == 0) {
-      lines_p<2>(r, u, tr, sp[5], tb, 1.f, h);
+      lines_p<2, MODE == 0>(r, u, tr, sp[5], tb, 1.f, h);
       TW* dst = static_cast<TW*>(p.dst);
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
@@ -1196,7 +1245,7 @@ __device__ __forceinline__ void cell6d4p_body(const KParams& p, const CUtensorMa
         ua[k] = __ldcs(uu + g0 + 64 * poff(k));
         ka[k] = MODE == 2 ? __ldcs(p.kref + g0 + 64 * poff(k)) : 0.f;
       }
-      lines_p<2>(r, u, tr, sp[5], tb, 1.f, h);
+      lines_p<2, MODE == 0>(r, u, tr, sp[5], tb, 1.f, h);
       TW* dst = static_cast<TW*>(p.dst);
       const float bf = static_cast<float>(p.b_dt);
       const float af = static_cast<float>(p.a_dt);
