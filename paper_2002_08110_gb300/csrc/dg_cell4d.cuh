@@ -211,24 +211,36 @@ __device__ __forceinline__ void pdir_split(float (&r)[3][kP], const float (&u)[3
       cf[4 * i + 3] = x.w;
     }
   }
+  // lines a and a + 1 (a even) hold adjacent values: they go through the
+  // packed FP32 FMA together (per lane the same sequence as one line alone)
+  const float2 c2 = make_float2(c, c);
 #pragma unroll
-  for (int a = 0; a < kP; ++a) {
-    float v[3];
+  for (int a = 0; a < kP; a += 2) {
+    float2 v[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) v[j] = __shfl_xor_sync(0xffffffffu, u[j][a], 1);
-    // the upwind neighbour's trace of line a: own half, then the partner's
-    float t = 0.f;
+    for (int j = 0; j < 3; ++j)
+      v[j] = make_float2(__shfl_xor_sync(0xffffffffu, u[j][a], 1), __shfl_xor_sync(0xffffffffu, u[j][a + 1], 1));
+    // the upwind neighbour's traces of lines a, a + 1: own half, then the partner's
+    float t0 = 0.f, t1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) t = fmaf(cf[21 + j], nb[j][a], t);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    for (int j = 0; j < 3; ++j) {
+      t0 = fmaf(cf[21 + j], nb[j][a], t0);
+      t1 = fmaf(cf[21 + j], nb[j][a + 1], t1);
+    }
+    t0 += __shfl_xor_sync(0xffffffffu, t0, 1);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, 1);
+    const float2 t = make_float2(t0, t1);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      float acc = cf[18 + i] * t;
+      float2 acc = __fmul2_rn(make_float2(cf[18 + i], cf[18 + i]), t);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) acc = fmaf(cf[3 * i + j], u[j][a], acc);
+      for (int j = 0; j < 3; ++j)
+        acc = __ffma2_rn(make_float2(cf[3 * i + j], cf[3 * i + j]), make_float2(u[j][a], u[j][a + 1]), acc);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) acc = fmaf(cf[9 + 3 * i + j], v[j], acc);
-      r[i][a] = fmaf(c, acc, r[i][a]);
+      for (int j = 0; j < 3; ++j) acc = __ffma2_rn(make_float2(cf[9 + 3 * i + j], cf[9 + 3 * i + j]), v[j], acc);
+      const float2 rr = __ffma2_rn(c2, acc, make_float2(r[i][a], r[i][a + 1]));
+      r[i][a] = rr.x;
+      r[i][a + 1] = rr.y;
     }
   }
 }
