@@ -399,6 +399,24 @@ dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, i
                         void* stream);
 
 /*
+ * Adjoint of one FP64 Vlasov-Poisson step of dg_vp_rk_step (the gradient of
+ * a final-time functional through the coupled steps, Sec. 6 with the
+ * differentiation of the north-star's pattern 3).  u: the state at the start
+ * of the step (FP64, read only); ubar: on entry dJ/du after the step, on
+ * return dJ/du before it (FP64, in place).  The step is not linear in u: its
+ * stage right-hand side is F(w) = L(a(w)) w with a_v = -E(w), E = P rho(w),
+ * so the call recomputes the step's five stage inputs from u and takes, in
+ * reverse stage order, J(w)^T = L(a)^T + R^T P^T B(w)^T with L^T the
+ * transposed operator (dg_apply_adjoint), B(w) the operator's derivative with
+ * respect to the field at the x nodes (upwind sides fixed by the current
+ * field), P^T the transposed Poisson map and R^T the transposed v
+ * quadrature.  All in FP64 kernels.  The handle owns 9 FP64 vectors of scratch
+ * for it (allocated on first use); on return its field is that of the
+ * step's first stage.  Errors: as dg_vp_rk_step.
+ */
+dg_status dg_vp_step_adjoint(dg_handle h, const double* u, double* ubar, double dt, void* stream);
+
+/*
  * The integrals of dg_integrals() for callers that cannot allocate device
  * memory: for example code inside a framework whose allocator owns all
  * device memory, or a long run that must not call cudaMalloc after start-up

@@ -109,6 +109,7 @@ def load():
         "dg_poisson_periodic_1d": (i, [vp, vp, vp, vp]),
         "dg_set_field_device": (i, [vp, vp, i, ctypes.c_double, vp]),
         "dg_vp_rk_step": (i, [vp, vp, vp, vp, ctypes.c_double, i, i, vp]),
+        "dg_vp_step_adjoint": (i, [vp, vp, vp, ctypes.c_double, vp]),
         "dg_rk_stage_host": (i, [vp, vp, vp, vp, i, ctypes.c_double, i, vp]),
         "dg_get_launch": (i, [vp, i, ctypes.POINTER(Launch)]),
         "dg_set_launch": (i, [vp, i, ctypes.POINTER(Launch)]),

@@ -260,6 +260,13 @@ class DG:
                                      float(dt), int(nsteps), prec, _stream()))
         return u
 
+    def vp_step_adjoint(self, u, ubar, dt):
+        """Adjoint of one FP64 Vlasov-Poisson step from the state ``u`` at its
+        start: ``ubar`` (dJ/du after the step) becomes dJ/du before it, in place."""
+        check(self.lib.dg_vp_step_adjoint(self.handle, self._vec(u, PREC_FP64, "u"),
+                                          self._vec(ubar, PREC_FP64, "ubar"), float(dt), _stream()))
+        return ubar
+
     def check(self):
         """Synchronise and raise DGError(DG_ERR_NONFINITE) if a kernel saw NaN/Inf."""
         check(self.lib.dg_check(self.handle, _stream()))

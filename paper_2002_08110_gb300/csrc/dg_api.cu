@@ -396,6 +396,7 @@ void free_ctx(dg_ctx* h) {
   cudaFree(h->field_flags_d);
   cudaFree(h->vp_rho);
   cudaFree(h->vp_e);
+  cudaFree(h->vpa);
   cudaFree(h->host_stage);
   cudaFree(h->in32);
   if (h->xfer_in) cudaStreamDestroy(h->xfer_in);
@@ -1077,6 +1078,101 @@ dg_status dg_vp_rk_step(dg_handle h, double* u, void* w0, void* w1, double dt, i
         return st;
     }
   }
+  return DG_OK;
+}
+
+// The tables of the 1D Poisson kernels.
+static PoissonTab poisson_tab(const dg_ctx* h) {
+  PoissonTab t;
+  std::memset(&t, 0, sizeof(t));
+  for (int q = 0; q < h->n; ++q) {
+    t.w[q] = h->tables.w[q];
+    for (int p = 0; p < h->n; ++p) t.Iq[q * kMaxN + p] = h->tables.Iq[q][p];
+  }
+  return t;
+}
+
+// One Vlasov-Poisson stage transposed (FP64): out = J(w)^T lam with
+// J(w) = L(a(w)) + B(w) P R (dg_vp_adjoint.cu); the field of w is set as the
+// forward stage sets it.  g, m: x-node scratch.
+static dg_status vp_stage_adjoint(dg_handle h, const double* w, const double* lam, double* out,
+                                  double* g, double* m, cudaStream_t s) {
+  dg_status st;
+  if ((st = dg_charge_density(h, w, DG_PREC_FP64, h->vp_rho, s)) != DG_OK) return st;
+  if ((st = dg_poisson_periodic_1d(h, h->vp_rho, h->vp_e, s)) != DG_OK) return st;
+  if ((st = set_field_device(h, h->vp_e, 1, -1.0, s)) != DG_OK) return st;   // a_v = -E
+  if ((st = apply_core(h, lam, out, DG_PREC_FP64, s, 1)) != DG_OK) return st;  // L(a)^T lam
+  double detJv = 1.0;
+  for (int j = h->dx; j < h->d; ++j) detJv *= h->h[j] / 2.0;
+  const double hphys = h->S[0] * h->h[0];
+  const PoissonTab pt = poisson_tab(h);
+  cudaError_t e;
+  if ((e = launch_field_adjoint(w, lam, h->cv_d64, h->ncx, h->ncv, h->npc, h->nqx, h->nqv, h->n, h->dv,
+                                h->ncell[h->dx], h->tables.t64, 2.0 / h->h[h->dx], g, s)) != cudaSuccess ||
+      (e = launch_poisson_1d_adjoint(g, m, h->ncx, h->n, pt, hphys, s)) != cudaSuccess ||
+      (e = launch_charge_adjoint_add(out, m, h->ncx, h->ncells, h->npc, h->nqx, h->n, h->dv,
+                                     h->tables.t64, detJv, s)) != cudaSuccess)
+    return cuda_fail(e, "Vlasov-Poisson adjoint kernels");
+  return DG_OK;
+}
+
+dg_status dg_vp_step_adjoint(dg_handle h, const double* u, double* ubar, double dt, void* stream) {
+  if (h == nullptr) return fail(DG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->basis == DG_BASIS_GLL_GAUSS)
+    return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need a collocated basis (DG_BASIS_GL or DG_BASIS_GLL)");
+  if (h->dx != 1) return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need dim_x = 1");
+  if (h->field_kind != DG_FIELD_PHASE_SPACE)
+    return fail(DG_ERR_INVALID_ARG, "Vlasov-Poisson steps need a phase-space handle");
+  if (h->curved) return fail(DG_ERR_UNSUPPORTED, "Vlasov-Poisson steps need an affine mesh");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dt is not finite");
+  dg_status st;
+  if ((st = check_vec(u, "u")) != DG_OK || (st = check_vec(ubar, "ubar")) != DG_OK) return st;
+  const size_t nb = static_cast<size_t>(h->n_dofs) * sizeof(double);
+  if (ranges_overlap(u, ubar, nb)) return fail(DG_ERR_INVALID_ARG, "u and ubar overlap");
+  if ((st = ensure_scratch(h, DG_PREC_FP64)) != DG_OK) return st;
+  cudaError_t err;
+  const size_t xb = static_cast<size_t>(h->ncx) * h->nqx * sizeof(double);
+  if (h->vp_rho == nullptr && ((err = cudaMalloc(&h->vp_rho, xb)) != cudaSuccess ||
+                               (err = cudaMalloc(&h->vp_e, xb)) != cudaSuccess))
+    return cuda_fail(err, "Vlasov-Poisson scratch");
+  if (h->vpa == nullptr && (err = cudaMalloc(&h->vpa, 9 * nb + 2 * xb)) != cudaSuccess) {
+    h->vpa = nullptr;
+    return cuda_fail(err, "adjoint Vlasov-Poisson scratch");
+  }
+  const long long n = h->n_dofs;
+  double* W[5];                          // the stage inputs w_0 .. w_4 of the step
+  for (int i = 0; i < 5; ++i) W[i] = h->vpa + i * n;
+  double* uc = h->vpa + 5 * n;           // the running state of the recomputation
+  double* wbar = h->vpa + 6 * n;
+  double* kbar = h->vpa + 7 * n;
+  double* tmp = h->vpa + 8 * n;
+  double* g = h->vpa + 9 * n;
+  double* m = g + h->ncx * h->nqx;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // recompute the step's stage inputs (the forward stages of dg_vp_rk_step)
+  if ((err = cudaMemcpyAsync(W[0], u, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(uc, u, nb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_fail(err, "adjoint stage copies");
+  for (int sg = 0; sg < 4; ++sg) {
+    if ((st = dg_charge_density(h, W[sg], DG_PREC_FP64, h->vp_rho, s)) != DG_OK) return st;
+    if ((st = dg_poisson_periodic_1d(h, h->vp_rho, h->vp_e, s)) != DG_OK) return st;
+    if ((st = set_field_device(h, h->vp_e, 1, -1.0, s)) != DG_OK) return st;
+    if ((st = enqueue_stage(h, W[sg], W[sg + 1], uc, sg, dt, DG_PREC_FP64, 0, s)) != DG_OK) return st;
+  }
+  // reverse through the stages: u_{s+1} = u_s + B_s dt K_s, w_{s+1} = u_s +
+  // A_s dt K_s, K_s = F(w_s); the last stage's w output is not an output of
+  // the step, so wbar starts at zero
+  if ((err = cudaMemsetAsync(wbar, 0, nb, s)) != cudaSuccess) return cuda_fail(err, "adjoint init");
+  for (int sg = 4; sg >= 0; --sg) {
+    const double a = sg < 4 ? kRkA[sg] * dt : 0.0;
+    if ((err = launch_lincomb(kbar, kRkB[sg] * dt, ubar, a, wbar, n, s)) != cudaSuccess ||
+        (err = launch_axpy(ubar, 1.0, wbar, n, s)) != cudaSuccess)
+      return cuda_fail(err, "adjoint stage combination");
+    if ((st = vp_stage_adjoint(h, W[sg], kbar, tmp, g, m, s)) != DG_OK) return st;
+    std::swap(wbar, tmp);
+  }
+  if ((err = launch_axpy(ubar, 1.0, wbar, n, s)) != cudaSuccess)   // w_0 = u
+    return cuda_fail(err, "adjoint stage combination");
   return DG_OK;
 }
 

@@ -184,6 +184,17 @@ struct PoissonTab {
 };
 cudaError_t launch_poisson_1d(const double* rho, double* e, long long ncx, int n,
                               const PoissonTab& t, double hphys, cudaStream_t s);
+// pieces of the transposed Vlasov-Poisson stage (dg_vp_adjoint.cu)
+cudaError_t launch_field_adjoint(const double* w, const double* lam, const double* cv64, long long ncx,
+                                 long long ncv, int npc, int nqx, int nqv, int n, int dv, long long ncv1,
+                                 const Tab1D<double>& t, double two_over_h, double* g, cudaStream_t s);
+cudaError_t launch_poisson_1d_adjoint(const double* y, double* out, long long ncx, int n,
+                                      const PoissonTab& t, double hphys, cudaStream_t s);
+cudaError_t launch_charge_adjoint_add(double* out, const double* m, long long ncx, long long ncells,
+                                      int npc, int nqx, int n, int dv, const Tab1D<double>& t,
+                                      double detJv, cudaStream_t s);
+cudaError_t launch_lincomb(double* y, double a, const double* x, double b, const double* z, long long n,
+                           cudaStream_t s);
 cudaError_t launch_field_speeds(const double* e, int comps, double scale, long long ncx, int nq,
                                 int dv, const double* two_over_hv, double* cv64, float* cv32,
                                 int* flags, int* err, cudaStream_t s);
@@ -258,6 +269,7 @@ struct dg_ctx {
   bool df_ready = false;
   double* vp_rho = nullptr;     // Vlasov-Poisson scratch: rho and E at the x nodes
   double* vp_e = nullptr;
+  double* vpa = nullptr;        // adjoint Vlasov-Poisson step: 9 FP64 vectors and 2 x-node arrays
   // device staging of the host-buffer stage call: u (FP64) and two stage vectors
   void* host_stage = nullptr; size_t host_stage_bytes = 0;
   float* in32 = nullptr;        // FP32 copy of an FP64 kernel input (n_dofs)
