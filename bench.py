@@ -514,8 +514,10 @@ def measure_configs(torch, hbm_peak, only=None):
         best = batch.autotune(us, w0s, w1s, dts, prec=PREC_FP32)
         # one untimed step: the kept configuration's graphs are captured anew
         batch.rk_step(us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32)
+        # four steps in one call (a call converts the FP64 states to the FP32
+        # stage vectors once, whatever its number of steps)
         reps = 4
-        ms = _timed(torch, lambda: batch.rk_step(us, w0s, w1s, dts, nsteps=1, prec=PREC_FP32), reps)
+        ms = _timed(torch, lambda: batch.rk_step(us, w0s, w1s, dts, nsteps=reps, prec=PREC_FP32), 1) / reps
         batch.check()
         st = ms / 5
         out["batched"] = {"workload": "64 instances, d in {3,4}, k in {2..5}, 8..24 cells/dir",
