@@ -1,7 +1,7 @@
 // Shared helpers of the kernels that stage cells in shared memory with the
 // TMA engine: mbarrier arrive / bounded wait, bulk copies, L2 policies and
-// prefetch, the generic-to-async proxy fence, and the driver's tensor-map
-// encoder.
+// prefetch, the generic-to-async proxy fence, and the CUDA driver's
+// tensor-map encoder.
 #pragma once
 
 #include <cuda.h>
@@ -74,7 +74,7 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// The driver's tensor-map encoder, looked up once through the runtime.
+// The CUDA driver's tensor-map encoder, looked up once through the runtime.
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static bool tried = false;
