@@ -51,17 +51,17 @@ struct Cell4 {
 // speed (nonzero).  Positive speed: r += c (Gp u + Lm t), t the neighbour
 // below's trace at +1; negative: r += c (Gn u - Lp t), t the neighbour
 // above's trace at -1.
-template <int N, int ST>
-__device__ __forceinline__ void dir4(float (&r)[N * N], const float (&u)[N * N],
-                                     const float (&nb)[N * N], float c, const Tab1D<float>& T) {
-  const bool pos = c > 0.f;
-  float G[N * N], L[N], l[N];
-#pragma unroll
-  for (int k = 0; k < N * N; ++k) G[k] = pos ? T.Gp[k] : T.Gn[k];
+// The side is a template argument, so the 1D tables are constant operands (no
+// registers, no per-thread selects); dir4 branches on the sign.
+template <int N, int ST, bool POS>
+__device__ __forceinline__ void dir4s(float (&r)[N * N], const float (&u)[N * N],
+                                      const float (&nb)[N * N], float c, const Tab1D<float>& T) {
+  const float* G = POS ? T.Gp : T.Gn;
+  float L[N], l[N];
 #pragma unroll
   for (int q = 0; q < N; ++q) {
-    L[q] = pos ? T.Lm[q] : -T.Lp[q];
-    l[q] = pos ? T.lp[q] : T.lm[q];
+    L[q] = POS ? T.Lm[q] : -T.Lp[q];
+    l[q] = POS ? T.lp[q] : T.lm[q];
   }
   constexpr int OT = ST == 1 ? N : 1;     // stride between the lines
 #pragma unroll
@@ -78,6 +78,13 @@ __device__ __forceinline__ void dir4(float (&r)[N * N], const float (&u)[N * N],
       r[b + q * ST] = fmaf(c, acc, r[b + q * ST]);
     }
   }
+}
+
+template <int N, int ST>
+__device__ __forceinline__ void dir4(float (&r)[N * N], const float (&u)[N * N],
+                                     const float (&nb)[N * N], float c, const Tab1D<float>& T) {
+  if (c > 0.f) dir4s<N, ST, true>(r, u, nb, c, T);
+  else dir4s<N, ST, false>(r, u, nb, c, T);
 }
 
 // A neighbour's column k (S contiguous values) into registers.
