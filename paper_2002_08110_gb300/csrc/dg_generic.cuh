@@ -62,6 +62,82 @@ struct CellInfo {
   static constexpr int kLen = 2 + 2 * D;
 };
 
+// One x line of a curved x-mesh (DXN = dim_x at compile time, so that the
+// loops over the Jacobian's components unroll).  Curved x-mesh: the flux speed
+// g = |J_x| c_j varies along the line.  With collocation the line's weak form
+// divided by the diagonal mass reads du_q = (1/|J_x,q|) [sum_p Dt[q][p] g_p u_p
+// - Lp[q] F(+1) + Lm[q] F(-1)], F(+-1) = g(+-1) u*(+-1) with the upwind state
+// at each face.
+template <int DXN, int D, int N, typename TC, typename TIN, bool SMEM, int J>
+__device__ __forceinline__ void curved_line(const KParams& p, const Tab1D<TC>& T, const TIN* src,
+                                            const TC* su, TC* sr, const long long* ci, int c,
+                                            long long cell, int base, int qx, int qv, int nqx, int nqv) {
+  constexpr int NP = Pow<N, D>::v;
+  constexpr int sj = Pow<N, J>::v;
+  const long long cx = ci[0], cv = ci[1];
+  constexpr int dxn = DXN, sc = 1 + DXN * DXN;
+  const TC* A = static_cast<const TC*>(p.ax_tab) + (cv * nqv + qv) * dxn;
+  const TC* Gc = static_cast<const TC*>(p.geo_c) + cx * nqx * sc;
+  TC uu[N], g[N], ij[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    uu[q] = SMEM ? su[c * NP + base + q * sj] : cvt<TC>(src[cell * NP + base + q * sj]);
+    const TC* gq = Gc + (qx + q * sj) * sc;
+    TC cq = TC(0);
+#pragma unroll
+    for (int m = 0; m < dxn; ++m) cq += gq[1 + J * dxn + m] * A[m];
+    g[q] = cq;
+    ij[q] = TC(1) / gq[0];
+  }
+  int f = 0, mul = 1, rr = qx, nf = 1;
+#pragma unroll
+  for (int m = 0; m < dxn; ++m) {
+    const int dg = rr % N;
+    rr /= N;
+    if (m != J) {
+      f += dg * mul;
+      mul *= N;
+      nf *= N;
+    }
+  }
+  const TC* Fm = static_cast<const TC*>(p.geo_f) + ((((cx * dxn + J) * 2 + 0) * nf) + f) * dxn;
+  const TC* Fp = static_cast<const TC*>(p.geo_f) + ((((cx * dxn + J) * 2 + 1) * nf) + f) * dxn;
+  TC gm = TC(0), gp = TC(0);
+#pragma unroll
+  for (int m = 0; m < dxn; ++m) {
+    gm += Fm[m] * A[m];
+    gp += Fp[m] * A[m];
+  }
+  TC tp = TC(0), tm = TC(0);
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    tp += T.lp[q] * uu[q];
+    tm += T.lm[q] * uu[q];
+  }
+  TC up = tp, um = tm;
+  if (!(gp > TC(0))) {           // inflow at +1: the neighbour above's -1 trace
+    const TIN* ns = src + ci[2 + 2 * J + 1] * NP + base;
+    up = TC(0);
+#pragma unroll
+    for (int q = 0; q < N; ++q) up += T.lm[q] * cvt<TC>(ns[q * sj]);
+  }
+  if (gm > TC(0)) {              // inflow at -1: the neighbour below's +1 trace
+    const TIN* ns = src + ci[2 + 2 * J] * NP + base;
+    um = TC(0);
+#pragma unroll
+    for (int q = 0; q < N; ++q) um += T.lp[q] * cvt<TC>(ns[q * sj]);
+  }
+  const TC Fplus = gp * up, Fminus = gm * um;
+  TC* r = sr + c * NP + base;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    TC acc = T.Lm[q] * Fminus - T.Lp[q] * Fplus;
+#pragma unroll
+    for (int s2 = 0; s2 < N; ++s2) acc += T.Dt[q * N + s2] * (g[s2] * uu[s2]);
+    r[q * sj] += ij[q] * acc;
+  }
+}
+
 // The lines of direction J of the block's cells (J compile-time, so that the
 // line stride N^J is a constant).
 template <int D, int N, typename TC, typename TIN, bool SMEM, bool CURVED, int J>
@@ -82,68 +158,14 @@ __device__ __forceinline__ void sweep_dir(const KParams& p, const Tab1D<TC>& T, 
     const int qv = p.dx == 1 ? base / N : (p.dx == 2 ? base / (N * N) : base / (N * N * N));
     const int qx = base - qv * nqx;
     if (CURVED && J < p.dx) {
-      // Curved x-mesh: the flux speed g = |J_x| c_j varies along the line.
-      // With collocation the line's weak form divided by the diagonal mass
-      // reads du_q = (1/|J_x,q|) [sum_p Dt[q][p] g_p u_p - Lp[q] F(+1)
-      //                            + Lm[q] F(-1)],
-      // F(+-1) = g(+-1) u*(+-1) with the upwind state at each face.
-      const int dxn = p.dx, sc = 1 + dxn * dxn;
-      const TC* A = static_cast<const TC*>(p.ax_tab) + (cv * nqv + qv) * dxn;
-      const TC* Gc = static_cast<const TC*>(p.geo_c) + cx * nqx * sc;
-      TC uu[N], g[N], ij[N];
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        uu[q] = SMEM ? su[c * NP + base + q * sj] : cvt<TC>(src[cell * NP + base + q * sj]);
-        const TC* gq = Gc + (qx + q * sj) * sc;
-        TC cq = TC(0);
-        for (int m = 0; m < dxn; ++m) cq += gq[1 + J * dxn + m] * A[m];
-        g[q] = cq;
-        ij[q] = TC(1) / gq[0];
-      }
-      int f = 0, mul = 1, rr = qx, nf = 1;
-      for (int m = 0; m < dxn; ++m) {
-        const int dg = rr % N;
-        rr /= N;
-        if (m != J) {
-          f += dg * mul;
-          mul *= N;
-          nf *= N;
+      if constexpr (CURVED) {
+        if (p.dx == 3) {
+          if constexpr (J < 3 && D >= 4) curved_line<3, D, N, TC, TIN, SMEM, J>(p, T, src, su, sr, ci, c, cell, base, qx, qv, nqx, nqv);
+        } else if (p.dx == 2) {
+          if constexpr (J < 2 && D >= 3) curved_line<2, D, N, TC, TIN, SMEM, J>(p, T, src, su, sr, ci, c, cell, base, qx, qv, nqx, nqv);
+        } else {
+          if constexpr (J < 1) curved_line<1, D, N, TC, TIN, SMEM, J>(p, T, src, su, sr, ci, c, cell, base, qx, qv, nqx, nqv);
         }
-      }
-      const TC* Fm = static_cast<const TC*>(p.geo_f) + ((((cx * dxn + J) * 2 + 0) * nf) + f) * dxn;
-      const TC* Fp = static_cast<const TC*>(p.geo_f) + ((((cx * dxn + J) * 2 + 1) * nf) + f) * dxn;
-      TC gm = TC(0), gp = TC(0);
-      for (int m = 0; m < dxn; ++m) {
-        gm += Fm[m] * A[m];
-        gp += Fp[m] * A[m];
-      }
-      TC tp = TC(0), tm = TC(0);
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        tp += T.lp[q] * uu[q];
-        tm += T.lm[q] * uu[q];
-      }
-      TC up = tp, um = tm;
-      if (!(gp > TC(0))) {           // inflow at +1: the neighbour above's -1 trace
-        const TIN* ns = src + ci[2 + 2 * J + 1] * NP + base;
-        up = TC(0);
-#pragma unroll
-        for (int q = 0; q < N; ++q) up += T.lm[q] * cvt<TC>(ns[q * sj]);
-      }
-      if (gm > TC(0)) {              // inflow at -1: the neighbour below's +1 trace
-        const TIN* ns = src + ci[2 + 2 * J] * NP + base;
-        um = TC(0);
-#pragma unroll
-        for (int q = 0; q < N; ++q) um += T.lp[q] * cvt<TC>(ns[q * sj]);
-      }
-      const TC Fplus = gp * up, Fminus = gm * um;
-      TC* r = sr + c * NP + base;
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        TC acc = T.Lm[q] * Fminus - T.Lp[q] * Fplus;
-#pragma unroll
-        for (int s2 = 0; s2 < N; ++s2) acc += T.Dt[q * N + s2] * (g[s2] * uu[s2]);
-        r[q * sj] += ij[q] * acc;
       }
       continue;
     }
