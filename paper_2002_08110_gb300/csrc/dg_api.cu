@@ -847,8 +847,12 @@ dg_status dg_create(int dim_x, int dim_v, int degree, const int* cells_x, const 
   if (h->curved) {
     std::vector<double> jx(static_cast<size_t>(h->ncx) * h->nqx);
     for (size_t i = 0; i < jx.size(); ++i) jx[i] = h->geo_c_host[i * (1 + dim_x * dim_x)];
-    if ((e = upload(h->geo_c_host, &h->geo_c64)) != cudaSuccess ||
-        (e = upload(h->geo_c_host, &h->geo_c32)) != cudaSuccess ||
+    // the kernels divide by |J_x| at every point: the device table holds its
+    // reciprocal (computed here in FP64)
+    std::vector<double> gc(h->geo_c_host);
+    for (size_t i = 0; i < jx.size(); ++i) gc[i * (1 + dim_x * dim_x)] = 1.0 / jx[i];
+    if ((e = upload(gc, &h->geo_c64)) != cudaSuccess ||
+        (e = upload(gc, &h->geo_c32)) != cudaSuccess ||
         (e = upload(h->geo_f_host, &h->geo_f64)) != cudaSuccess ||
         (e = upload(h->geo_f_host, &h->geo_f32)) != cudaSuccess ||
         (e = upload(h->ax_host, &h->ax64)) != cudaSuccess ||

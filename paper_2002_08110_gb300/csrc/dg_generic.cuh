@@ -87,7 +87,7 @@ __device__ __forceinline__ void curved_line(const KParams& p, const Tab1D<TC>& T
 #pragma unroll
     for (int m = 0; m < dxn; ++m) cq += gq[1 + J * dxn + m] * A[m];
     g[q] = cq;
-    ij[q] = TC(1) / gq[0];
+    ij[q] = gq[0];                       // 1 / |J_x| at the point
   }
   int f = 0, mul = 1, rr = qx, nf = 1;
 #pragma unroll

@@ -115,7 +115,7 @@ struct KParams {
   // src (same rounding as its own loads), read by tensor copies instead
   const float* src32;
   // curved x-mesh (nullptr: affine), in the compute type: per x cell and x
-  // point [ncx][n^dx][1 + dx*dx] = (|J_x|, |J_x| J_x^{-1} row-major); per x
+  // point [ncx][n^dx][1 + dx*dx] = (1/|J_x|, |J_x| J_x^{-1} row-major); per x
   // cell, direction j, side (0: -1, 1: +1) and face point (the other x
   // digits) [ncx][dx][2][n^(dx-1)][dx] = |J_x| (J_x^{-1})_{j,:}; and the
   // physical a_x at the v points [ncv][n^dv][dx]
