@@ -19,3 +19,18 @@ def test_flop_entry_counts_the_folded_line_operator():
 def test_algorithmic_bytes_per_dof():
     b = bench.BYTES_PER_DOF
     assert b["stage_fp32w_fp64u"] == 24 and b["apply_fp32"] == 8 and b["apply_fp64"] == 16
+
+
+def test_kernel_hash_ignores_comments_only(tmp_path, monkeypatch):
+    """The recorded DRAM bytes stay keyed to the stage kernel's code: a comment
+    or whitespace edit keeps the hash, a code edit changes it."""
+    csrc = tmp_path / "paper_2002_08110_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ["k.cu"])
+    (csrc / "k.cu").write_text("// one\nint f(int x) { return x + 1; }  /* two */\n")
+    h0 = bench.kernel_hash()
+    (csrc / "k.cu").write_text("// changed comment\nint  f(int x)\n{ return x + 1; }\n/* other\n block */\n")
+    assert bench.kernel_hash() == h0
+    (csrc / "k.cu").write_text("// one\nint f(int x) { return x + 2; }\n")
+    assert bench.kernel_hash() != h0
