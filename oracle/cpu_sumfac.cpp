@@ -8,9 +8,11 @@
 // along every direction (sum factorisation, Sec. 2.4 and Algorithm 2), the
 // upwind flux on the 2d faces with the neighbour's trace across periodic
 // boundaries, and the inverse of the diagonal mass matrix of the
-// Gauss-Legendre collocation (Algorithm 2 step 4).  FP64 throughout, OpenMP
-// over cells.  It shares no code with the CUDA library: its 1D tables come
-// from its own Newton iteration on the Legendre polynomials, and it keeps
+// Gauss-Legendre collocation (Algorithm 2 step 4), or of the Gauss-Lobatto
+// collocation (nodes and quadrature at the Lobatto points).  FP64
+// throughout, OpenMP over cells.  It shares no code with the CUDA library:
+// its 1D tables come from its own Newton iterations on the Legendre
+// polynomials, and it keeps
 // the cell and face terms apart as the weak form states them.
 //
 // Per direction j and line of n nodes (all other node digits fixed), with
@@ -81,6 +83,43 @@ void gauss_legendre(int n, double* x, double* w) {
   }
 }
 
+// n-point Gauss-Lobatto rule (n >= 2): the end points and the N - 1 interior
+// roots of P_N' (N = n - 1), by Newton's method on P_N' with P_N'' from
+// Legendre's equation (1 - z^2) P'' - 2 z P' + N (N + 1) P = 0, started from
+// the Chebyshev-Lobatto points; weights 2 / (N (N + 1) P_N(z)^2).
+void gauss_lobatto(int n, double* x, double* w) {
+  const int N = n - 1;
+  const double pi = 3.14159265358979323846;
+  auto legendre = [N](double z, double& pN, double& pNm1) {
+    double p0 = 1.0, p1 = z;
+    for (int m = 2; m <= N; ++m) {
+      const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+      p0 = p1;
+      p1 = p2;
+    }
+    pN = p1;
+    pNm1 = p0;
+  };
+  for (int i = 0; i < n; ++i) {
+    double z = -std::cos(pi * i / N);
+    if (i > 0 && i < N) {
+      for (int it = 0; it < 100; ++it) {
+        double pN, pNm1;
+        legendre(z, pN, pNm1);
+        const double d1 = N * (z * pN - pNm1) / (z * z - 1.0);                 // P_N'
+        const double d2 = (2.0 * z * d1 - N * (N + 1.0) * pN) / (1.0 - z * z);   // P_N''
+        const double dz = d1 / d2;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+    }
+    double pN, pNm1;
+    legendre(z, pN, pNm1);
+    x[i] = z;
+    w[i] = 2.0 / (N * (N + 1.0) * pN * pN);
+  }
+}
+
 // Lagrange basis through the nodes z: value of phi_i at t.
 double lagrange(const double* z, int n, int i, double t) {
   double v = 1.0;
@@ -116,6 +155,8 @@ typedef struct {
   int field_kind;           // 0 constant a; 1 a = (v_1..v_dx, E(x))
   double a[6];
   const double* e_nodes;    // kind 1: [ncx][n^dx][dv], E at the x nodes (NULL: E = 0)
+  int basis;                // 0: Gauss-Legendre collocation; 1: Gauss-Lobatto
+                            // collocation (nodes and quadrature at the GLL points, k >= 1)
 } sf_problem;
 
 struct sf_plan {
@@ -140,7 +181,7 @@ int sf_threads(void) {
 
 sf_plan* sf_create(const sf_problem* pb) {
   if (!pb || pb->dx < 1 || pb->dv < 1 || pb->dx + pb->dv > kMaxD || pb->k < 0 ||
-      pb->k + 1 > kMaxN)
+      pb->k + 1 > kMaxN || pb->basis < 0 || pb->basis > 1 || (pb->basis == 1 && pb->k < 1))
     return nullptr;
   sf_plan* p = new sf_plan();
   p->dx = pb->dx;
@@ -163,7 +204,8 @@ sf_plan* sf_create(const sf_problem* pb) {
   p->ncx = 1;
   for (int j = 0; j < dx; ++j) p->ncx *= pb->cells[j];
   p->ncv = p->ncells / p->ncx;
-  gauss_legendre(n, p->zeta, p->w);
+  if (pb->basis == 1) gauss_lobatto(n, p->zeta, p->w);
+  else gauss_legendre(n, p->zeta, p->w);
   for (int q = 0; q < n; ++q)
     for (int pp = 0; pp < n; ++pp) p->Dw[q][pp] = lagrange_d(p->zeta, n, q, p->zeta[pp]) * p->w[pp];
   for (int i = 0; i < n; ++i) {

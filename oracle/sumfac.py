@@ -24,7 +24,7 @@ class Problem_(ctypes.Structure):
                 ("cells", ctypes.c_int * 6), ("lo", ctypes.c_double * 6),
                 ("hi", ctypes.c_double * 6), ("S", ctypes.c_double * 9),
                 ("field_kind", ctypes.c_int), ("a", ctypes.c_double * 6),
-                ("e_nodes", ctypes.POINTER(ctypes.c_double))]
+                ("e_nodes", ctypes.POINTER(ctypes.c_double)), ("basis", ctypes.c_int)]
 
 
 def build():
@@ -75,13 +75,17 @@ def threads():
 class SumFac:
     """Plan for one mesh and field.  ``e_nodes`` (phase-space field): E at
     the x nodes, array (x cells, x nodes, dv) with cells and nodes
-    lexicographic (first direction fastest)."""
+    lexicographic (first direction fastest).  ``basis``: "gl" (Gauss-Legendre
+    collocation) or "gllc" (Gauss-Lobatto collocation, k >= 1)."""
 
     def __init__(self, dx, dv, k, cells_x, cells_v, x_lo, x_hi, v_lo, v_hi, a=None,
-                 e_nodes=None, shear=None):
+                 e_nodes=None, shear=None, basis="gl"):
         lib = load()
         pb = Problem_()
         pb.dx, pb.dv, pb.k = dx, dv, k
+        if basis not in ("gl", "gllc"):
+            raise ValueError("basis must be 'gl' or 'gllc'")
+        pb.basis = 0 if basis == "gl" else 1
         for j, c in enumerate(list(cells_x) + list(cells_v)):
             pb.cells[j] = int(c)
         for j, (a_, b_) in enumerate(zip(list(x_lo) + list(v_lo), list(x_hi) + list(v_hi))):

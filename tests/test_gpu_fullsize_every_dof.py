@@ -6,7 +6,8 @@ term scale M^{-1} |A| |w| (``apply_abs``; the oracle is pinned to the dense
 and axis-wise routes, and its term scale to ``Problem.apply_abs``, in
 ``test_oracle_sumfac.py``).
 
-6D: 8^6 cells, k = 3 (1.07e9 values; the 128-thread pencil kernel).
+6D: 8^6 cells, k = 3 (1.07e9 values; the 128-thread pencil kernel), in the
+Gauss-Legendre and the Gauss-Lobatto collocation (the face-layer variant).
 5D adjoint workload: 12^2 x 8^3 cells (the persistent 5D kernel).
 4D at k = 5: 16^4 cells (the pair kernel).
 The host holds the stage vector, the oracle's K and term scale, and the GPU's
@@ -41,18 +42,20 @@ def _mem_available_gb():
     return 0.0
 
 
-def _stage_every_dof(w, stage, state):
+def _stage_every_dof(w, stage, state, basis=0, floor_rel=0.0):
     """One FP32-sweep stage of workload ``w`` on the GPU from the FP64 state
-    ``state`` (host array), checked value by value against the CPU oracle."""
+    ``state`` (host array), checked value by value against the CPU oracle.
+    basis 1: Gauss-Lobatto collocation.  floor_rel: an allowance on K relative
+    to the largest term scale (see the Lobatto test)."""
     from oracle.sumfac import SumFac
-    from paper_2002_08110_gb300 import DG, PREC_FP32, reference_nodes
+    from paper_2002_08110_gb300 import DG, PREC_FP32, basis_nodes
     n = w.n_dofs
     if _mem_available_gb() < 48.0 * n / 1.0e9 + 8.0:
         pytest.skip(f"needs ~{48 * n / 1e9 + 8:.0f} GB of free host memory")
-    zeta, _ = reference_nodes(w.k)
-    e = W.e_table(w, zeta)
+    _, qpts, _ = basis_nodes(basis, w.k)
+    e = W.e_table(w, qpts)
     dt, _ = W.time_step(w)
-    dg = DG(e_nodes=e, **W.dg_kwargs(w))
+    dg = DG(e_nodes=e, basis=basis, **W.dg_kwargs(w))
     assert dg.get_launch(PREC_FP32)["variant"] >= 1
     u = torch.from_numpy(state).to("cuda")
     w_in = u.float()
@@ -68,11 +71,12 @@ def _stage_every_dof(w, stage, state):
     torch.cuda.empty_cache()
     kw = dict(e_nodes=e) if w.field_kind == 1 else dict(a=w.a_const)
     sf = SumFac(w.dx, w.dv, w.k, w.cells_x, w.cells_v, w.x_lo, w.x_hi, w.v_lo, w.v_hi,
-                shear=W.dg_kwargs(w).get("shear"), **kw)
+                shear=W.dg_kwargs(w).get("shear"), basis="gllc" if basis == 1 else "gl", **kw)
     K = sf.apply(win)
     S = sf.apply_abs(win)
     sf.close()
     del win
+    floor = floor_rel * float(S.max())
     a = lsrk.B[4] if stage == 4 else lsrk.A[stage]
     chunk = 1 << 24
     worst_u = worst_w = 0.0
@@ -82,7 +86,7 @@ def _stage_every_dof(w, stage, state):
         u_ref = uo + lsrk.B[stage] * dt * Kc
         w_ref = u_ref if stage == 4 else uo + a * dt * Kc
         # K to 1e-5 of its term scale (the FP32 sweeps), u in FP64 on top
-        bound_u = 1e-14 * np.abs(u_ref) + 1e-5 * dt * (Sc + np.abs(Kc))
+        bound_u = 1e-14 * np.abs(u_ref) + 1e-5 * dt * (Sc + np.abs(Kc)) + dt * floor
         ru = np.abs(u_new[sl] - u_ref) / bound_u
         # w_out adds its own FP32 rounding
         bound_w = bound_u + 2.5e-7 * (np.abs(uo) + np.abs(a * dt * Kc)) + 1e-30
@@ -99,6 +103,17 @@ def test_6d_stage_every_value():
     w = W.config_6d()
     zeta = np.polynomial.legendre.leggauss(w.n)[0]
     _stage_every_dof(w, 1, W.separable_state(w, zeta))
+
+
+def test_6d_gauss_lobatto_collocation_stage_every_value():
+    """The Lobatto-collocation stage at 8^6 (the face-layer kernel).  Speeds
+    below 1e-12 of a cell's largest (v = 0 on Lobatto face nodes, E at its
+    zeros) carry no flux in the FP32 tables: entries made only of such terms
+    are exact to 1e-12 of the largest term scale."""
+    from paper_2002_08110_gb300 import basis_nodes
+    w = W.config_6d()
+    nodes, _, _ = basis_nodes(1, w.k)
+    _stage_every_dof(w, 2, W.separable_state(w, nodes), basis=1, floor_rel=1e-12)
 
 
 def test_5d_adjoint_workload_stage_every_value():

@@ -22,7 +22,7 @@ CASES = [
 ]
 
 
-def _pair(dx, dv, k, cells, kind, seed):
+def _pair(dx, dv, k, cells, kind, seed, basis="gl"):
     rng = np.random.default_rng(seed)
     d = dx + dv
     x_lo, x_hi, v_lo, v_hi = [0.0] * dx, [1.0] * dx, [-1.0] * dv, [1.5] * dv
@@ -30,17 +30,18 @@ def _pair(dx, dv, k, cells, kind, seed):
     if kind == "const":
         a = rng.uniform(-1, 1, d)
         p = Problem(dx, dv, k, cells[:dx], cells[dx:], x_lo, x_hi, v_lo, v_hi, ConstantField(a),
-                    shear=shear)
-        sf = SumFac(dx, dv, k, cells[:dx], cells[dx:], x_lo, x_hi, v_lo, v_hi, a=a, shear=shear)
+                    shear=shear, basis=basis)
+        sf = SumFac(dx, dv, k, cells[:dx], cells[dx:], x_lo, x_hi, v_lo, v_hi, a=a, shear=shear,
+                    basis=basis)
     else:
         amp, ph = rng.uniform(0.3, 1.0, dv), rng.uniform(0, 1, dv)
 
         def E(yx):
             return amp * np.sin(2 * np.pi * (np.asarray(yx).sum(-1, keepdims=True) + ph))
         p = Problem(dx, dv, k, cells[:dx], cells[dx:], x_lo, x_hi, v_lo, v_hi,
-                    PhaseSpaceField(dx, dv, E), shear=shear)
+                    PhaseSpaceField(dx, dv, E), shear=shear, basis=basis)
         sf = SumFac(dx, dv, k, cells[:dx], cells[dx:], x_lo, x_hi, v_lo, v_hi,
-                    e_nodes=e_table_from_oracle(p, E), shear=shear)
+                    e_nodes=e_table_from_oracle(p, E), shear=shear, basis=basis)
     return sf, p
 
 
@@ -103,3 +104,19 @@ def test_sumfac_stage_on_a_cell_range():
     assert np.array_equal(part_u[:lo * npc], u[:lo * npc])
     assert np.array_equal(part_u[hi * npc:], u[hi * npc:])
     sf.close()
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[2] >= 1], ids=lambda c: f"{c[0]}x{c[1]}v_k{c[2]}")
+@pytest.mark.parametrize("kind", ["const", "phase"])
+def test_sumfac_gauss_lobatto_collocation_equals_oracle(case, kind):
+    """The Gauss-Lobatto collocation (nodes and quadrature at the Lobatto
+    points; the traces are the face nodes) against the oracle's "gllc"
+    element, operator and term scale to round-off."""
+    dx, dv, k, cells = case
+    if kind == "phase" and dv < dx:
+        pytest.skip("phase-space field needs dv >= dx")
+    sf, p = _pair(dx, dv, k, cells, kind, seed=5 * k + dx + 3 * dv, basis="gllc")
+    u = np.random.default_rng(2).standard_normal(p.n_dofs)
+    scale = p.apply_abs(u)
+    assert_term_scale(sf.apply(u), p.apply(u), scale, 1e-13, what="Lobatto collocation")
+    assert np.max(np.abs(sf.apply_abs(u) - scale) / np.maximum(scale, 1e-300)) <= 1e-13
