@@ -103,6 +103,8 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.dg_rk_step(None, None, None, None, 0.1, 1, 0, 0, None) == 1
     assert lib.dg_rk_stage(None, None, None, None, 0, 0.1, 0, 0, None) == 1
     assert lib.dg_check(None, None) == 1
+    assert lib.dg_vp_rk_step(None, None, None, None, 0.1, 1, 0, None) == 1
+    assert lib.dg_vp_step_adjoint(None, None, None, 0.1, None) == 1
     assert lib.dg_destroy(None) == 0
 
 
